@@ -1,0 +1,232 @@
+/*
+ * bst.h -- C ABI of the block-sparse symmetric tensor library (GB300, sm_103a).
+ *
+ * A symmetric tensor is a direct sum of dense reduced blocks, each labelled
+ * by one conserved charge per leg (Sec. 2, Eqs. "tensor-blocks" and
+ * "tensor-cgc").  Every leg has a direction (flow); a block is allowed iff
+ * its charges satisfy the addition rule sum_i flow_i * q_i = 0, all other
+ * blocks being identically zero (Sec. 2, worked example and the remark on
+ * forbidden blocks; no global charge shift is allowed).  For U(1) the
+ * generalised Clebsch-Gordan coefficient of a block is a single number and
+ * the rule is enforced by hand (Sec. 2, text after Eq. "tensor-cgc").
+ *
+ * Conventions used by every call:
+ *   - charges are integers: 2*Sz for U(1);
+ *   - a leg's sectors are given with strictly ascending charges and
+ *     positive reduced degeneracies (Sec. 2, "Reduced and Total
+ *     Dimensions": the reduced dimension is the sum of the degeneracies);
+ *   - canonical layout: blocks are the allowed sector tuples sorted
+ *     lexicographically by per-leg sector index (leg 0 most significant);
+ *     each block is dense row-major (leg 0 slowest); blocks are stored
+ *     back to back, so a tensor's data is one array of nnz doubles;
+ *   - all data pointers named `*_data` / `a`, `b`, `c`, ... are DEVICE
+ *     pointers owned by the caller; the library never frees them;
+ *   - layouts are immutable and reference counted; every call that returns
+ *     a layout returns a new reference the caller must release;
+ *   - compute calls are asynchronous and ordered on the given stream; the
+ *     returned status covers argument, symmetry and planning errors and
+ *     launch failures; device-side errors (bounded waits, non-finite
+ *     values) are recorded in a device error word read by bst_ctx_sync;
+ *   - no C++ exception and no abort crosses this interface; on error the
+ *     output arguments are left untouched and bst_last_error() returns a
+ *     message for the calling thread.
+ */
+#ifndef BST_H
+#define BST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BST_API __attribute__((visibility("default")))
+#else
+#define BST_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* bst_stream; /* a cudaStream_t; NULL = legacy default */
+
+typedef enum {
+  BST_OK = 0,
+  BST_E_ARG = 1,          /* bad argument (null pointer, out-of-range index, ...) */
+  BST_E_SYMMETRY = 2,     /* flows/charges do not match on contracted legs */
+  BST_E_SHAPE = 3,        /* sizes/capacities inconsistent */
+  BST_E_OOM = 4,          /* device or host allocation failed */
+  BST_E_CUDA = 5,         /* CUDA runtime/library error */
+  BST_E_TIMEOUT = 6,      /* a bounded device wait expired */
+  BST_E_NUMERIC = 7,      /* non-finite value or failed decomposition */
+  BST_E_UNSUPPORTED = 8   /* valid request the library does not implement */
+} bst_status;
+
+typedef enum { BST_U1 = 1 } bst_group;
+
+/* Arithmetic of the block GEMMs.
+ *   BST_FP64:  plain FP64 (DMMA) grouped GEMM;
+ *   BST_OZAKI: FP64 operands split into integer-valued BF16 slices with a
+ *              shared power-of-two scale per row; slice products run on the
+ *              tcgen05 tensor cores with FP32 accumulation in tensor memory,
+ *              exact over short K chunks, and are recombined with FP64
+ *              weights in the epilogue.  ~44 significant bits. */
+typedef enum { BST_FP64 = 0, BST_OZAKI = 1 } bst_prec;
+
+typedef struct {
+  int32_t flow;           /* +1 incoming, -1 outgoing */
+  int32_t nsect;          /* number of sectors (>0) */
+  const int32_t* charge;  /* nsect charges, strictly ascending */
+  const int64_t* deg;     /* nsect reduced degeneracies, each > 0 */
+} bst_leg;
+
+typedef struct bst_ctx_s* bst_ctx;
+typedef struct bst_layout_s* bst_layout;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `workspace_bytes` is the initial
+ * size of the device workspace used for intermediates (0: grow on demand at
+ * plan time; once a plan is cached its calls allocate nothing). */
+BST_API bst_status bst_ctx_create(int device, size_t workspace_bytes, bst_ctx* out);
+BST_API bst_status bst_ctx_destroy(bst_ctx ctx);
+/* Thread-local message of the last failed call on this thread ("" if none). */
+BST_API const char* bst_last_error(void);
+/* Synchronise `stream`, then read and clear the device error word.
+ * Returns BST_E_TIMEOUT / BST_E_NUMERIC if a kernel recorded one. */
+BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
+/* Number of kernels this context launched so far (all calls). */
+BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
+
+/* ---- layouts -------------------------------------------------------------- */
+
+/* Canonical block layout of a tensor with the given legs (Sec. 2, Eq.
+ * "tensor-blocks").  BST_E_ARG for rank < 1 or > 8, unsorted charges or
+ * non-positive degeneracies. */
+BST_API bst_status bst_layout_create(bst_ctx ctx, bst_group group, int32_t rank,
+                             const bst_leg* legs, bst_layout* out);
+BST_API bst_status bst_layout_retain(bst_layout l);
+BST_API bst_status bst_layout_release(bst_layout l);
+/* rank, number of blocks and number of stored elements. */
+BST_API bst_status bst_layout_info(bst_layout l, int32_t* rank, int64_t* nblocks, int64_t* nnz);
+/* Leg i: flow and sector count; if `charges`/`degs` are non-NULL they
+ * receive nsect entries each. */
+BST_API bst_status bst_layout_leg(bst_layout l, int32_t i, int32_t* flow, int32_t* nsect,
+                          int32_t* charges, int64_t* degs);
+/* Block i in canonical order: per-leg sector indices (rank entries),
+ * element offset into the data array, per-leg extents (rank entries). */
+BST_API bst_status bst_layout_block(bst_layout l, int64_t i, int32_t* sector_idx,
+                            int64_t* offset, int64_t* shape);
+/* The dual layout: every flow reversed, same blocks, same storage order
+ * (the conjugate tensor of Sec. 3.2's double layer A*). */
+BST_API bst_status bst_layout_dual(bst_layout l, bst_layout* out);
+
+/* ---- tensor operations ----------------------------------------------------- */
+
+/* dst = src with legs permuted: dst leg j is src leg perm[j].  Returns the
+ * canonical layout of the permuted legs in *dst (new reference) and writes
+ * nnz(src) doubles to dst_data (must not alias src_data). */
+BST_API bst_status bst_permute(bst_ctx ctx, bst_layout src, const double* src_data,
+                       const int32_t* perm, bst_layout* dst, double* dst_data,
+                       bst_stream stream);
+
+/* Merge consecutive legs (Sec. 3.2: merging legs).  group_sizes[g] legs of
+ * src (in order) become output leg g; sum(group_sizes) == rank(src).  The
+ * fused leg takes the flow of its first member; its charge is
+ * flow_0 * sum_i flow_i q_i; its sectors ascend in charge; inside a sector
+ * the member-sector tuples ascend lexicographically and the inner index of
+ * a tuple is row-major over the member legs.  Writes nnz(src) doubles. */
+BST_API bst_status bst_fuse(bst_ctx ctx, bst_layout src, const double* src_data,
+                    int32_t ngroups, const int32_t* group_sizes,
+                    bst_layout* dst, double* dst_data, bst_stream stream);
+
+/* Output layout of contracting legsA[i] of A with legsB[i] of B (Sec. 2,
+ * contraction of block pairs with equal charges on the contracted legs).
+ * Output legs: A's open legs in order, then B's open legs.  Contracted
+ * legs must have opposite flows and identical sector lists
+ * (BST_E_SYMMETRY otherwise). */
+BST_API bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs,
+                               const int32_t* legsA, const int32_t* legsB,
+                               bst_layout* C);
+
+/* c = alpha * contract(a, b) + beta * c, with C the layout from
+ * bst_contract_layout.  Matched block pairs are grouped by the conserved
+ * charge through the cut, so every group is one dense GEMM whose result is
+ * already reduced (Sec. 2, grouping by output quantum numbers so the
+ * unreduced result never exists).  `prec` selects the GEMM arithmetic.
+ * beta == 0 ignores the previous contents of c (NaN-safe). */
+BST_API bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a,
+                        bst_layout B, const double* b,
+                        int32_t npairs, const int32_t* legsA, const int32_t* legsB,
+                        bst_prec prec, double alpha, double beta,
+                        bst_layout C, double* c, bst_stream stream);
+
+/* Double layer of a site tensor A[p,l,u,r,d] (Sec. 3.2): a = sum_p A (x) A*,
+ * ket and bra legs fused pairwise into rank-4 legs [l,u,r,d] (fused charge
+ * q_ket - q_bra).  If R is non-NULL it is a remover R[r,l',s] (Sec. 3.1,
+ * incoming r, outgoing l' and s); its double layer is absorbed on the right
+ * leg so that the result's right leg carries l''s structure.
+ * First call with a == NULL to get the output layout in *a_layout (new
+ * reference); then call again with the same inputs, *a_layout set and a
+ * device buffer a of nnz(*a_layout) doubles. */
+BST_API bst_status bst_double_layer(bst_ctx ctx, bst_layout A, const double* A_data,
+                            bst_layout R, const double* R_data,
+                            bst_layout* a_layout, double* a, bst_stream stream);
+
+/* SVD projectors of a CTMRG move (Sec. 3: the truncation the paper takes
+ * from corboz14).  Rtop[alpha, beta] and Rbot[alpha', beta'] are the two
+ * half systems; their first `ncut` legs are the left cut (alpha, alpha')
+ * and the remaining legs the right cut (beta, beta').  With
+ * N = Rtop^T Rbot (over the left cut) = U S V^T per conserved-charge sector,
+ * the chi largest singular values over all sectors are kept (ties: smaller
+ * |q| then smaller q, where q is the charge of the new leg; values below
+ * rel_cutoff * sigma_max dropped), and
+ *     P  = Rbot V S^-1/2    legs [alpha'..., new]   (new leg flow new_flow)
+ *     Pt = S^-1/2 U^T Rtop^T legs [new^dual, alpha...]
+ * with the sign of every kept left singular vector fixed by making its
+ * largest-magnitude entry positive (lowest index on ties).  The new leg
+ * lists sectors by ascending charge, singular values descending inside a
+ * sector.  p and pt are device buffers of at least dim(alpha')*chi and
+ * chi*dim(alpha) doubles; svals (HOST, chi doubles) receives the kept
+ * singular values in new-leg order; *kept their count.  This call
+ * synchronises the stream once (the global truncation is a host decision). */
+BST_API bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double* rtop,
+                             bst_layout Rbot, const double* rbot, int32_t ncut,
+                             int64_t chi, double rel_cutoff, int32_t new_flow,
+                             bst_prec prec,
+                             bst_layout* P, double* p, bst_layout* Pt, double* pt,
+                             double* svals, int64_t* kept, bst_stream stream);
+
+/* One-site CTMRG environment: corners C1..C4 and edges T1..T4 (index 0..3).
+ * Legs: C1[R,D] C2[L,D] C3[U,L] C4[U,R]  T1[L,D,R] T2[U,L,D] T3[L,U,R]
+ * T4[U,R,D]; the site tensor is a[L,U,R,D].  c[i], t[i] are device buffers
+ * with capacities c_cap[i], t_cap[i] (doubles); a move rewrites the buffers
+ * of the tensors it renews in place and replaces their layouts (releasing
+ * the old references). */
+typedef struct {
+  bst_layout C[4], T[4];
+  double* c[4];
+  double* t[4];
+  int64_t c_cap[4], t_cap[4];
+} bst_env;
+
+typedef struct {
+  int64_t kept[4];        /* kept states per directional move (L,R,U,D order of execution) */
+  double smin_over_smax[4];
+  double trunc_weight[4]; /* sum of discarded sigma / sum of all sigma */
+} bst_ctm_stats;
+
+/* CTMRG move on a one-site cell (Sec. 3 and Sec. 3.2): dir 0 = LEFT (renews
+ * C1, T4, C4), 1 = UP (C1, T1, C2), 2 = RIGHT (C2, T2, C3), 3 = DOWN
+ * (C3, T3, C4), 4 = the full move LEFT, RIGHT, UP, DOWN in sequence, each
+ * on the updated environment.  Every directional move computes the four
+ * enlarged corners, the half systems, the projectors (as
+ * bst_svd_projector with rel_cutoff) and renormalises and normalises the
+ * renewed tensors (Frobenius norm 1).  stats may be NULL. */
+BST_API bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a,
+                        bst_env* env, int64_t chi, double rel_cutoff, bst_prec prec,
+                        bst_ctm_stats* stats, bst_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BST_H */

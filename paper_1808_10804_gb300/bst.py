@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/bst.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libbst.so`` built in-tree (see ``build.py``).  Device buffers are
+float64 CUDA tensors from PyTorch (used for memory and streams only); the
+library fails loudly if it is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbst.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bst.h")
+
+FP64, OZAKI = 0, 1
+PREC = {"fp64": FP64, "ozaki": OZAKI, FP64: FP64, OZAKI: OZAKI}
+LEFT, UP, RIGHT, DOWN, ALL = 0, 1, 2, 3, 4
+ROLES = ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4")
+
+_lib = None
+
+
+class BstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bst error {code}: {msg}")
+        self.code = code
+
+
+class _Leg(C.Structure):
+    _fields_ = [("flow", C.c_int32), ("nsect", C.c_int32),
+                ("charge", C.POINTER(C.c_int32)), ("deg", C.POINTER(C.c_int64))]
+
+
+class _Env(C.Structure):
+    _fields_ = [("C", C.c_void_p * 4), ("T", C.c_void_p * 4),
+                ("c", C.c_void_p * 4), ("t", C.c_void_p * 4),
+                ("c_cap", C.c_int64 * 4), ("t_cap", C.c_int64 * 4)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("kept", C.c_int64 * 4), ("smin_over_smax", C.c_double * 4),
+                ("trunc_weight", C.c_double * 4)]
+
+
+def exported_names():
+    """Function names declared in include/bst.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"\b(bst_[a-z_0-9]+)\s*\(", txt)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1808_10804_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "bst_ctx_create": [C.c_int, C.c_size_t, P(vp)],
+        "bst_ctx_destroy": [vp],
+        "bst_ctx_sync": [vp, vp],
+        "bst_ctx_launch_count": [vp],
+        "bst_layout_create": [vp, C.c_int, i32, P(_Leg), P(vp)],
+        "bst_layout_retain": [vp],
+        "bst_layout_release": [vp],
+        "bst_layout_info": [vp, P(i32), P(i64), P(i64)],
+        "bst_layout_leg": [vp, i32, P(i32), P(i32), P(i32), P(i64)],
+        "bst_layout_block": [vp, i64, P(i32), P(i64), P(i64)],
+        "bst_layout_dual": [vp, P(vp)],
+        "bst_permute": [vp, vp, vp, P(i32), P(vp), vp, vp],
+        "bst_fuse": [vp, vp, vp, i32, P(i32), P(vp), vp, vp],
+        "bst_contract_layout": [vp, vp, vp, i32, P(i32), P(i32), P(vp)],
+        "bst_contract": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), C.c_int, dbl, dbl, vp, vp, vp],
+        "bst_double_layer": [vp, vp, vp, vp, vp, P(vp), vp, vp],
+        "bst_svd_projector": [vp, vp, vp, vp, vp, i32, i64, dbl, i32, C.c_int, P(vp), vp, P(vp), vp,
+                              P(dbl), P(i64), vp],
+        "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.bst_ctx_launch_count.restype = C.c_int64
+    L.bst_last_error.restype = C.c_char_p
+    L.bst_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != 0:
+        raise BstError(st, lib().bst_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+def _i32(xs):
+    xs = list(xs)
+    return (C.c_int32 * max(1, len(xs)))(*xs)
+
+
+@dataclass(frozen=True)
+class Leg:
+    flow: int
+    charges: tuple
+    degs: tuple
+
+    @property
+    def dim(self):
+        return sum(self.degs)
+
+    def dual(self):
+        return Leg(-self.flow, self.charges, self.degs)
+
+
+class Layout:
+    """A reference to an interned, immutable block layout."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle
+        r, nb, nz = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().bst_layout_info(self.h, C.byref(r), C.byref(nb), C.byref(nz)))
+        self.rank, self.nblocks, self.nnz = r.value, nb.value, nz.value
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib().bst_layout_release(self.h)
+        except Exception:
+            pass
+
+    def __eq__(self, other):
+        return isinstance(other, Layout) and self.h.value == other.h.value
+
+    def __hash__(self):
+        return hash(self.h.value)
+
+    @property
+    def legs(self):
+        out = []
+        for i in range(self.rank):
+            f, n = C.c_int32(), C.c_int32()
+            _check(lib().bst_layout_leg(self.h, i, C.byref(f), C.byref(n), None, None))
+            q = (C.c_int32 * n.value)()
+            d = (C.c_int64 * n.value)()
+            _check(lib().bst_layout_leg(self.h, i, None, None, q, d))
+            out.append(Leg(f.value, tuple(q), tuple(d)))
+        return out
+
+    def blocks(self):
+        out = []
+        s = (C.c_int32 * self.rank)()
+        sh = (C.c_int64 * self.rank)()
+        off = C.c_int64()
+        for b in range(self.nblocks):
+            _check(lib().bst_layout_block(self.h, b, s, C.byref(off), sh))
+            out.append((tuple(s), off.value, tuple(sh)))
+        return out
+
+    def dual(self):
+        h = C.c_void_p()
+        _check(lib().bst_layout_dual(self.h, C.byref(h)))
+        return Layout(self.ctx, h)
+
+    def empty(self, device=None):
+        return torch.empty(max(self.nnz, 0), dtype=torch.float64,
+                           device=device or f"cuda:{self.ctx.device}")
+
+
+class Context:
+    def __init__(self, device=0, workspace_bytes=0):
+        self.device = device
+        h = C.c_void_p()
+        _check(lib().bst_ctx_create(device, workspace_bytes, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _check(lib().bst_ctx_destroy(self.h))
+            self.h = None
+
+    def sync(self, stream=None):
+        _check(lib().bst_ctx_sync(self.h, _stream(stream)))
+
+    @property
+    def launches(self):
+        return lib().bst_ctx_launch_count(self.h)
+
+    def layout(self, legs):
+        legs = [l if isinstance(l, Leg) else Leg(int(l["flow"]), tuple(l["charges"]), tuple(l["degs"]))
+                for l in legs]
+        arr = (_Leg * len(legs))()
+        keep = []
+        for i, l in enumerate(legs):
+            q = (C.c_int32 * len(l.charges))(*l.charges)
+            d = (C.c_int64 * len(l.degs))(*l.degs)
+            keep += [q, d]
+            arr[i] = _Leg(l.flow, len(l.charges), q, d)
+        h = C.c_void_p()
+        _check(lib().bst_layout_create(self.h, 1, len(legs), arr, C.byref(h)))
+        return Layout(self, h)
+
+    # ---- operations ------------------------------------------------------------
+    def permute(self, L, x, perm, stream=None):
+        h = C.c_void_p()
+        # the output layout is known before the launch; allocate afterwards is
+        # not possible, so size by nnz of the source (a permutation keeps nnz)
+        out = torch.empty(L.nnz, dtype=torch.float64, device=x.device)
+        _check(lib().bst_permute(self.h, L.h, _ptr(x), _i32(perm), C.byref(h), _ptr(out), _stream(stream)))
+        return Layout(self, h), out
+
+    def fuse(self, L, x, groups, stream=None):
+        h = C.c_void_p()
+        out = torch.empty(L.nnz, dtype=torch.float64, device=x.device)
+        _check(lib().bst_fuse(self.h, L.h, _ptr(x), len(groups), _i32(groups), C.byref(h), _ptr(out),
+                              _stream(stream)))
+        return Layout(self, h), out
+
+    def contract_layout(self, A, B, legsA, legsB):
+        h = C.c_void_p()
+        _check(lib().bst_contract_layout(self.h, A.h, B.h, len(legsA), _i32(legsA), _i32(legsB), C.byref(h)))
+        return Layout(self, h)
+
+    def contract(self, A, a, B, b, legsA, legsB, prec="fp64", alpha=1.0, beta=0.0, Cl=None, c=None,
+                 stream=None):
+        if Cl is None:
+            Cl = self.contract_layout(A, B, legsA, legsB)
+        if c is None:
+            c = torch.empty(Cl.nnz, dtype=torch.float64, device=a.device)
+        _check(lib().bst_contract(self.h, A.h, _ptr(a), B.h, _ptr(b), len(legsA), _i32(legsA), _i32(legsB),
+                                  PREC[prec], alpha, beta, Cl.h, _ptr(c), _stream(stream)))
+        return Cl, c
+
+    def double_layer(self, A, a, R=None, r=None, stream=None):
+        h = C.c_void_p()
+        _check(lib().bst_double_layer(self.h, A.h, _ptr(a), R.h if R else None, _ptr(r) if R else None,
+                                      C.byref(h), None, _stream(stream)))
+        L = Layout(self, h)
+        out = torch.empty(L.nnz, dtype=torch.float64, device=a.device)
+        _check(lib().bst_double_layer(self.h, A.h, _ptr(a), R.h if R else None, _ptr(r) if R else None,
+                                      C.byref(h), _ptr(out), _stream(stream)))
+        return L, out
+
+    def svd_projector(self, Rt, rt, Rb, rb, ncut, chi, rel_cutoff=1e-14, new_flow=-1, prec="fp64",
+                      stream=None):
+        na = 1
+        for l in Rt.legs[:ncut]:
+            na *= l.dim
+        nap = 1
+        for l in Rb.legs[:ncut]:
+            nap *= l.dim
+        p = torch.empty(nap * chi, dtype=torch.float64, device=rt.device)
+        pt = torch.empty(na * chi, dtype=torch.float64, device=rt.device)
+        sv = (C.c_double * chi)()
+        kept = C.c_int64()
+        hp, hpt = C.c_void_p(), C.c_void_p()
+        _check(lib().bst_svd_projector(self.h, Rt.h, _ptr(rt), Rb.h, _ptr(rb), ncut, chi, rel_cutoff, new_flow,
+                                       PREC[prec], C.byref(hp), _ptr(p), C.byref(hpt), _ptr(pt), sv,
+                                       C.byref(kept), _stream(stream)))
+        P, Pt = Layout(self, hp), Layout(self, hpt)
+        return P, p[:P.nnz], Pt, pt[:Pt.nnz], list(sv)[:kept.value], kept.value
+
+    def ctm_move(self, env, a_layout, a, direction, chi, rel_cutoff=1e-14, prec="fp64", stream=None):
+        """env: Env; renewed tensors are rewritten in place."""
+        e = env.to_c()
+        st = _Stats()
+        _check(lib().bst_ctm_move(self.h, direction, a_layout.h, _ptr(a), C.byref(e), chi, rel_cutoff,
+                                  PREC[prec], C.byref(st), _stream(stream)))
+        env.from_c(e)
+        return {"kept": list(st.kept), "smin_over_smax": list(st.smin_over_smax),
+                "trunc_weight": list(st.trunc_weight)}
+
+
+class Env:
+    """CTMRG environment: layouts and device buffers with capacities."""
+
+    def __init__(self, ctx, layouts, data, caps=None):
+        self.ctx = ctx
+        self.L = dict(layouts)
+        self.buf = {}
+        for r in ROLES:
+            cap = (caps or {}).get(r, self.L[r].nnz)
+            b = torch.zeros(max(cap, 1), dtype=torch.float64, device=f"cuda:{ctx.device}")
+            b[:self.L[r].nnz].copy_(data[r])
+            self.buf[r] = b
+
+    def data(self, r):
+        return self.buf[r][:self.L[r].nnz]
+
+    def to_c(self):
+        e = _Env()
+        for i in range(4):
+            for kind, arr, carr, cap in (("C", e.C, e.c, e.c_cap), ("T", e.T, e.t, e.t_cap)):
+                r = f"{kind}{i + 1}"
+                lib().bst_layout_retain(self.L[r].h)
+                arr[i] = self.L[r].h.value
+                carr[i] = self.buf[r].data_ptr()
+                cap[i] = self.buf[r].numel()
+        return e
+
+    def from_c(self, e):
+        for i in range(4):
+            for kind, arr in (("C", e.C), ("T", e.T)):
+                r = f"{kind}{i + 1}"
+                # the library released our extra reference on replaced layouts
+                # and handed back new ones; wrap them (ownership moves here)
+                self.L[r] = Layout(self.ctx, C.c_void_p(arr[i]))

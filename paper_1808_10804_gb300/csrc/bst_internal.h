@@ -1,0 +1,242 @@
+// Internal declarations of the block-sparse symmetric tensor library.
+// Nothing here crosses the C ABI (include/bst.h): C++ types, exceptions and
+// containers stay inside the shared library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bst.h"
+
+namespace bst {
+
+constexpr int kMaxRank = 8;
+
+// Internal error: converted to a bst_status at the ABI boundary.
+struct Error : std::runtime_error {
+  bst_status code;
+  Error(bst_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define BST_REQUIRE(cond, code, msg)                                   \
+  do {                                                                 \
+    if (!(cond)) throw ::bst::Error((code), (msg));                    \
+  } while (0)
+
+#define BST_CUDA(call)                                                           \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      throw ::bst::Error(BST_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// One leg: flow and sectors (Sec. 2).  `off` are sector offsets in the dense
+// index of the leg.
+struct Leg {
+  int flow = 1;
+  std::vector<int> q;
+  std::vector<int64_t> d;
+  std::vector<int64_t> off;
+  int64_t dim = 0;
+  void finish();
+  bool same_space(const Leg& o) const { return q == o.q && d == o.d; }
+  bool operator==(const Leg& o) const { return flow == o.flow && same_space(o); }
+  Leg dual() const { Leg l = *this; l.flow = -flow; return l; }
+  int find(int charge) const;  // sector index of a charge or -1
+};
+
+// Canonical block layout (immutable, interned per context).
+struct Layout {
+  std::atomic<int> refs{1};
+  struct Ctx* ctx = nullptr;
+  uint64_t id = 0;
+  int group = BST_U1;
+  int rank = 0;
+  std::vector<Leg> legs;
+  int64_t nblocks = 0, nnz = 0;
+  std::vector<int32_t> sect;    // nblocks * rank sector indices
+  std::vector<int64_t> offset;  // nblocks element offsets
+  std::vector<int64_t> shape;   // nblocks * rank extents
+  std::unordered_map<uint64_t, int64_t> index;  // packed sector tuple -> block
+  std::string key;              // structural key used for interning
+
+  int64_t block_of(const int32_t* s) const;
+  static uint64_t pack(const int32_t* s, int r) {
+    uint64_t k = 0;
+    for (int i = 0; i < r; ++i) k = (k << 8) | uint64_t(uint8_t(s[i]));
+    return k;
+  }
+};
+
+// Element-wise relayout between a contiguous block (row-major over `shape`)
+// and a strided region of another buffer.
+struct RelTask {
+  int64_t blk_off;     // element offset of the contiguous side
+  int64_t mat_base;    // element offset of the strided side
+  int32_t rank;
+  int32_t n;           // number of elements
+  int32_t shape[kMaxRank];
+  int64_t mstride[kMaxRank];
+};
+
+// Sector-matrix view of a block tensor w.r.t. (row legs, col legs): one dense
+// row-major matrix per conserved charge through the cut (key = sum over the
+// col legs of flow*q).
+struct MatSector {
+  int64_t key = 0;
+  int64_t rows = 0, cols = 0;
+  int64_t off = 0;  // element offset in the matrix buffer
+  std::vector<std::vector<int32_t>> rcfg, ccfg;  // sector tuples
+  std::vector<int64_t> roff, coff;                // offsets of each config
+  std::map<std::vector<int32_t>, int64_t> rmap, cmap;
+};
+
+struct MatView {
+  std::vector<int> rowlegs, collegs;
+  std::vector<MatSector> secs;
+  std::map<int64_t, int> by_key;
+  int64_t total = 0;
+  std::vector<RelTask> tasks;  // one per tensor block with nonzero size
+  const MatSector* find(int64_t key) const {
+    auto it = by_key.find(key);
+    return it == by_key.end() ? nullptr : &secs[it->second];
+  }
+};
+
+// A relayout ready to launch: tasks and chunk table on the device.
+struct DevRelayout {
+  RelTask* tasks = nullptr;
+  int2* chunks = nullptr;
+  int nchunks = 0;
+  int ntasks = 0;
+  void upload(const std::vector<RelTask>& t);
+  void free_all();
+};
+
+// One GEMM of a grouped launch: C[m,n] = sum_k A[m,k] B[n,k] with generic
+// element strides (a_m, a_k), (b_n, b_k), (c_m, c_n).
+struct GemmProb {
+  int32_t M, N, K, pad;
+  int64_t a_off, b_off, c_off;
+  int64_t a_m, a_k, b_n, b_k, c_m, c_n;
+};
+
+struct DevGemm {
+  GemmProb* probs = nullptr;
+  int32_t* tile_prob = nullptr;   // tile -> problem
+  int32_t* tile_idx = nullptr;    // tile -> linear tile index inside its problem
+  int ntiles = 0, nprobs = 0;
+  void upload(const std::vector<GemmProb>& p, int tm, int tn);
+  void free_all();
+};
+
+struct OzakiPlan;  // mixed-precision GEMM plan (gemm_ozaki.cu)
+
+// Contraction plan (cached per (A, B, pairs)).
+struct ContractPlan {
+  Layout *A = nullptr, *B = nullptr, *C = nullptr;
+  MatView va, vb, vc;
+  DevRelayout ra, rb, rc;      // A->Amat, B->Bmat, Cmat->C
+  std::vector<GemmProb> probs; // per matched sector
+  DevGemm g;
+  OzakiPlan* oz = nullptr;
+  int64_t amat = 0, bmat = 0, cmat = 0;  // matrix buffer sizes (elements)
+  ~ContractPlan();
+};
+
+// Device buffer that only grows (the caller synchronises before growth).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void* get(size_t need, cudaStream_t s);
+  void free_all();
+};
+
+struct Ctx {
+  int device = 0;
+  std::mutex mu;
+  uint64_t next_id = 1;
+  std::map<std::string, Layout*> interned;  // structural key -> layout (one ref held)
+  std::map<std::string, std::unique_ptr<ContractPlan>> cplans;
+  std::map<std::string, std::unique_ptr<DevRelayout>> rplans;
+  std::map<std::string, DevBuf> bufs;
+  std::map<std::string, std::unique_ptr<DevGemm>> gplans;
+  int* d_err = nullptr;                     // device error word
+  std::atomic<int64_t> launches{0};
+  void* cusolver = nullptr;
+  double* d_scratch_small = nullptr;
+  ~Ctx();
+  void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
+};
+
+// layout.cpp
+Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs);  // new reference
+void retain(Layout* l);
+void release(Layout* l);
+Leg fuse_legs(const std::vector<Leg>& legs, std::vector<std::vector<int32_t>>* tuples_per_sector = nullptr);
+std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& legs, int64_t target);
+
+// plan.cpp
+MatView make_matview(const Layout* L, const std::vector<int>& rowlegs, const std::vector<int>& collegs,
+                     bool build_tasks = true);
+ContractPlan* get_contract_plan(Ctx* ctx, Layout* A, Layout* B, const std::vector<int>& la,
+                                const std::vector<int>& lb);
+DevRelayout* get_permute_plan(Ctx* ctx, Layout* src, const std::vector<int>& perm, Layout** dst);
+DevRelayout* get_fuse_plan(Ctx* ctx, Layout* src, const std::vector<int>& groups, Layout** dst);
+void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, bst_prec prec,
+                  double alpha, double beta, double* c, cudaStream_t s, bool scatter = true,
+                  double** cmat_out = nullptr);
+
+// relayout.cu
+void launch_relayout(Ctx* ctx, const DevRelayout& r, const double* blk, double* mat, int dir,
+                     double alpha, double beta, cudaStream_t s);
+
+// gemm_f64.cu
+DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmProb>& probs);
+void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* B, double* C,
+                     cudaStream_t s);
+extern const int kF64TileM, kF64TileN;
+
+// gemm_ozaki.cu
+void ozaki_prepare(Ctx* ctx, ContractPlan* p);
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
+                    cudaStream_t s);
+void ozaki_free(OzakiPlan* oz);
+// generic Ozaki GEMM over a problem list (used by the projector)
+void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs,
+                          const double* A, const double* B, double* C, cudaStream_t s);
+
+// projector.cu
+struct ProjResult {
+  Layout* P = nullptr;
+  Layout* Pt = nullptr;
+  Leg newleg;
+  std::vector<double> svals;
+  int64_t kept = 0;
+  double smin_over_smax = 0, trunc_weight = 0;
+};
+ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
+                         int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
+                         cudaStream_t s);
+
+// ctm.cpp
+void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,
+              bst_prec prec, bst_ctm_stats* stats, cudaStream_t s);
+
+// misc kernels (relayout.cu)
+void launch_scale(Ctx* ctx, double* x, int64_t n, const double* dev_scalar_inv, cudaStream_t s);
+void launch_sumsq(Ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStream_t s);
+void launch_fill(Ctx* ctx, double* x, int64_t n, double v, cudaStream_t s);
+
+inline void count_launch(Ctx* ctx, int n = 1) { ctx->launches += n; }
+
+}  // namespace bst

@@ -1,0 +1,220 @@
+// Directional CTMRG moves on a one-site cell (Sec. 3 and Sec. 3.2).
+//
+// A LEFT move absorbs the site column into the left environment column:
+//   Q1 = C1 T1 T4 a, Q2 = T1 C2 a T2, Q3 = a T2 T3 C3, Q4 = T4 a C4 T3
+//   Rt = Q1 Q2 (top half), Rb = Q4 Q3 (bottom half)
+//   projectors P, Pt from the SVD of Rt^T Rb (svd_projector)
+//   C1' = (C1 T1) P,  T4' = (Pt T4 a) P,  C4' = Pt (C4 T3),  each normalised.
+// Other directions rotate the network by quarter turns (a leg permutation of
+// every tensor), run the LEFT move and rotate the renewed tensors back.
+//
+// Leg directions of the roles: C1[R,D] C2[L,D] C3[U,L] C4[U,R]
+// T1[L,D,R] T2[U,L,D] T3[L,U,R] T4[U,R,D], a[L,U,R,D].
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "bst_internal.h"
+
+namespace bst {
+
+namespace {
+
+enum Role { C1 = 0, C2, C3, C4, T1, T2, T3, T4, SITE, NROLE };
+const char* kDirs[NROLE] = {"RD", "LD", "UL", "UR", "LDR", "ULD", "LUR", "URD", "LURD"};
+// one counter-clockwise quarter turn: the tensor at role r moves to kRot[r]
+const Role kRot[NROLE] = {C4, C1, C2, C3, T4, T1, T2, T3, SITE};
+
+char rot_dir(char d) {  // direction a leg points to after the turn
+  switch (d) {
+    case 'U': return 'L';
+    case 'L': return 'D';
+    case 'D': return 'R';
+    default: return 'U';  // 'R'
+  }
+}
+
+struct Src {
+  int role;               // role in the original frame
+  std::vector<int> perm;  // rotated leg j = original leg perm[j]
+};
+
+// For k quarter turns: where every rotated role comes from.
+std::vector<Src> rotation(int k) {
+  std::vector<Src> cur(NROLE);
+  for (int r = 0; r < NROLE; ++r) {
+    cur[r].role = r;
+    cur[r].perm.resize(strlen(kDirs[r]));
+    std::iota(cur[r].perm.begin(), cur[r].perm.end(), 0);
+  }
+  for (int t = 0; t < k; ++t) {
+    std::vector<Src> nxt(NROLE);
+    for (int o = 0; o < NROLE; ++o) {
+      const int n = kRot[o];
+      const char* od = kDirs[o];
+      const char* nd = kDirs[n];
+      const int r = int(strlen(nd));
+      nxt[n].role = cur[o].role;
+      nxt[n].perm.resize(r);
+      for (int j = 0; j < r; ++j) {
+        int src = -1;
+        for (int i = 0; i < r; ++i)
+          if (rot_dir(od[i]) == nd[j]) src = i;
+        nxt[n].perm[j] = cur[o].perm[src];
+      }
+    }
+    cur = nxt;
+  }
+  return cur;
+}
+
+inline Layout* L_(bst_layout x) { return reinterpret_cast<Layout*>(x); }
+
+bool is_identity(const std::vector<int>& p) {
+  for (size_t i = 0; i < p.size(); ++i)
+    if (p[i] != int(i)) return false;
+  return true;
+}
+
+struct T {
+  Layout* L;
+  const double* d;
+};
+
+// c = a.legs(la) * b.legs(lb); result in a named context buffer
+T contract(Ctx* ctx, const char* name, T a, T b, std::vector<int> la, std::vector<int> lb, bst_prec prec,
+           cudaStream_t s) {
+  ContractPlan* p = get_contract_plan(ctx, a.L, b.L, la, lb);
+  double* out = (double*)ctx->buf(name, sizeof(double) * std::max<int64_t>(p->C->nnz, 1), s);
+  run_contract(ctx, p, a.d, b.d, prec, 1.0, 0.0, out, s);
+  return {p->C, out};
+}
+
+void normalise(Ctx* ctx, double* x, int64_t n, cudaStream_t s) {
+  double* ss = (double*)ctx->buf("ctm.sumsq", sizeof(double), s);
+  launch_sumsq(ctx, x, n, ss, s);
+  launch_scale(ctx, x, n, ss, s);
+}
+
+}  // namespace
+
+static void left_move(Ctx* ctx, T* r, int64_t chi, double cutoff, bst_prec prec, T out[3], ProjResult* pres,
+                      cudaStream_t s) {
+  T a = r[SITE];
+  T X1 = contract(ctx, "ctm.X1", r[C1], r[T1], {0}, {0}, prec, s);        // [C1.D, T1.D, T1.R]
+  T X2 = contract(ctx, "ctm.X2", X1, r[T4], {0}, {0}, prec, s);           // [T1.D, T1.R, T4.R, T4.D]
+  T Q1 = contract(ctx, "ctm.Q1", X2, a, {0, 2}, {1, 0}, prec, s);         // [T1.R, T4.D, a.R, a.D]
+  T Y1 = contract(ctx, "ctm.Y1", r[T1], r[C2], {2}, {0}, prec, s);        // [T1.L, T1.D, C2.D]
+  T Y2 = contract(ctx, "ctm.Y2", Y1, r[T2], {2}, {0}, prec, s);           // [T1.L, T1.D, T2.L, T2.D]
+  T Q2 = contract(ctx, "ctm.Q2", Y2, a, {1, 2}, {1, 2}, prec, s);         // [T1.L, T2.D, a.L, a.D]
+  T Rt = contract(ctx, "ctm.Rt", Q1, Q2, {0, 2}, {0, 2}, prec, s);        // [T4.D, a.D | T2.D, a.D]
+  T Z1 = contract(ctx, "ctm.Z1", r[T4], r[C4], {2}, {0}, prec, s);        // [T4.U, T4.R, C4.R]
+  T Z2 = contract(ctx, "ctm.Z2", Z1, r[T3], {2}, {0}, prec, s);           // [T4.U, T4.R, T3.U, T3.R]
+  T Q4 = contract(ctx, "ctm.Q4", Z2, a, {1, 2}, {0, 3}, prec, s);         // [T4.U, T3.R, a.U, a.R]
+  T W1 = contract(ctx, "ctm.W1", r[T2], r[C3], {2}, {0}, prec, s);        // [T2.U, T2.L, C3.L]
+  T W2 = contract(ctx, "ctm.W2", W1, r[T3], {2}, {2}, prec, s);           // [T2.U, T2.L, T3.L, T3.U]
+  T Q3 = contract(ctx, "ctm.Q3", W2, a, {1, 3}, {2, 3}, prec, s);         // [T2.U, T3.L, a.L, a.U]
+  T Rb = contract(ctx, "ctm.Rb", Q4, Q3, {1, 3}, {1, 2}, prec, s);        // [T4.U, a.U | T2.U, a.U]
+  const int new_flow = r[C1].L->legs[1].flow;
+  int64_t pcap = Rb.L->legs[0].dim * Rb.L->legs[1].dim * chi;
+  int64_t ptcap = Rt.L->legs[0].dim * Rt.L->legs[1].dim * chi;
+  double* P = (double*)ctx->buf("ctm.P", sizeof(double) * pcap, s);
+  double* Pt = (double*)ctx->buf("ctm.Pt", sizeof(double) * ptcap, s);
+  *pres = svd_projector(ctx, Rt.L, Rt.d, Rb.L, Rb.d, 2, chi, cutoff, new_flow, prec, P, Pt, s);
+  T tP{pres->P, P}, tPt{pres->Pt, Pt};
+  // renormalise: C1' = X1 P, T4' = ((Pt T4) a) P, C4' = Pt (C4 T3)
+  out[0] = contract(ctx, "ctm.C1n", X1, tP, {0, 1}, {0, 1}, prec, s);    // [T1.R, new]
+  T W = contract(ctx, "ctm.W", tPt, r[T4], {1}, {0}, prec, s);             // [new^, a.D, T4.R, T4.D]
+  T Z = contract(ctx, "ctm.Z", W, a, {2, 1}, {0, 1}, prec, s);             // [new^, T4.D, a.R, a.D]
+  out[1] = contract(ctx, "ctm.T4n", Z, tP, {1, 3}, {0, 1}, prec, s);     // [new^, a.R, new]
+  T Y = contract(ctx, "ctm.Y", r[C4], r[T3], {1}, {0}, prec, s);           // [C4.U, T3.U, T3.R]
+  out[2] = contract(ctx, "ctm.C4n", tPt, Y, {1, 2}, {0, 1}, prec, s);    // [new^, T3.R]
+  for (int i = 0; i < 3; ++i) normalise(ctx, const_cast<double*>(out[i].d), out[i].L->nnz, s);
+}
+
+void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double cutoff,
+              bst_prec prec, bst_ctm_stats* stats, cudaStream_t s) {
+  BST_REQUIRE(dir >= 0 && dir <= 4, BST_E_ARG, "dir must be 0..4");
+  BST_REQUIRE(a->rank == 4, BST_E_ARG, "site tensor must have rank 4");
+  for (int i = 0; i < 4; ++i) {
+    BST_REQUIRE(env->C[i] && env->T[i] && env->c[i] && env->t[i], BST_E_ARG, "env has a null entry");
+    BST_REQUIRE(L_(env->C[i])->rank == 2 && L_(env->T[i])->rank == 3, BST_E_ARG,
+                "env ranks must be 2 (C) and 3 (T)");
+  }
+  if (stats) memset(stats, 0, sizeof(*stats));
+  std::vector<int> seq;
+  if (dir == 4) seq = {0, 2, 1, 3};  // LEFT, RIGHT, UP, DOWN
+  else seq = {dir};
+  int step = 0;
+  for (int d : seq) {
+    // rotation index: LEFT 0, UP 1, RIGHT 2, DOWN 3 quarter turns
+    const int k = d;
+    std::vector<Src> rot = rotation(k);
+    T orig[NROLE];
+    for (int i = 0; i < 4; ++i) {
+      orig[C1 + i] = {L_(env->C[i]), env->c[i]};
+      orig[T1 + i] = {L_(env->T[i]), env->t[i]};
+    }
+    orig[SITE] = {a, ad};
+    T r[NROLE];
+    for (int n = 0; n < NROLE; ++n) {
+      const Src& src = rot[n];
+      if (is_identity(src.perm)) {
+        r[n] = orig[src.role];
+      } else {
+        Layout* dst = nullptr;
+        DevRelayout* rp = get_permute_plan(ctx, orig[src.role].L, src.perm, &dst);
+        std::string nm = "ctm.rot" + std::to_string(n);
+        double* buf = (double*)ctx->buf(nm, sizeof(double) * std::max<int64_t>(dst->nnz, 1), s);
+        launch_relayout(ctx, *rp, orig[src.role].d, buf, 0, 1.0, 0.0, s);
+        release(dst);  // the intern table keeps the layout alive
+        r[n] = {dst, buf};
+      }
+    }
+    T out[3];
+    ProjResult pr;
+    left_move(ctx, r, chi, cutoff, prec, out, &pr, s);
+    // map renewed rotated roles C1, T4, C4 back to the original frame
+    const int renewed[3] = {C1, T4, C4};
+    for (int i = 0; i < 3; ++i) {
+      const Src& src = rot[renewed[i]];
+      std::vector<int> inv(src.perm.size());
+      for (size_t j = 0; j < src.perm.size(); ++j) inv[src.perm[j]] = int(j);
+      Layout* nl = nullptr;
+      double* dst;
+      int64_t cap;
+      bst_layout* slot;
+      if (src.role < T1) {
+        dst = env->c[src.role - C1];
+        cap = env->c_cap[src.role - C1];
+        slot = &env->C[src.role - C1];
+      } else {
+        dst = env->t[src.role - T1];
+        cap = env->t_cap[src.role - T1];
+        slot = &env->T[src.role - T1];
+      }
+      if (is_identity(inv)) {
+        nl = out[i].L;
+        retain(nl);
+        BST_REQUIRE(nl->nnz <= cap, BST_E_SHAPE, "env buffer capacity too small for the renewed tensor");
+        BST_CUDA(cudaMemcpyAsync(dst, out[i].d, sizeof(double) * nl->nnz, cudaMemcpyDeviceToDevice, s));
+      } else {
+        DevRelayout* rp = get_permute_plan(ctx, out[i].L, inv, &nl);
+        BST_REQUIRE(nl->nnz <= cap, BST_E_SHAPE, "env buffer capacity too small for the renewed tensor");
+        launch_relayout(ctx, *rp, out[i].d, dst, 0, 1.0, 0.0, s);
+      }
+      release(L_(*slot));
+      *slot = reinterpret_cast<bst_layout>(nl);
+    }
+    if (stats && step < 4) {
+      stats->kept[step] = pr.kept;
+      stats->smin_over_smax[step] = pr.smin_over_smax;
+      stats->trunc_weight[step] = pr.trunc_weight;
+    }
+    release(pr.P);
+    release(pr.Pt);
+    ++step;
+  }
+}
+
+}  // namespace bst

@@ -1,0 +1,196 @@
+"""GPU parity: every call of the C ABI against the dense FP64 oracle on the
+same seeded inputs.  Block structure must match bit-exactly; values within
+1e-12 relative (Frobenius) for the FP64 path."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import ctm as octm  # noqa: E402
+from oracle import u1  # noqa: E402
+from workloads import u1_config, values  # noqa: E402
+from bst_helpers import gpu_network, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_10804_gb300 import build
+    build.build()
+    from paper_1808_10804_gb300 import bst as b
+    return b
+
+
+@pytest.fixture(scope="module")
+def ctx(bst):
+    c = bst.Context(0)
+    yield c
+    c.close()
+
+
+def rand_legs(rng, rank, maxdeg):
+    legs = []
+    for _ in range(rank):
+        qs = sorted(rng.choice(np.arange(-3, 4), size=int(rng.integers(1, 4)), replace=False))
+        legs.append(u1.Leg(int(rng.choice([1, -1])), tuple(int(q) for q in qs),
+                           tuple(int(d) for d in rng.integers(1, maxdeg + 1, size=len(qs)))))
+    return legs
+
+
+def dev(x):
+    return torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def upload(bst, ctx, legs, dense):
+    L = ctx.layout([to_bst_leg(bst, l) for l in legs])
+    return L, dev(u1.from_dense(legs, dense))
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("maxdeg", [3, 40])
+def test_contract_matches_oracle(bst, ctx, seed, maxdeg):
+    """Random layouts; large degeneracies make sector GEMMs span several 64x64
+    tiles with ragged edges."""
+    rng = np.random.default_rng(100 + seed)
+    shared = rand_legs(rng, 2 if maxdeg > 3 else 2, maxdeg)
+    ao = rand_legs(rng, 1 if maxdeg > 3 else 2, maxdeg)
+    bo = rand_legs(rng, 1 if maxdeg > 3 else 2, maxdeg)
+    a_legs = [ao[0], shared[0]] + ao[1:] + [shared[1]]
+    b_legs = [shared[1].dual()] + bo + [shared[0].dual()]
+    A = u1.to_dense(a_legs, rng.standard_normal(u1.nnz(a_legs)))
+    B = u1.to_dense(b_legs, rng.standard_normal(u1.nnz(b_legs)))
+    la = [1, len(a_legs) - 1]
+    lb = [len(b_legs) - 1, 0]
+    ref = np.tensordot(A, B, axes=(la, lb))
+    AL, ad = upload(bst, ctx, a_legs, A)
+    BL, bd = upload(bst, ctx, b_legs, B)
+    CL, cd = ctx.contract(AL, ad, BL, bd, la, lb)
+    c_legs = [l for i, l in enumerate(a_legs) if i not in la] + [l for i, l in enumerate(b_legs) if i not in lb]
+    assert [to_oracle_leg(l) for l in CL.legs] == c_legs
+    got = cd.cpu().numpy()
+    want = u1.from_dense(c_legs, ref)
+    assert got.shape == want.shape
+    assert rel_err(got, want) < 1e-13
+    # alpha/beta accumulation
+    c2 = cd.clone()
+    ctx.contract(AL, ad, BL, bd, la, lb, alpha=2.0, beta=-0.5, Cl=CL, c=c2)
+    assert rel_err(c2.cpu().numpy(), 1.5 * want) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_permute_and_fuse_match_oracle(bst, ctx, seed):
+    rng = np.random.default_rng(200 + seed)
+    legs = rand_legs(rng, 4, 4)
+    T = u1.to_dense(legs, rng.standard_normal(u1.nnz(legs)))
+    L, d = upload(bst, ctx, legs, T)
+    perm = [int(x) for x in rng.permutation(4)]
+    PL, pd = ctx.permute(L, d, perm)
+    plegs = [legs[p] for p in perm]
+    assert [to_oracle_leg(l) for l in PL.legs] == plegs
+    assert np.array_equal(pd.cpu().numpy(), u1.from_dense(plegs, np.transpose(T, perm)))
+    FL, fd = ctx.fuse(L, d, [2, 1, 1])
+    fl, F = u1.fuse(legs[:2])
+    flegs = [fl, legs[2], legs[3]]
+    assert [to_oracle_leg(l) for l in FL.legs] == flegs
+    ref = np.einsum("kab,abcd->kcd", F, T)
+    assert np.array_equal(fd.cpu().numpy(), u1.from_dense(flegs, ref))
+
+
+@pytest.mark.parametrize("name", ["tiny", "d4chi16", "d6chi72"])
+def test_double_layer_with_remover(bst, ctx, name):
+    cfg = u1_config(name)
+    A_legs = [u1.leg_from_spec(s) for s in cfg["A"]]
+    R_legs = [u1.leg_from_spec(s) for s in cfg["R"]]
+    A = u1.to_dense(A_legs, values(0, "A", u1.nnz(A_legs)))
+    R = u1.to_dense(R_legs, values(0, "R", u1.nnz(R_legs)))
+    legs, a = u1.double_layer(A_legs, A, R_legs, R)
+    AL = ctx.layout(cfg["A"])
+    RL = ctx.layout(cfg["R"])
+    aL, ad = ctx.double_layer(AL, dev(values(0, "A", AL.nnz)), RL, dev(values(0, "R", RL.nnz)))
+    assert [to_oracle_leg(l) for l in aL.legs] == legs
+    assert rel_err(ad.cpu().numpy(), u1.from_dense(legs, a)) < 1e-14
+
+
+def oracle_net(name, seed=0):
+    return octm.u1_network(u1_config(name), seed)
+
+
+def test_svd_projector_matches_oracle(bst, ctx):
+    net = oracle_net("d4chi16")
+    L = {r: net[r][0] for r in octm.ROLES}
+    q = octm.quarters(net)
+    out, info = octm.left_move(net, 16, return_info=True)
+    rt_legs = [L["T4"][2], L["a"][3], L["T2"][2], L["a"][3]]
+    rb_legs = [L["T4"][0], L["a"][1], L["T2"][0], L["a"][1]]
+    RtL, rt = upload(bst, ctx, rt_legs, q["Rt"])
+    RbL, rb = upload(bst, ctx, rb_legs, q["Rb"])
+    P, p, Pt, pt, sv, kept = ctx.svd_projector(RtL, rt, RbL, rb, 2, 16, 1e-14, -1)
+    assert kept == info["kept"]
+    nl = info["new_leg"]
+    assert to_oracle_leg(P.legs[2]) == nl
+    assert np.allclose(sv, info["svals"], rtol=1e-12, atol=0)
+    p_legs = [L["T4"][0], L["a"][1], nl]
+    pt_legs = [nl.dual(), L["T4"][2], L["a"][3]]
+    na = L["T4"][2].dim * L["a"][3].dim
+    P_ref = info["P"].reshape(L["T4"][0].dim, L["a"][1].dim, -1)
+    Pt_ref = info["Pt"].reshape(-1, L["T4"][2].dim, L["a"][3].dim)
+    assert rel_err(p.cpu().numpy(), u1.from_dense(p_legs, P_ref)) < TOL64
+    assert rel_err(pt.cpu().numpy(), u1.from_dense(pt_legs, Pt_ref)) < TOL64
+    assert na * 16 >= Pt.nnz
+
+
+def gpu_env(bst, ctx, name, chi_cap):
+    cfg = u1_config(name)
+    aL, ad, Ls, data = gpu_network(bst, ctx, cfg)
+    caps = {}
+    for r, Lr in Ls.items():
+        dims = [l.dim for l in Lr.legs]
+        # renewed tensors keep their site leg and get chi-sized env legs
+        caps[r] = int(np.prod([d if i == 1 and r.startswith("T") else chi_cap for i, d in enumerate(dims)]))
+        caps[r] = max(caps[r], Lr.nnz)
+    return cfg, aL, ad, bst.Env(ctx, Ls, data, caps)
+
+
+def compare_env(env, net, roles, tol):
+    errs = {}
+    for r in roles:
+        legs, dense = net[r]
+        assert [to_oracle_leg(l) for l in env.L[r].legs] == legs, r
+        errs[r] = rel_err(env.data(r).cpu().numpy(), u1.from_dense(legs, dense))
+    assert max(errs.values()) < tol, errs
+    return errs
+
+
+@pytest.mark.parametrize("name,direction", [("tiny", 0), ("d4chi16", 0), ("d4chi16", 1), ("d4chi16", 2),
+                                            ("d4chi16", 3)])
+def test_directional_move_fp64(bst, ctx, name, direction):
+    cfg, aL, ad, env = gpu_env(bst, ctx, name, u1_config(name)["chi"])
+    net = oracle_net(name)
+    d = "LURD"[direction]
+    ref = octm.move(net, d, cfg["chi"])
+    ctx.ctm_move(env, aL, ad, direction, cfg["chi"])
+    renewed = {"L": ("C1", "T4", "C4"), "U": ("C1", "T1", "C2"), "R": ("C2", "T2", "C3"),
+               "D": ("C3", "T3", "C4")}[d]
+    compare_env(env, ref, renewed, TOL64)
+    ctx.sync()
+
+
+def test_full_move_fp64_d4chi16(bst, ctx):
+    cfg, aL, ad, env = gpu_env(bst, ctx, "d4chi16", 16)
+    net = oracle_net("d4chi16")
+    ref = octm.full_move(net, cfg["chi"])
+    ctx.ctm_move(env, aL, ad, 4, cfg["chi"])
+    compare_env(env, ref, ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4"), TOL64)
+
+
+def test_left_move_fp64_d6chi72(bst, ctx):
+    """Full-size D=6, chi=72 left move (the benchmark's directional step)."""
+    cfg, aL, ad, env = gpu_env(bst, ctx, "d6chi72", 72)
+    net = oracle_net("d6chi72")
+    ref = octm.move(net, "L", cfg["chi"])
+    ctx.ctm_move(env, aL, ad, 0, cfg["chi"])
+    compare_env(env, ref, ("C1", "T4", "C4"), TOL64)
