@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""CTMRG moves/s on one GB300: U(1) one-site cell, D=6, chi=72, full move.
+
+One step = the whole hot path on the fixed seeded inputs: double layer with
+remover (S0), then the LEFT, RIGHT, UP, DOWN directional moves, each
+building the four enlarged corners, the half systems, the SVD projectors,
+and renormalising and normalising the renewed environment tensors.
+The environment is restored from a device copy before every step.
+
+Prints one JSON line (rank 0).  --impl reference times the dense FP64 CPU
+oracle on the host cores instead.  With N>1 ranks every rank runs an
+independent replica (the move does not shard; no collective on the data
+path) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "d6chi72"
+METRIC = "CTMRG moves/s & block-sparse TFLOP/s vs plain FP64 GPU path at rel err <=1e-9"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                d = json.load(f)
+            d["source"] = "measured"
+            return d
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS)
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index, self.lines, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_time(steps=1, warmup=0):
+    """Dense FP64 oracle: double layer + full move of the same workload on the
+    host cores; returns (seconds per move list, cores)."""
+    import numpy as np
+    from oracle import ctm as octm
+    from workloads import u1_config
+    cfg = u1_config(WORKLOAD)
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        net = octm.u1_network(cfg)
+        octm.full_move(net, cfg["chi"])
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+    return times, os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    times, cores = cpu_oracle_time(args.steps, args.warmup)
+    v = 1.0 / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "u1_D6_chi72_full_move", "D": 6, "chi": 72},
+            "cpu_baseline": {"value": v, "unit": "moves/s", "cores": cores, "kind": "oracle",
+                             "sample": "one full move (double layer + L,R,U,D) per step, dense numpy FP64"},
+            "e2e": {"value": v, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    from paper_1808_10804_gb300 import build as b
+    b.build()
+    from paper_1808_10804_gb300 import bst
+    from paper_1808_10804_gb300.ctmrg import Network
+    from workloads import u1_config, values
+
+    cfg = u1_config(WORKLOAD)
+    ctx = bst.Context(local)
+    draw = lambda name, n: values(0, name, n)
+    net = Network(ctx, {"A": cfg["A"], "R": cfg["R"]}, cfg["x"], cfg["chi"], draw, device=dev)
+    prec = args.prec
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(p=prec):
+        net.reset()
+        return net.step(p)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    # reference result of the FP64 path for the accuracy report
+    one_step("fp64")
+    ref64 = {r: net.env.data(r).cpu().numpy() for r in bst.ROLES}
+    refL = {r: net.env.L[r] for r in bst.ROLES}
+    one_step(prec)
+    torch.cuda.synchronize()
+    err = 0.0
+    for r in bst.ROLES:
+        if net.env.L[r] == refL[r]:
+            x = net.env.data(r).cpu().numpy()
+            err = max(err, float(np.linalg.norm(x - ref64[r]) / np.linalg.norm(ref64[r])))
+        else:
+            err = float("inf")
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launches
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))          # L2 flush between steps (outside the events)
+            ev[i][0].record(stream)
+            one_step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = (ctx.launches - l0) // args.steps
+    ms = [a.elapsed_time(b_) for a, b_ in ev]
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # per-kernel-class profile of one extra step (events around every launch)
+    ctx.profile(True)
+    one_step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    algo_flops = sum(v[2] for k, v in prof.items() if k.startswith("gemm"))
+
+    # end to end through the public API: inputs from pinned host memory,
+    # renewed environment read back every step
+    e2e_ms, h2d, d2h = [], 0, 0
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h2d = net.reset_from_host()
+        net.step(prec)
+        outs = [net.env.data(r).cpu() for r in bst.ROLES]
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t1))
+        d2h = sum(8 * o.numel() for o in outs)
+
+    # plain FP64 GPU path, same steps, for the comparison the metric names
+    fp64_ms = None
+    if prec != "fp64":
+        ev2 = []
+        for i in range(max(3, args.steps // 2)):
+            flush.fill_(float(i))
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_step("fp64")
+            b_.record(stream)
+            ev2.append((a, b_))
+        torch.cuda.synchronize()
+        fp64_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev2)
+
+    if rank != 0:
+        return
+    pk = peaks()
+    mine = {k: v for k, v in prof.items() if k != "svd_cusolver"}
+    dom = max(mine.items(), key=lambda kv: kv[1][1])
+    name, (n, tms, fl, by) = dom
+    if name.startswith("gemm"):
+        if name == "gemm_f64":
+            peak = pk["bf16_tflops"] * 1.25 / 2250.0   # FP64 tensor peak from the nominal ratio
+        else:
+            peak = pk["bf16_tflops"]
+        executed = fl * (15.0 if name == "gemm_ozaki" else 1.0)
+        achieved = executed / (tms / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "launches_per_step": n,
+                "peak_source": pk["source"]}
+    else:
+        achieved = by / (tms / 1e3) / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "launches_per_step": n, "peak_source": pk["source"]}
+    total_prof = sum(v[1] for v in prof.values())
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        times, cores = cpu_oracle_time(1, 0)
+        cpu = {"value": 1.0 / times[0], "unit": "moves/s", "cores": cores, "kind": "oracle",
+               "sample": "one full move (double layer + L,R,U,D) of the same workload, dense numpy FP64"}
+    v = world * 1e3 / ms_step
+    line = {
+        "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16x5-slices->f64",
+        "data": "synthetic",
+        "config": {"workload": "u1_D6_chi72_full_move", "D": 6, "chi": 72, "prec": prec,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
+        "block_sparse_tflops": algo_flops / (ms_step / 1e3) / 1e12,
+        "rel_err_vs_fp64_path": err,
+        "fp64_path_ms_per_step": fp64_ms,
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "roofline": roof,
+        "kernel_share": {k: round(v_[1] / total_prof, 4) for k, v_ in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": 1e3 / statistics.mean(e2e_ms), "unit": "moves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "ozaki"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

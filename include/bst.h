@@ -96,6 +96,16 @@ BST_API const char* bst_last_error(void);
 BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
 /* Number of kernels this context launched so far (all calls). */
 BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
+/* Per-kernel-class timing: enable != 0 starts recording a CUDA event pair
+ * around every launch of the library's kernels on its stream (and clears
+ * earlier records); 0 stops.  Synchronises the device. */
+BST_API bst_status bst_ctx_profile(bst_ctx ctx, int32_t enable);
+/* Aggregate of kernel class idx (0-based, in first-launch order): its name
+ * (NUL-terminated, at most cls_len bytes), launches, summed event time in
+ * ms, summed algorithmic FLOPs and bytes.  BST_E_ARG past the last class.
+ * Waits for the recorded events. */
+BST_API bst_status bst_ctx_profile_read(bst_ctx ctx, int32_t idx, char* cls, int32_t cls_len,
+                                        int64_t* launches, double* ms, double* flops, double* bytes);
 
 /* ---- layouts -------------------------------------------------------------- */
 

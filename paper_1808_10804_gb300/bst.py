@@ -69,6 +69,8 @@ def lib():
         "bst_ctx_destroy": [vp],
         "bst_ctx_sync": [vp, vp],
         "bst_ctx_launch_count": [vp],
+        "bst_ctx_profile": [vp, i32],
+        "bst_ctx_profile_read": [vp, i32, C.c_char_p, i32, P(i64), P(dbl), P(dbl), P(dbl)],
         "bst_layout_create": [vp, C.c_int, i32, P(_Leg), P(vp)],
         "bst_layout_retain": [vp],
         "bst_layout_release": [vp],
@@ -206,6 +208,23 @@ class Context:
     @property
     def launches(self):
         return lib().bst_ctx_launch_count(self.h)
+
+    def profile(self, enable=True):
+        _check(lib().bst_ctx_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel class: (launches, ms, flops, bytes)} of the recorded launches."""
+        out = {}
+        i = 0
+        while True:
+            name = C.create_string_buffer(64)
+            n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+            st = lib().bst_ctx_profile_read(self.h, i, name, 64, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by))
+            if st != 0:
+                break
+            out[name.value.decode()] = (n.value, ms.value, fl.value, by.value)
+            i += 1
+        return out
 
     def layout(self, legs):
         legs = [l if isinstance(l, Leg) else Leg(int(l["flow"]), tuple(l["charges"]), tuple(l["degs"]))

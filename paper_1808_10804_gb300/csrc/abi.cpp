@@ -1,5 +1,6 @@
 // The C ABI (include/bst.h): argument checks, error capture, handle casts.
 // No C++ exception crosses this file's functions.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -46,6 +47,7 @@ Ctx::~Ctx() {
   gplans.clear();
   for (auto& kv : bufs) kv.second.free_all();
   for (auto& kv : interned) delete kv.second;
+  for (auto e : evpool) cudaEventDestroy(e);
   if (d_err) cudaFree(d_err);
 }
 }  // namespace bst
@@ -131,6 +133,49 @@ bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream) {
 }
 
 int64_t bst_ctx_launch_count(bst_ctx ctx) { return ctx ? C_(ctx)->launches.load() : 0; }
+
+bst_status bst_ctx_profile(bst_ctx ctx, int32_t enable) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    Ctx* c = C_(ctx);
+    if (c->device >= 0) BST_CUDA(cudaDeviceSynchronize());
+    c->prof = enable != 0;
+    c->recs.clear();
+    c->evused = 0;
+  });
+}
+
+bst_status bst_ctx_profile_read(bst_ctx ctx, int32_t idx, char* cls, int32_t cls_len, int64_t* launches,
+                                double* ms, double* flops, double* bytes) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    Ctx* c = C_(ctx);
+    std::vector<std::string> names;
+    for (auto& r : c->recs)
+      if (std::find(names.begin(), names.end(), r.cls) == names.end()) names.push_back(r.cls);
+    BST_REQUIRE(idx >= 0 && idx < int32_t(names.size()), BST_E_ARG, "no such kernel class");
+    int64_t n = 0;
+    double t = 0, f = 0, b = 0;
+    for (auto& r : c->recs) {
+      if (r.cls != names[idx]) continue;
+      float x = 0;
+      BST_CUDA(cudaEventSynchronize(r.b));
+      BST_CUDA(cudaEventElapsedTime(&x, r.a, r.b));
+      ++n;
+      t += x;
+      f += r.flops;
+      b += r.bytes;
+    }
+    if (cls && cls_len > 0) {
+      std::strncpy(cls, names[idx].c_str(), size_t(cls_len) - 1);
+      cls[cls_len - 1] = 0;
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+  });
+}
 
 bst_status bst_layout_create(bst_ctx ctx, bst_group group, int32_t rank, const bst_leg* legs, bst_layout* out) {
   return guarded([&] {

@@ -118,6 +118,7 @@ struct DevRelayout {
   int2* chunks = nullptr;
   int nchunks = 0;
   int ntasks = 0;
+  double elems = 0;
   void upload(const std::vector<RelTask>& t);
   void free_all();
 };
@@ -135,6 +136,7 @@ struct DevGemm {
   int32_t* tile_prob = nullptr;   // tile -> problem
   int32_t* tile_idx = nullptr;    // tile -> linear tile index inside its problem
   int ntiles = 0, nprobs = 0;
+  double flops = 0;  // algorithmic 2*M*N*K summed over the problems
   void upload(const std::vector<GemmProb>& p, int tm, int tn);
   void free_all();
 };
@@ -161,8 +163,19 @@ struct DevBuf {
   void free_all();
 };
 
+// Optional per-kernel-class timing with CUDA events on the launching stream.
+struct ProfRec {
+  std::string cls;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
 struct Ctx {
   int device = 0;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
   std::mutex mu;
   uint64_t next_id = 1;
   std::map<std::string, Layout*> interned;  // structural key -> layout (one ref held)
@@ -238,5 +251,14 @@ void launch_sumsq(Ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStr
 void launch_fill(Ctx* ctx, double* x, int64_t n, double v, cudaStream_t s);
 
 inline void count_launch(Ctx* ctx, int n = 1) { ctx->launches += n; }
+
+// Times the launches issued during its lifetime when profiling is on.
+struct ProfScope {
+  Ctx* c;
+  cudaStream_t s;
+  long idx = -1;
+  ProfScope(Ctx* ctx, cudaStream_t st, const char* cls, double flops, double bytes);
+  ~ProfScope();
+};
 
 }  // namespace bst

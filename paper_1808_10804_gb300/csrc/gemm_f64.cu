@@ -17,6 +17,8 @@ constexpr int kPad = 2;
 void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn) {
   free_all();
   nprobs = int(p.size());
+  flops = 0;
+  for (auto& x : p) flops += 2.0 * double(x.M) * x.N * x.K;
   std::vector<int32_t> tp, ti;
   for (int i = 0; i < nprobs; ++i) {
     int mt = (p[i].M + tm - 1) / tm, nt = (p[i].N + tn - 1) / tn;
@@ -126,6 +128,7 @@ DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmPr
 
 void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* B, double* C, cudaStream_t s) {
   if (g.ntiles == 0) return;
+  ProfScope ps(ctx, s, "gemm_f64", g.flops, 0.0);
   gemm_f64_kernel<<<g.ntiles, 128, 0, s>>>(g.probs, g.tile_prob, g.tile_idx, A, B, C);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);

@@ -156,6 +156,8 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   double* dX = (double*)ctx->buf("proj.X", sizeof(double) * std::max<int64_t>(pn->cmat, 1), s);
   int* dInfo = (int*)ctx->buf("proj.info", sizeof(int) * secs.size(), s);
   BST_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int) * secs.size(), s));
+  {
+  ProfScope ps_svd(ctx, s, "svd_cusolver", 0.0, 0.0);
   for (size_t i = 0; i < secs.size(); ++i) {
     Sec& x = secs[i];
     double* A = Nm + x.cs->off;
@@ -173,6 +175,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
                                     dV + x.v_off, x.mn, dW, lwork, dR, dInfo + i));
     }
     count_launch(ctx);
+  }
   }
   std::vector<double> hS(stot);
   std::vector<int> hInfo(secs.size());

@@ -11,12 +11,32 @@
 
 namespace bst {
 
+ProfScope::ProfScope(Ctx* ctx, cudaStream_t st, const char* cls, double flops, double bytes) : c(ctx), s(st) {
+  if (!c->prof) return;
+  while (c->evpool.size() < c->evused + 2) {
+    cudaEvent_t e;
+    BST_CUDA(cudaEventCreate(&e));
+    c->evpool.push_back(e);
+  }
+  ProfRec r{cls, c->evpool[c->evused], c->evpool[c->evused + 1], flops, bytes};
+  c->evused += 2;
+  BST_CUDA(cudaEventRecord(r.a, s));
+  idx = long(c->recs.size());
+  c->recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (idx >= 0) cudaEventRecord(c->recs[idx].b, s);
+}
+
 constexpr int kChunk = 2048;
 constexpr int kRelThreads = 256;
 
 void DevRelayout::upload(const std::vector<RelTask>& t) {
   free_all();
   ntasks = int(t.size());
+  elems = 0;
+  for (auto& x : t) elems += x.n;
   std::vector<int2> ch;
   for (int i = 0; i < ntasks; ++i)
     for (int s = 0; s < t[i].n; s += kChunk) ch.push_back(make_int2(i, s));
@@ -106,6 +126,7 @@ __global__ void __launch_bounds__(kRelThreads) relayout_kernel(const RelTask* __
 void launch_relayout(Ctx* ctx, const DevRelayout& r, const double* blk, double* mat, int dir, double alpha,
                      double beta, cudaStream_t s) {
   if (r.nchunks == 0) return;
+  ProfScope ps(ctx, s, "relayout", 0.0, 16.0 * r.elems);
   relayout_kernel<<<r.nchunks, kRelThreads, 0, s>>>(r.tasks, r.chunks, const_cast<double*>(blk), mat, dir,
                                                      alpha, beta);
   BST_CUDA(cudaGetLastError());
