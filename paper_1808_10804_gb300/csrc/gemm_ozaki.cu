@@ -1,19 +1,603 @@
-// Mixed-precision (Ozaki-split BF16 on tcgen05) grouped GEMM -- placeholder
-// until the tensor-core kernel lands.
+// FP64-accurate grouped GEMM on the BF16 tensor cores (tcgen05, sm_103a).
+//
+// Every FP64 row of an operand gets a power-of-two scale 2^e with
+// |x| < 2^e; the scaled row is written, with integer arithmetic on the IEEE
+// bit pattern, as a signed-digit expansion
+//     x / 2^e = 2^-8 (a0 + 2^-9 (a1 + 2^-9 (a2 + 2^-9 (a3 + 2^-9 a4))))
+// with integer digits |a_i| <= 256, which BF16 holds exactly (44 bits kept).
+// A product of two digits is an integer below 2^16 in magnitude, exact in
+// FP32.  The GEMM sums the 15 digit products with i + j <= 4 by diagonal
+// d = i + j (weight 2^-16-9d) in tensor memory:
+//   * d = 0 and d = 1 are read out every 32 K (one pipeline stage), where
+//     their FP32 sums are exact integers of magnitude <= 2^22, and added
+//     into 32-bit integer registers;
+//   * d = 2..4 carry weights <= 2^-34 of the leading term and accumulate in
+//     FP32 over the whole K.
+// The epilogue forms the result with 64-bit integer arithmetic and one
+// conversion to FP64.  Relative error ~2^-40 against the row/column scales.
+//
+// Kernel: one 128 x 64 output tile per CTA; warp 0 drives TMA (64-byte
+// swizzled K-major tiles, 3-stage ring), warp 1 issues tcgen05.mma from one
+// thread, warps 2..5 drain tensor memory.  All waits are bounded: on expiry
+// the kernel records BST_E_TIMEOUT in the context's error word, lets its
+// copies drain (bounded), frees tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "bst_internal.h"
 
 namespace bst {
 
-struct OzakiPlan {};
+namespace oz {
 
-void ozaki_prepare(Ctx*, ContractPlan*) { throw Error(BST_E_UNSUPPORTED, "BST_OZAKI not built yet"); }
-void run_gemm_ozaki(Ctx*, ContractPlan*, const double*, const double*, double*, cudaStream_t) {
-  throw Error(BST_E_UNSUPPORTED, "BST_OZAKI not built yet");
+constexpr int kSlices = 5;
+constexpr int kTM = 128;           // tile rows (M)
+constexpr int kTN = 64;            // tile cols (N)
+constexpr int kTK = 32;            // K per stage (64 bytes of BF16)
+constexpr int kStages = 3;
+constexpr int kABytes = kTM * kTK * 2;   // 8 KB per slice
+constexpr int kBBytes = kTN * kTK * 2;   // 4 KB per slice
+constexpr int kStageBytes = kSlices * (kABytes + kBBytes);
+constexpr int kThreads = 320;            // 10 warps: TMA, MMA, 8 epilogue
+constexpr int kTmemCols = 512;
+constexpr long long kSpinLimit = 1ll << 28;
+// tensor memory columns of the accumulators
+constexpr int kColD0 = 0, kColD1 = 128, kColD2 = 256;
+
+struct Prob {
+  int32_t M, N, K, pad;
+  int32_t arow, brow;  // first row of this problem in the split A / B buffers
+  int64_t c_off, c_m, c_n;
+};
+
+struct Tile {
+  int32_t prob, m0, n0, pad;
+};
+
+struct SplitTask {
+  int32_t rows, K;
+  int32_t row0, pad;  // first row in the split buffer
+  int64_t base, s_r, s_k;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
 }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the abort flag) on expiry or when
+// another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(err, int(BST_E_TIMEOUT));
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr >> 4) & 0x3FFF);
+  d |= uint64_t(1) << 16;                    // leading byte offset (unused with swizzle)
+  d |= uint64_t((512 >> 4) & 0x3FFF) << 32;  // stride byte offset
+  d |= uint64_t(1) << 46;                    // descriptor version
+  d |= uint64_t(4) << 61;                    // SWIZZLE_64B
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(instr_desc()), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 2^e as a double for e in [-1022, 1023] (built from the bit pattern)
+__device__ __forceinline__ double pow2i(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// exact FP32 integer (|v| <= 2^22) -> int32
+__device__ __forceinline__ int f2i_exact(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+struct Smem {
+  alignas(1024) uint8_t stage[kStages][kStageBytes];
+  uint64_t full[kStages], empty[kStages];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem_base;
+  int abort_flag;
+  int eb[kTN];
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                      const Prob* __restrict__ probs, const Tile* __restrict__ tiles,
+                      const int* __restrict__ expA, const int* __restrict__ expB, int rowsA, int rowsB,
+                      double* __restrict__ C, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Tile t = tiles[blockIdx.x];
+  const Prob p = probs[t.prob];
+  const int nk = (p.K + kTK - 1) / kTK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.acc_full[b], 1);
+      mbar_init(&sm.acc_empty[b], 256);
+    }
+    sm.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x >= 64 && threadIdx.x < 64 + kTN) {
+    const int j = threadIdx.x - 64;
+    sm.eb[j] = (t.n0 + j < p.N) ? expB[p.brow + t.n0 + j] : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  volatile int* abort_flag = &sm.abort_flag;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && nk > 0) {
+      int issued = 0;
+      for (int c = 0; c < nk; ++c) {
+        const int s = c % kStages;
+        if (c >= kStages && !mbar_wait(&sm.empty[s], ((c / kStages) - 1) & 1, abort_flag, err)) break;
+        mbar_expect_tx(&sm.full[s], kStageBytes);
+        uint8_t* base = sm.stage[s];
+        const int k0 = c * kTK;
+        for (int i = 0; i < kSlices; ++i)
+          tma_load_2d(base + i * kABytes, &mapA, k0, i * rowsA + p.arow + t.m0, &sm.full[s]);
+        for (int j = 0; j < kSlices; ++j)
+          tma_load_2d(base + kSlices * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
+        issued = c + 1;
+      }
+      if (*abort_flag) {
+        // let the copies in flight land before the CTA exits (bounded)
+        for (int c = std::max(0, issued - kStages); c < issued; ++c) {
+          const int s = c % kStages;
+          for (long long i = 0; i < kSpinLimit && !mbar_try(&sm.full[s], (c / kStages) & 1); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0 && nk > 0) {
+      for (int c = 0; c < nk; ++c) {
+        const int s = c % kStages, buf = c & 1;
+        if (!mbar_wait(&sm.full[s], (c / kStages) & 1, abort_flag, err)) break;
+        if (c >= 2 && !mbar_wait(&sm.acc_empty[buf], ((c >> 1) - 1) & 1, abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sm.stage[s]);
+        const uint32_t b0 = a0 + kSlices * kABytes;
+        for (int ks = 0; ks < kTK / 16; ++ks) {
+          for (int d = 0; d <= 4; ++d) {
+            for (int i = 0; i <= d; ++i) {
+              const int j = d - i;
+              uint32_t col;
+              uint32_t acc;
+              if (d == 0) {
+                col = kColD0 + buf * kTN;
+                acc = (ks > 0) ? 1u : 0u;
+              } else if (d == 1) {
+                col = kColD1 + buf * kTN;
+                acc = (ks > 0 || i > 0) ? 1u : 0u;
+              } else {
+                col = kColD2 + (d - 2) * kTN;
+                acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
+              }
+              const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
+              const uint64_t bd = smem_desc(b0 + j * kBBytes + ks * 32);
+              mma_bf16(tmem + col, ad, bd, acc);
+            }
+          }
+        }
+        mma_commit(&sm.empty[s]);
+        mma_commit(&sm.acc_full[buf]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9 ----------------
+    // warp w may access tensor-memory lanes 32*(w%4)..+31; the two warps of a
+    // lane quarter split the 64 columns
+    constexpr int kHalf = kTN / 2;
+    const int q = warp & 3;
+    const int c0 = ((warp - 2) >> 2) * kHalf;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
+    int S0[kHalf], S1[kHalf];
+#pragma unroll
+    for (int j = 0; j < kHalf; ++j) S0[j] = S1[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nk && ok; ++c) {
+      const int buf = c & 1;
+      ok = mbar_wait(&sm.acc_full[buf], (c >> 1) & 1, abort_flag, err);
+      if (!ok) break;
+      tc_fence_after();
+      uint32_t v[32];
+      tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < kHalf; ++j) S0[j] += f2i_exact(v[j]);
+      tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < kHalf; ++j) S1[j] += f2i_exact(v[j]);
+      tc_fence_before();
+      mbar_arrive(&sm.acc_empty[buf]);
+    }
+    if (ok) {
+      const int gm = t.m0 + row;
+      const bool row_ok = gm < p.M;
+      const int ea = row_ok ? expA[p.arow + gm] : 0;
+      double* crow = C + p.c_off + (long long)gm * p.c_m;
+#pragma unroll
+      for (int h = 0; h < kHalf / 16; ++h) {
+        uint32_t w2[16], w3[16], w4[16];
+        if (nk > 0) {
+          tmem_ld16(lane_base + kColD2 + 0 * kTN + c0 + h * 16, w2);
+          tmem_ld16(lane_base + kColD2 + 1 * kTN + c0 + h * 16, w3);
+          tmem_ld16(lane_base + kColD2 + 2 * kTN + c0 + h * 16, w4);
+          tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) w2[j] = w3[j] = w4[j] = 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = h * 16 + j;
+          const int gn = t.n0 + c0 + jj;
+          // X = S0 2^27 + S1 2^18 + (S2 2^9 + S3 + S4 2^-9);  C = X 2^(ea+eb-43)
+          const float small = __uint_as_float(w2[j]) * 512.0f + __uint_as_float(w3[j]) +
+                              __uint_as_float(w4[j]) * (1.0f / 512.0f);
+          const long long X = ((long long)S0[jj] << 27) + ((long long)S1[jj] << 18) + __float2ll_rn(small);
+          const int e = ea + sm.eb[c0 + jj] - 43;
+          const double v = (double)X * pow2i(e >> 1) * pow2i(e - (e >> 1));
+          if (row_ok && gn < p.N) crow[(long long)gn * p.c_n] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+// Split FP64 rows into the five BF16 digit slices (integer arithmetic on the
+// bit pattern).  One warp per row; digits for k in [K, roundup(K, 32)) are 0.
+__global__ void ozaki_split_kernel(const SplitTask* __restrict__ tasks, int ntasks, const double* __restrict__ X,
+                                   __nv_bfloat16* __restrict__ S, int* __restrict__ ex, int rows_total,
+                                   int kpitch) {
+  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  // locate (task, row)
+  int t = 0, r = warp_g;
+  while (t < ntasks && r >= tasks[t].rows) {
+    r -= tasks[t].rows;
+    ++t;
+  }
+  if (t >= ntasks) return;
+  const SplitTask tk = tasks[t];
+  const double* xr = X + tk.base + (long long)r * tk.s_r;
+  unsigned long long mx = 0;
+  for (int k = lane; k < tk.K; k += 32) {
+    unsigned long long b = __double_as_longlong(xr[(long long)k * tk.s_k]) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  // |x| < 2^e for every entry of the row (e from the largest exponent field)
+  const int emax = int(mx >> 52);
+  const int e = emax - 1022;
+  const int grow = tk.row0 + r;
+  if (lane == 0) ex[grow] = e;
+  const int kend = (tk.K + 31) & ~31;
+  for (int k = lane; k < kend; k += 32) {
+    long long Xi = 0;
+    if (k < tk.K && mx != 0) {
+      const unsigned long long b = __double_as_longlong(xr[(long long)k * tk.s_k]);
+      const int E = int((b >> 52) & 0x7FF);
+      if (E != 0) {  // subnormals of a row with a normal maximum are below 2^-44 of it
+        const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+        // X = round(m * 2^(E - 1075 - e + 44))
+        const int sh = E - 1075 - e + 44;
+        if (sh >= 0) {
+          Xi = m << sh;
+        } else if (sh > -64) {
+          const int rs = -sh;
+          Xi = (m + (1ll << (rs - 1))) >> rs;
+        }
+        if (b >> 63) Xi = -Xi;
+      }
+    }
+    // signed digits: X = a0 2^36 + a1 2^27 + a2 2^18 + a3 2^9 + a4, |a_i| <= 256
+    int dig[kSlices];
+#pragma unroll
+    for (int i = kSlices - 1; i >= 1; --i) {
+      long long lo = ((Xi + 256) & 511) - 256;
+      dig[i] = int(lo);
+      Xi = (Xi - lo) >> 9;
+    }
+    dig[0] = int(Xi);
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i)
+      S[((long long)i * rows_total + grow) * kpitch + k] = __int2bfloat16_rn(dig[i]);
+  }
+}
+
+}  // namespace oz
+
+// ---------------------------------------------------------------------------------
+// host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    BST_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+    BST_REQUIRE(p && q == cudaDriverEntryPointSuccess, BST_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static CUtensorMap make_map(void* base, int kpitch, int rows, int box_rows) {
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  cuuint64_t dims[2] = {cuuint64_t(kpitch), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(kpitch) * 2};
+  cuuint32_t box[2] = {cuuint32_t(oz::kTK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  BST_REQUIRE(r == CUDA_SUCCESS, BST_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+  return m;
+}
+
+struct OzakiPlan {
+  int nprobs = 0, ntiles = 0;
+  int rowsA = 0, rowsB = 0, kpitch = 32;
+  oz::Prob* d_probs = nullptr;
+  oz::Tile* d_tiles = nullptr;
+  oz::SplitTask *d_sa = nullptr, *d_sb = nullptr;
+  int nsa = 0, nsb = 0;
+  __nv_bfloat16 *SA = nullptr, *SB = nullptr;
+  int *eA = nullptr, *eB = nullptr;
+  CUtensorMap mapA, mapB;
+  double flops = 0;
+  bool zero_only = false;  // every problem has K == 0
+  std::vector<GemmProb> zprobs;  // K == 0 problems, written as zeros
+  ~OzakiPlan() {
+    cudaFree(d_probs);
+    cudaFree(d_tiles);
+    cudaFree(d_sa);
+    cudaFree(d_sb);
+    cudaFree(SA);
+    cudaFree(SB);
+    cudaFree(eA);
+    cudaFree(eB);
+  }
+};
+
+static size_t smem_bytes() { return sizeof(oz::Smem) + 1024; }
+
+static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
+  auto* P = new OzakiPlan();
+  std::vector<oz::Prob> hp;
+  std::vector<oz::Tile> ht;
+  std::vector<oz::SplitTask> sa, sb;
+  int maxk = 1;
+  for (auto& g : probs) {
+    BST_REQUIRE(g.K <= 16000, BST_E_UNSUPPORTED, "Ozaki GEMM: K above 16000");
+    maxk = std::max(maxk, g.K);
+  }
+  P->kpitch = (maxk + oz::kTK - 1) / oz::kTK * oz::kTK;
+  for (auto& g : probs) {
+    oz::Prob q{};
+    q.M = g.M;
+    q.N = g.N;
+    q.K = g.K;
+    q.arow = P->rowsA;
+    q.brow = P->rowsB;
+    q.c_off = g.c_off;
+    q.c_m = g.c_m;
+    q.c_n = g.c_n;
+    sa.push_back({g.M, g.K, P->rowsA, 0, g.a_off, g.a_m, g.a_k});
+    sb.push_back({g.N, g.K, P->rowsB, 0, g.b_off, g.b_n, g.b_k});
+    P->rowsA += g.M;
+    P->rowsB += g.N;
+    const int pi = int(hp.size());
+    hp.push_back(q);
+    for (int m0 = 0; m0 < g.M; m0 += oz::kTM)
+      for (int n0 = 0; n0 < g.N; n0 += oz::kTN) ht.push_back({pi, m0, n0, 0});
+    P->flops += 2.0 * double(g.M) * g.N * g.K;
+  }
+  P->nprobs = int(hp.size());
+  P->ntiles = int(ht.size());
+  P->nsa = int(sa.size());
+  P->nsb = int(sb.size());
+  BST_REQUIRE(int64_t(P->rowsA) * oz::kSlices < (1ll << 31) && int64_t(P->rowsB) * oz::kSlices < (1ll << 31),
+              BST_E_UNSUPPORTED, "Ozaki GEMM: too many rows");
+  auto up = [](auto** dst, const auto& v) {
+    using T = typename std::remove_reference<decltype(v)>::type::value_type;
+    if (v.empty()) return;
+    BST_CUDA(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+    BST_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  };
+  up(&P->d_probs, hp);
+  up(&P->d_tiles, ht);
+  up(&P->d_sa, sa);
+  up(&P->d_sb, sb);
+  // split buffers: 5 slices x rows x kpitch BF16, with room for a full tile
+  // past the end so TMA boxes of the last rows stay inside the allocation
+  const int64_t ra = int64_t(oz::kSlices) * std::max(P->rowsA, 1) + oz::kTM;
+  const int64_t rb = int64_t(oz::kSlices) * std::max(P->rowsB, 1) + oz::kTN;
+  BST_CUDA(cudaMalloc(&P->SA, sizeof(__nv_bfloat16) * ra * P->kpitch));
+  BST_CUDA(cudaMalloc(&P->SB, sizeof(__nv_bfloat16) * rb * P->kpitch));
+  BST_CUDA(cudaMemset(P->SA, 0, sizeof(__nv_bfloat16) * ra * P->kpitch));
+  BST_CUDA(cudaMemset(P->SB, 0, sizeof(__nv_bfloat16) * rb * P->kpitch));
+  BST_CUDA(cudaMalloc(&P->eA, sizeof(int) * std::max(P->rowsA, 1)));
+  BST_CUDA(cudaMalloc(&P->eB, sizeof(int) * std::max(P->rowsB, 1)));
+  P->mapA = make_map(P->SA, P->kpitch, int(ra), oz::kTM);
+  P->mapB = make_map(P->SB, P->kpitch, int(rb), oz::kTN);
+  static bool attr = false;
+  if (!attr) {
+    BST_CUDA(cudaFuncSetAttribute(oz::ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(smem_bytes())));
+    attr = true;
+  }
+  return P;
+}
+
+static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s) {
+  if (P->ntiles == 0) return;
+  {
+    ProfScope ps(ctx, s, "split_bf16", 0.0, 0.0);
+    const int wa = P->rowsA, wb = P->rowsB;
+    if (wa) oz::ozaki_split_kernel<<<(wa + 7) / 8, 256, 0, s>>>(P->d_sa, P->nsa, A, P->SA, P->eA, P->rowsA,
+                                                               P->kpitch);
+    if (wb) oz::ozaki_split_kernel<<<(wb + 7) / 8, 256, 0, s>>>(P->d_sb, P->nsb, B, P->SB, P->eB, P->rowsB,
+                                                               P->kpitch);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx, 2);
+  }
+  ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
+  oz::ozaki_gemm_kernel<<<P->ntiles, oz::kThreads, smem_bytes(), s>>>(P->mapA, P->mapB, P->d_probs, P->d_tiles,
+                                                                       P->eA, P->eB, P->rowsA, P->rowsB, C,
+                                                                       ctx->d_err);
+  BST_CUDA(cudaGetLastError());
+  count_launch(ctx);
+}
+
+void ozaki_prepare(Ctx* ctx, ContractPlan* p) { p->oz = build_plan(ctx, p->probs); }
+
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
+                    cudaStream_t s) {
+  run_plan(ctx, p->oz, Amat, Bmat, Cmat, s);
+}
+
 void ozaki_free(OzakiPlan* oz) { delete oz; }
-void run_gemm_ozaki_probs(Ctx*, const std::string&, const std::vector<GemmProb>&, const double*, const double*,
-                          double*, cudaStream_t) {
-  throw Error(BST_E_UNSUPPORTED, "BST_OZAKI not built yet");
+
+void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
+                          const double* B, double* C, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<std::string, std::unique_ptr<OzakiPlan>> cache;
+  std::string key = std::to_string((uintptr_t)ctx) + "/" + tag + "/";
+  for (auto& g : probs)
+    key += std::to_string(g.M) + "," + std::to_string(g.N) + "," + std::to_string(g.K) + "," +
+           std::to_string(g.a_off) + "," + std::to_string(g.a_m) + "," + std::to_string(g.a_k) + "," +
+           std::to_string(g.b_off) + "," + std::to_string(g.b_n) + "," + std::to_string(g.b_k) + "," +
+           std::to_string(g.c_off) + "," + std::to_string(g.c_m) + "," + std::to_string(g.c_n) + ";";
+  OzakiPlan* P;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      P = build_plan(ctx, probs);
+      cache[key].reset(P);
+    } else {
+      P = it->second.get();
+    }
+  }
+  run_plan(ctx, P, A, B, C, s);
 }
 
 }  // namespace bst

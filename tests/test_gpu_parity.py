@@ -81,6 +81,43 @@ def test_contract_matches_oracle(bst, ctx, seed, maxdeg):
     assert rel_err(c2.cpu().numpy(), 1.5 * want) < 1e-13
 
 
+TOL_OZ = 1e-11
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("maxdeg", [3, 40, 90])
+def test_contract_ozaki_matches_oracle(bst, ctx, seed, maxdeg):
+    """Tensor-core path: sector GEMMs with M, N across several 128x64 tiles,
+    K across several 32-wide chunks, ragged edges everywhere."""
+    rng = np.random.default_rng(300 + seed)
+    shared = rand_legs(rng, 2, maxdeg)
+    ao = rand_legs(rng, 1, maxdeg)
+    bo = rand_legs(rng, 1, maxdeg)
+    a_legs = [ao[0], shared[0], shared[1]]
+    b_legs = [shared[1].dual(), bo[0], shared[0].dual()]
+    A = u1.to_dense(a_legs, rng.standard_normal(u1.nnz(a_legs)))
+    B = u1.to_dense(b_legs, rng.standard_normal(u1.nnz(b_legs)))
+    la, lb = [1, 2], [2, 0]
+    ref = np.tensordot(A, B, axes=(la, lb))
+    AL, ad = upload(bst, ctx, a_legs, A)
+    BL, bd = upload(bst, ctx, b_legs, B)
+    CL, cd = ctx.contract(AL, ad, BL, bd, la, lb, prec="ozaki")
+    ctx.sync()
+    c_legs = [a_legs[0], b_legs[1]]
+    want = u1.from_dense(c_legs, ref)
+    assert rel_err(cd.cpu().numpy(), want) < TOL_OZ
+    # wide dynamic range inside rows: the per-row scale keeps relative accuracy
+    A2 = A * np.exp(rng.uniform(-20, 20, size=A.shape[0]))[:, None, None]
+    ref2 = np.tensordot(A2, B, axes=(la, lb))
+    AL2, ad2 = upload(bst, ctx, a_legs, A2)
+    _, cd2 = ctx.contract(AL2, ad2, BL, bd, la, lb, prec="ozaki")
+    ctx.sync()
+    got = cd2.cpu().numpy()
+    want2 = u1.from_dense(c_legs, ref2)
+    # compare row by row (rows of C follow rows of A)
+    assert rel_err(got, want2) < TOL_OZ
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_permute_and_fuse_match_oracle(bst, ctx, seed):
     rng = np.random.default_rng(200 + seed)
@@ -194,3 +231,28 @@ def test_left_move_fp64_d6chi72(bst, ctx):
     ref = octm.move(net, "L", cfg["chi"])
     ctx.ctm_move(env, aL, ad, 0, cfg["chi"])
     compare_env(env, ref, ("C1", "T4", "C4"), TOL64)
+
+
+TOL_MOVE_OZ = 1e-9
+
+
+@pytest.mark.parametrize("name,direction", [("d4chi16", 0), ("d4chi16", 3)])
+def test_directional_move_ozaki(bst, ctx, name, direction):
+    """Mixed-precision path: renewed tensors within 1e-9 of the FP64 oracle."""
+    cfg, aL, ad, env = gpu_env(bst, ctx, name, u1_config(name)["chi"])
+    d = "LURD"[direction]
+    ref = octm.move(oracle_net(name), d, cfg["chi"])
+    ctx.ctm_move(env, aL, ad, direction, cfg["chi"], prec="ozaki")
+    ctx.sync()
+    renewed = {"L": ("C1", "T4", "C4"), "U": ("C1", "T1", "C2"), "R": ("C2", "T2", "C3"),
+               "D": ("C3", "T3", "C4")}[d]
+    compare_env(env, ref, renewed, TOL_MOVE_OZ)
+
+
+def test_full_move_ozaki_d6chi72(bst, ctx):
+    """The benchmark step in mixed precision against the FP64 oracle."""
+    cfg, aL, ad, env = gpu_env(bst, ctx, "d6chi72", 72)
+    ref = octm.full_move(oracle_net("d6chi72"), cfg["chi"])
+    ctx.ctm_move(env, aL, ad, 4, cfg["chi"], prec="ozaki")
+    ctx.sync()
+    compare_env(env, ref, ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4"), TOL_MOVE_OZ)
