@@ -96,6 +96,17 @@ BST_API const char* bst_last_error(void);
 BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
 /* Number of kernels this context launched so far (all calls). */
 BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
+/* Eigensolver behind bst_svd_projector and bst_ctm_move.
+ *   BST_PROJ_SUBSPACE (default): per sector of N, subspace iteration on
+ *     N^T N with a block of up to 160 vectors (iters steps, CholQR
+ *     orthonormalisation), a Rayleigh-Ritz step solved by an FP32 Jacobi
+ *     eigensolver and refined to FP64 by Ogita-Aishima steps; sectors of
+ *     dimension <= 160 are decomposed directly.  Every matrix product runs
+ *     in the call's bst_prec arithmetic.  Falls back to BST_PROJ_GESVD when
+ *     chi + 16 exceeds the block.
+ *   BST_PROJ_GESVD: full FP64 SVD of every sector with cuSOLVER gesvd. */
+typedef enum { BST_PROJ_GESVD = 0, BST_PROJ_SUBSPACE = 1 } bst_proj_method;
+BST_API bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters);
 /* Per-kernel-class timing: enable != 0 starts recording a CUDA event pair
  * around every launch of the library's kernels on its stream (and clears
  * earlier records); 0 stops.  Synchronises the device. */

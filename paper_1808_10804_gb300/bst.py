@@ -70,6 +70,7 @@ def lib():
         "bst_ctx_sync": [vp, vp],
         "bst_ctx_launch_count": [vp],
         "bst_ctx_profile": [vp, i32],
+        "bst_ctx_set_projector": [vp, i32, i32],
         "bst_ctx_profile_read": [vp, i32, C.c_char_p, i32, P(i64), P(dbl), P(dbl), P(dbl)],
         "bst_layout_create": [vp, C.c_int, i32, P(_Leg), P(vp)],
         "bst_layout_retain": [vp],
@@ -208,6 +209,10 @@ class Context:
     @property
     def launches(self):
         return lib().bst_ctx_launch_count(self.h)
+
+    def set_projector(self, method="subspace", iters=14):
+        m = {"gesvd": 0, "subspace": 1}[method]
+        _check(lib().bst_ctx_set_projector(self.h, m, iters))
 
     def profile(self, enable=True):
         _check(lib().bst_ctx_profile(self.h, 1 if enable else 0))

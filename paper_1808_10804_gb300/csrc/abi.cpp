@@ -134,6 +134,16 @@ bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream) {
 
 int64_t bst_ctx_launch_count(bst_ctx ctx) { return ctx ? C_(ctx)->launches.load() : 0; }
 
+bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    BST_REQUIRE(method == BST_PROJ_GESVD || method == BST_PROJ_SUBSPACE, BST_E_ARG, "unknown projector method");
+    BST_REQUIRE(iters >= 1 && iters <= 200, BST_E_ARG, "iters must be 1..200");
+    C_(ctx)->proj_method = method;
+    C_(ctx)->proj_iters = iters;
+  });
+}
+
 bst_status bst_ctx_profile(bst_ctx ctx, int32_t enable) {
   return guarded([&] {
     BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");

@@ -1,0 +1,329 @@
+// Small dense kernels for the projector's eigensolver.
+//
+// The projector needs the leading eigenpairs of the sector Gram matrices
+// G = N^T N.  Large sectors are first reduced by subspace iteration (GEMMs
+// on the tensor cores); the resulting b x b (b <= 160) symmetric problems
+// are solved here:
+//   * jacobi_eig_f32: cyclic two-sided Jacobi in FP32, one CTA per problem,
+//     parallel round-robin pair ordering, eigenvalues sorted descending;
+//   * oa_update: one step of the Ogita-Aishima refinement, which lifts the
+//     FP32 eigenvectors to FP64 accuracy using only matrix products
+//     (R = I - X^T X, S = X^T H X, X <- X (I + E));
+//   * cholinv_f32: FP32 Cholesky factor M = L L^T and the inverse of L^T,
+//     used to orthonormalise the subspace-iteration block (CholQR).
+#include <cmath>
+
+#include "bst_internal.h"
+
+namespace bst {
+
+constexpr int kEigMax = 160;
+
+struct SmallProb {
+  int32_t b, pad;
+  int64_t in_off;   // b x b FP64 input, row-major
+  int64_t out_off;  // b x b FP64 output, row-major
+  int64_t val_off;  // b FP64 values
+};
+
+// One CTA per problem.  A and V live in shared memory as FP32.
+__global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
+                                                      double* __restrict__ out, double* __restrict__ vals,
+                                                      int max_sweeps) {
+  extern __shared__ float sh[];
+  const SmallProb pr = probs[blockIdx.x];
+  const int b = pr.b;
+  const int bp = b + (b & 1);  // even number of indices for the pairing
+  const int ld = bp + 1;
+  float* A = sh;
+  float* V = A + bp * ld;
+  float* cs = V + bp * ld;      // cos per pair
+  float* sn = cs + bp / 2;      // sin per pair
+  int* pp = (int*)(sn + bp / 2);
+  int* qq = pp + bp / 2;
+  float* red = (float*)(qq + bp / 2);
+  int* order = (int*)(red + 256);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double* H = in + pr.in_off;
+  for (int e = tid; e < bp * bp; e += nt) {
+    const int i = e / bp, j = e % bp;
+    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j]) : 0.0f;
+    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int npair = bp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test: off-diagonal vs diagonal Frobenius mass
+    float off = 0.f, dia = 0.f;
+    for (int e = tid; e < b * b; e += nt) {
+      const int i = e / b, j = e % b;
+      const float a = A[i * ld + j];
+      if (i == j) dia += a * a;
+      else off += a * a;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    const float offs = red[0];
+    __syncthreads();
+    red[tid] = dia;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    const float dias = red[0];
+    __syncthreads();
+    if (offs <= 1e-14f * dias) break;
+    for (int r = 0; r < bp - 1; ++r) {
+      // round-robin pairing: index bp-1 fixed, the others rotate
+      for (int k = tid; k < npair; k += nt) {
+        int p, q;
+        if (k == 0) {
+          p = bp - 1;
+          q = r;
+        } else {
+          p = (r + k) % (bp - 1);
+          q = (r - k + (bp - 1)) % (bp - 1);
+        }
+        if (p > q) {
+          int x = p;
+          p = q;
+          q = x;
+        }
+        pp[k] = p;
+        qq[k] = q;
+        const float apq = A[p * ld + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-30f) {
+          const float app = A[p * ld + p], aqq = A[q * ld + q];
+          const float tau = (aqq - app) / (2.f * apq);
+          const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+        }
+        cs[k] = c;
+        sn[k] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < npair * bp; e += nt) {
+        const int k = e / bp, j = e % bp;
+        const int p = pp[k], q = qq[k];
+        const float c = cs[k], s = sn[k];
+        const float ap = A[p * ld + j], aq = A[q * ld + j];
+        A[p * ld + j] = c * ap - s * aq;
+        A[q * ld + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < npair * bp; e += nt) {
+        const int k = e / bp, i = e % bp;
+        const int p = pp[k], q = qq[k];
+        const float c = cs[k], s = sn[k];
+        const float ap = A[i * ld + p], aq = A[i * ld + q];
+        A[i * ld + p] = c * ap - s * aq;
+        A[i * ld + q] = s * ap + c * aq;
+        const float vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - s * vq;
+        V[i * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // descending order of the eigenvalues (ties: lower index first)
+  for (int i = tid; i < b; i += nt) {
+    const float ai = A[i * ld + i];
+    int rank = 0;
+    for (int j = 0; j < b; ++j) {
+      const float aj = A[j * ld + j];
+      rank += (aj > ai) || (aj == ai && j < i);
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+  double* X = out + pr.out_off;
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, jn = e % b;
+    X[(long long)i * b + jn] = double(V[i * ld + order[jn]]);
+  }
+  for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]);
+}
+
+size_t jacobi_smem(int b) {
+  const int bp = b + (b & 1);
+  return sizeof(float) * (2 * bp * (bp + 1) + bp + 256) + sizeof(int) * (bp + bp);
+}
+
+// Ogita-Aishima step, elementwise part.  In: XtX (b x b), S = X^T H X.
+// Out: E (b x b) and lam (b):  R = I - XtX, lam_i = S_ii / (1 - R_ii),
+// E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when |lam_i - lam_j| > delta,
+// else R_ij / 2.
+__global__ void oa_update(const SmallProb* __restrict__ probs, const double* __restrict__ XtX,
+                          const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam,
+                          double rel_delta) {
+  const SmallProb pr = probs[blockIdx.x];
+  const int b = pr.b;
+  const double* xx = XtX + pr.in_off;
+  const double* s = S + pr.in_off;
+  double* e = E + pr.in_off;
+  double* l = lam + pr.val_off;
+  __shared__ double smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    const double rii = 1.0 - xx[(long long)i * b + i];
+    l[i] = s[(long long)i * b + i] / (1.0 - rii);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int i = 0; i < b; ++i) m = fmax(m, fabs(l[i]));
+    smax = m;
+  }
+  __syncthreads();
+  const double delta = rel_delta * smax;
+  for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
+    const int i = q / b, j = q % b;
+    const double rij = (i == j ? 1.0 : 0.0) - xx[q];
+    double v;
+    if (i == j || fabs(l[i] - l[j]) <= delta) v = 0.5 * rij;
+    else v = (s[q] + l[j] * rij) / (l[j] - l[i]);
+    e[q] = v;
+  }
+}
+
+// X <- X + XE (in place; XE computed by a GEMM)
+__global__ void add_inplace(double* __restrict__ X, const double* __restrict__ XE, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    X[i] += XE[i];
+}
+
+// FP32 Cholesky of M (b x b, FP64 in) and Rinv = (L^T)^-1 (upper, FP64 out).
+__global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
+                                                   double* __restrict__ out, int* err) {
+  extern __shared__ float sh[];
+  const SmallProb pr = probs[blockIdx.x];
+  const int b = pr.b, ld = b + 1;
+  float* L = sh;            // b x ld
+  float* Li = L + b * ld;   // b x ld, inverse of L
+  const double* M = in + pr.in_off;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // scale by the diagonal so the factorisation sees unit diagonal
+  float* dsc = Li + b * ld;
+  for (int i = tid; i < b; i += nt) {
+    const double d = M[(long long)i * b + i];
+    dsc[i] = d > 0 ? float(1.0 / sqrt(d)) : 1.0f;
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, j = e % b;
+    L[i * ld + j] = float(M[e]) * dsc[i] * dsc[j];
+  }
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    if (tid == 0) {
+      float d = L[k * ld + k];
+      if (!(d > 1e-30f)) {
+        d = 1e-30f;
+        atomicExch(err, int(BST_E_NUMERIC));
+      }
+      L[k * ld + k] = sqrtf(d);
+    }
+    __syncthreads();
+    const float dk = L[k * ld + k];
+    for (int i = k + 1 + tid; i < b; i += nt) L[i * ld + k] /= dk;
+    __syncthreads();
+    const int m = b - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i * ld + j] -= L[i * ld + k] * L[j * ld + k];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower factor, one column per thread
+  for (int j = tid; j < b; j += nt) {
+    for (int i = 0; i < b; ++i) {
+      if (i < j) {
+        Li[i * ld + j] = 0.f;
+        continue;
+      }
+      float acc = (i == j) ? 1.f : 0.f;
+      for (int k = j; k < i; ++k) acc -= L[i * ld + k] * Li[k * ld + j];
+      Li[i * ld + j] = acc / L[i * ld + i];
+    }
+  }
+  __syncthreads();
+  // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
+  // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
+  double* R = out + pr.out_off;
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, j = e % b;
+    R[e] = double(dsc[i]) * double(Li[j * ld + i]);
+  }
+}
+
+size_t cholinv_smem(int b) { return sizeof(float) * (2 * b * (b + 1) + b); }
+
+// out = alpha * I + beta * in (square blocks)
+__global__ void ident_combo(const SmallProb* __restrict__ probs, const double* __restrict__ in, double* __restrict__ out,
+                            double alpha, double beta) {
+  const SmallProb pr = probs[blockIdx.x];
+  const int b = pr.b;
+  for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
+    const int i = q / b, j = q % b;
+    out[pr.out_off + q] = (i == j ? alpha : 0.0) + beta * in[pr.in_off + q];
+  }
+}
+
+// Deterministic pseudo-random normal entries (counter-based hash + Box-Muller).
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__global__ void randn_fill(double* x, long long n, uint64_t seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint64_t a = mix64(seed * 0x9E3779B97F4A7C15ull + 2 * i + 1);
+    const uint64_t c = mix64(a ^ 0xD1B54A32D192ED03ull);
+    const double u1 = (double((a >> 11) + 1)) * (1.0 / 9007199254740992.0);
+    const double u2 = double(c >> 11) * (1.0 / 9007199254740992.0);
+    x[i] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  }
+}
+
+// Residual norms of Ritz pairs: res_j = ||Y[:,j] - lam_j V[:,j]|| / lam_max
+struct ResProb {
+  int32_t m, k;
+  int64_t y_off, v_off, val_off, ld;
+};
+
+__global__ void ritz_residual(const ResProb* __restrict__ probs, const double* __restrict__ Y,
+                              const double* __restrict__ V, const double* __restrict__ vals, double* __restrict__ res) {
+  const ResProb pr = probs[blockIdx.x];
+  const int j = blockIdx.y;
+  if (j >= pr.k) return;
+  __shared__ double sh[256];
+  const double lam = vals[pr.val_off + j];
+  double acc = 0;
+  for (int i = threadIdx.x; i < pr.m; i += blockDim.x) {
+    const double r = Y[pr.y_off + (long long)i * pr.ld + j] - lam * V[pr.v_off + (long long)i * pr.ld + j];
+    acc += r * r;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[pr.val_off + j] = sqrt(sh[0]);
+}
+
+}  // namespace bst

@@ -29,13 +29,13 @@ void launch_transpose(const double* A, double* Y, int M, int N, cudaStream_t s);
       throw ::bst::Error(BST_E_CUDA, std::string(#call) + " failed: " + std::to_string(int(st_))); \
   } while (0)
 
-// Gauge and scale: for kept vector j, u_j = column j of the left factor
+// Gauge and scale (U = N V when u_div_sigma, else the left vector): for kept vector j, u_j = column j of the left factor
 // (element i at U[i*us_i + j*us_j]); sign from the largest |u_j(i)| (lowest i
 // on ties); writes Uo[i*m + j] = sign*u/sqrt(s_j) (row-major [m x k]) and
 // Vo[i*k + j] = sign*v/sqrt(s_j) (row-major [n x k]).
 __global__ void gauge_scale_kernel(const double* U, long long us_i, long long us_j, int m,
                                    const double* V, long long vs_i, long long vs_j, int n,
-                                   const double* S, int k, double* Uo, double* Vo) {
+                                   const double* S, int k, double* Uo, double* Vo, int u_div_sigma) {
   const int j = blockIdx.x;
   if (j >= k) return;
   __shared__ double sv[256];
@@ -65,7 +65,8 @@ __global__ void gauge_scale_kernel(const double* U, long long us_i, long long us
   }
   const double sgn = (U[(long long)si[0] * us_i + j * us_j] < 0) ? -1.0 : 1.0;
   const double f = sgn / sqrt(S[j]);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) Uo[(long long)i * k + j] = f * U[i * us_i + j * us_j];
+  const double fu = u_div_sigma ? f / S[j] : f;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) Uo[(long long)i * k + j] = fu * U[i * us_i + j * us_j];
   for (int i = threadIdx.x; i < n; i += blockDim.x) Vo[(long long)i * k + j] = f * V[i * vs_i + j * vs_j];
 }
 
@@ -90,12 +91,235 @@ static ProjView* get_projview(Ctx* ctx, Layout* L, const std::vector<int>& rows,
   return raw;
 }
 
-ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
-                         int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
-                         cudaStream_t s) {
-  BST_REQUIRE(ncut >= 1 && ncut < Rt->rank && ncut < Rb->rank, BST_E_ARG, "bad ncut");
-  BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
-  BST_REQUIRE(new_flow == 1 || new_flow == -1, BST_E_ARG, "new_flow must be +1 or -1");
+
+// kernels of eig.cu
+struct SmallProb {
+  int32_t b, pad;
+  int64_t in_off, out_off, val_off;
+};
+struct ResProb {
+  int32_t m, k;
+  int64_t y_off, v_off, val_off, ld;
+};
+__global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int);
+__global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double);
+__global__ void add_inplace(double*, const double*, long long);
+__global__ void cholinv_f32(const SmallProb*, const double*, double*, int*);
+__global__ void ident_combo(const SmallProb*, const double*, double*, double, double);
+__global__ void randn_fill(double*, long long, uint64_t);
+__global__ void ritz_residual(const ResProb*, const double*, const double*, const double*, double*);
+size_t jacobi_smem(int b);
+size_t cholinv_smem(int b);
+constexpr int kEigMax = 160;
+
+static GemmProb gp(int M, int N, int K, int64_t ao, int64_t am, int64_t ak, int64_t bo, int64_t bn, int64_t bk,
+                   int64_t co, int64_t cm, int64_t cn) {
+  GemmProb g{};
+  g.M = M; g.N = N; g.K = K;
+  g.a_off = ao; g.a_m = am; g.a_k = ak;
+  g.b_off = bo; g.b_n = bn; g.b_k = bk;
+  g.c_off = co; g.c_m = cm; g.c_n = cn;
+  return g;
+}
+
+static std::string probs_key(const std::vector<GemmProb>& probs) {
+  std::string k;
+  for (auto& g : probs)
+    k += std::to_string(g.M) + "," + std::to_string(g.N) + "," + std::to_string(g.K) + "," +
+         std::to_string(g.a_off) + "," + std::to_string(g.a_m) + "," + std::to_string(g.a_k) + "," +
+         std::to_string(g.b_off) + "," + std::to_string(g.b_n) + "," + std::to_string(g.b_k) + "," +
+         std::to_string(g.c_off) + "," + std::to_string(g.c_m) + "," + std::to_string(g.c_n) + ";";
+  return k;
+}
+
+// FP64-accurate grouped GEMM in the requested arithmetic.
+static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std::vector<GemmProb>& probs,
+                     const double* A, const double* B, double* C, cudaStream_t s) {
+  if (probs.empty()) return;
+  if (prec == BST_FP64)
+    launch_gemm_f64(ctx, *get_dev_gemm(ctx, tag + "/" + probs_key(probs), probs), A, B, C, s);
+  else
+    run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s);
+}
+
+template <class T>
+static T* upload_cached(Ctx* ctx, const std::string& name, const std::vector<T>& v, cudaStream_t s) {
+  T* d = (T*)ctx->buf(name, sizeof(T) * std::max<size_t>(v.size(), 1), s);
+  BST_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+struct PSec {
+  const MatSector *cs, *as, *bs;
+  int M, N;        // N_s is M x N (rows: right cut of Rt, cols: right cut of Rb)
+  int c;           // candidate singular values (descending)
+  int64_t v_off;   // right vectors, row-major N x c
+  int64_t s_off;   // offset into the host sigma list
+  bool direct;     // eigen-decomposition of N^T N without subspace iteration
+  int b;           // small problem size
+  int64_t q_off, z_off, sm_off, val_off;
+};
+
+static void setup_attrs() {
+  static bool done = false;
+  if (done) return;
+  BST_CUDA(cudaFuncSetAttribute(jacobi_eig_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jacobi_smem(kEigMax))));
+  BST_CUDA(cudaFuncSetAttribute(cholinv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cholinv_smem(kEigMax))));
+  done = true;
+}
+
+// Symmetric eigenproblems (b <= 160) in FP64 accuracy: FP32 Jacobi, then
+// two Ogita-Aishima refinement steps.  H: inputs, X: vectors out, lam: values.
+static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
+                      int64_t smtot, int64_t valtot, cudaStream_t s) {
+  if (sp.empty()) return;
+  setup_attrs();
+  SmallProb* dsp = upload_cached(ctx, "eig.sp", sp, s);
+  int bmax = 0;
+  for (auto& p : sp) bmax = std::max(bmax, p.b);
+  {
+    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
+    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 30);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
+  double* XtX = (double*)ctx->buf("eig.xtx", sizeof(double) * smtot, s);
+  double* T = (double*)ctx->buf("eig.t", sizeof(double) * smtot, s);
+  double* S = (double*)ctx->buf("eig.s", sizeof(double) * smtot, s);
+  double* E = (double*)ctx->buf("eig.e", sizeof(double) * smtot, s);
+  std::vector<GemmProb> g_xtx, g_hx, g_s, g_xe;
+  for (auto& p : sp) {
+    const int b = p.b;
+    const int64_t o = p.in_off;
+    g_xtx.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));     // X^T X
+    g_hx.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // H X
+    g_s.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));       // X^T T
+    g_xe.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // X E
+  }
+  for (int it = 0; it < 2; ++it) {
+    gemm_any(ctx, "oa.xtx", prec, g_xtx, X, X, XtX, s);
+    gemm_any(ctx, "oa.hx", prec, g_hx, H, X, T, s);
+    gemm_any(ctx, "oa.s", prec, g_s, X, T, S, s);
+    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-10);
+    gemm_any(ctx, "oa.xe", prec, g_xe, X, E, T, s);
+    add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx, 2);
+  }
+}
+
+// Leading right singular vectors of every sector of N: subspace iteration on
+// N^T N (block b) and a Rayleigh-Ritz step; small sectors directly.
+// Fills dV (row-major N x c per sector) and hSig; returns false when a
+// sector needs more candidates than the small eigensolver holds.
+static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int64_t chi, bst_prec prec, int iters,
+                             double*& dV, std::vector<double>& hSig, cudaStream_t s) {
+  int64_t vtot = 0, qtot = 0, ztot = 0, smtot = 0, valtot = 0;
+  for (auto& x : secs) {
+    x.direct = x.N <= kEigMax;
+    x.b = x.direct ? x.N : kEigMax;
+    if (!x.direct && std::min<int64_t>(chi, x.N) + 16 > x.b) return false;
+    x.c = x.b;
+    x.v_off = vtot;
+    vtot += int64_t(x.N) * x.c;
+    x.q_off = qtot;
+    qtot += x.direct ? 0 : int64_t(x.N) * x.b;
+    x.z_off = ztot;
+    ztot += x.direct ? 0 : int64_t(std::max(x.M, x.N)) * x.b;
+    x.sm_off = smtot;
+    smtot += int64_t(x.b) * x.b;
+    x.val_off = valtot;
+    valtot += x.b;
+  }
+  dV = (double*)ctx->buf("proj.V2", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+  double* Q = (double*)ctx->buf("proj.Q", sizeof(double) * std::max<int64_t>(qtot, 1), s);
+  double* Z = (double*)ctx->buf("proj.Z", sizeof(double) * std::max<int64_t>(ztot, 1), s);
+  double* Y = (double*)ctx->buf("proj.Y", sizeof(double) * std::max<int64_t>(qtot, 1), s);
+  double* Msm = (double*)ctx->buf("proj.M", sizeof(double) * std::max<int64_t>(smtot, 1), s);
+  double* Rinv = (double*)ctx->buf("proj.Rinv", sizeof(double) * std::max<int64_t>(smtot, 1), s);
+  double* Xv = (double*)ctx->buf("proj.X2", sizeof(double) * std::max<int64_t>(smtot, 1), s);
+  double* lam = (double*)ctx->buf("proj.lam", sizeof(double) * std::max<int64_t>(valtot, 1), s);
+  std::vector<GemmProb> g_z, g_y, g_gram, g_qr, g_h, g_v, g_direct;
+  std::vector<SmallProb> sp_it, sp_all;
+  for (auto& x : secs) {
+    SmallProb sp{x.b, 0, x.sm_off, x.sm_off, x.val_off};
+    sp_all.push_back(sp);
+    const int64_t no = x.cs->off;
+    if (x.direct) {
+      g_direct.push_back(gp(x.N, x.N, x.M, no, 1, x.N, no, 1, x.N, x.sm_off, x.N, 1));  // N^T N
+      continue;
+    }
+    sp_it.push_back(sp);
+    const int b = x.b;
+    g_z.push_back(gp(x.M, b, x.N, no, x.N, 1, x.q_off, 1, b, x.z_off, b, 1));          // Z = N Q
+    g_y.push_back(gp(x.N, b, x.M, no, 1, x.N, x.z_off, 1, b, x.q_off, b, 1));          // Y = N^T Z
+    g_gram.push_back(gp(b, b, x.N, x.q_off, 1, b, x.q_off, 1, b, x.sm_off, b, 1));     // Y^T Y
+    g_qr.push_back(gp(x.N, b, b, x.q_off, b, 1, x.sm_off, 1, b, x.q_off, b, 1));       // Y Rinv
+    g_h.push_back(gp(b, b, x.M, x.z_off, 1, b, x.z_off, 1, b, x.sm_off, b, 1));        // Z^T Z
+    g_v.push_back(gp(x.N, b, b, x.q_off, b, 1, x.sm_off, 1, b, x.v_off, b, 1));        // V = Q W
+  }
+  SmallProb* dsp_it = sp_it.empty() ? nullptr : upload_cached(ctx, "proj.spit", sp_it, s);
+  setup_attrs();
+  int bmax = 1;
+  for (auto& x : secs) bmax = std::max(bmax, x.b);
+  if (!sp_it.empty()) {
+    // deterministic random start
+    for (auto& x : secs)
+      if (!x.direct) {
+        const int64_t n = int64_t(x.N) * x.b;
+        randn_fill<<<int(std::min<int64_t>((n + 255) / 256, 1216)), 256, 0, s>>>(Q + x.q_off, n,
+                                                                              0x5eed0000ull + uint64_t(x.cs->key + 4096));
+        count_launch(ctx);
+      }
+    auto orth = [&](const char* tag) {
+      // CholQR with an FP32 factor: Y <- Y R^-1 (Y lives in Q)
+      gemm_any(ctx, std::string("ss.gram") + tag, prec, g_gram, Q, Q, Msm, s);
+      cholinv_f32<<<int(sp_it.size()), 256, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+      count_launch(ctx);
+      BST_CUDA(cudaGetLastError());
+      gemm_any(ctx, std::string("ss.qr") + tag, prec, g_qr, Q, Rinv, Y, s);
+      std::swap(Q, Y);
+    };
+    for (int t = 0; t < iters; ++t) {
+      gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
+      gemm_any(ctx, "ss.y", prec, g_y, Nm, Z, Y, s);
+      std::swap(Q, Y);
+      orth("");
+    }
+    // second CholQR pass and a first-order polish: orthonormal to FP64
+    orth("2");
+    gemm_any(ctx, "ss.gram3", prec, g_gram, Q, Q, Msm, s);
+    ident_combo<<<int(sp_it.size()), 256, 0, s>>>(dsp_it, Msm, Rinv, 1.5, -0.5);
+    count_launch(ctx);
+    gemm_any(ctx, "ss.qr3", prec, g_qr, Q, Rinv, Y, s);
+    std::swap(Q, Y);
+    // Rayleigh-Ritz: H = (N Q)^T (N Q)
+    gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
+    gemm_any(ctx, "ss.h", prec, g_h, Z, Z, Msm, s);
+  }
+  gemm_any(ctx, "ss.direct", prec, g_direct, Nm, Nm, Msm, s);
+  small_eig(ctx, prec, sp_all, Msm, Xv, lam, smtot, valtot, s);
+  // V = Q W (iterative) or W (direct)
+  if (!g_v.empty()) gemm_any(ctx, "ss.v", prec, g_v, Q, Xv, dV, s);
+  for (auto& x : secs)
+    if (x.direct)
+      BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
+                               cudaMemcpyDeviceToDevice, s));
+  std::vector<double> hl(valtot);
+  BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaStreamSynchronize(s));
+  hSig.assign(valtot, 0.0);
+  for (auto& x : secs) {
+    x.s_off = x.val_off;
+    for (int j = 0; j < x.c; ++j) hSig[x.val_off + j] = std::sqrt(std::max(hl[x.val_off + j], 0.0));
+  }
+  return true;
+}
+
+// Full FP64 SVD of every sector with cuSOLVER (gesvd); used for sectors the
+// small eigensolver cannot hold.
+static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>& secs, double*& dV,
+                          std::vector<double>& hSig, cudaStream_t s) {
   if (!ctx->cusolver) {
     cusolverDnHandle_t h;
     BST_CUSOLVER(cusolverDnCreate(&h));
@@ -103,7 +327,76 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   }
   cusolverDnHandle_t h = (cusolverDnHandle_t)ctx->cusolver;
   BST_CUSOLVER(cusolverDnSetStream(h, s));
+  int64_t stot = 0, utot = 0, vtot = 0, vt2 = 0;
+  int lwork = 0, maxmn = 1;
+  std::vector<int64_t> u_off(secs.size()), vt_off(secs.size());
+  for (size_t i = 0; i < secs.size(); ++i) {
+    auto& x = secs[i];
+    const int mn = std::min(x.M, x.N);
+    x.c = mn;
+    x.s_off = stot;
+    stot += mn;
+    u_off[i] = utot;
+    utot += int64_t(std::max(x.M, x.N)) * mn;
+    vt_off[i] = vt2;
+    vt2 += int64_t(mn) * mn;
+    x.v_off = vtot;
+    vtot += int64_t(x.N) * mn;
+    const bool trans = x.N >= x.M;
+    int m = trans ? x.N : x.M, n = trans ? x.M : x.N, lw = 0;
+    BST_CUSOLVER(cusolverDnDgesvd_bufferSize(h, m, n, &lw));
+    lwork = std::max(lwork, lw);
+    maxmn = std::max(maxmn, mn);
+  }
+  double* dS = (double*)ctx->buf("proj.S", sizeof(double) * std::max<int64_t>(stot, 1), s);
+  double* dU = (double*)ctx->buf("proj.U", sizeof(double) * std::max<int64_t>(utot, 1), s);
+  double* dVT = (double*)ctx->buf("proj.VT", sizeof(double) * std::max<int64_t>(vt2, 1), s);
+  double* dW = (double*)ctx->buf("proj.work", sizeof(double) * std::max(lwork, 1), s);
+  double* dR = (double*)ctx->buf("proj.rwork", sizeof(double) * maxmn, s);
+  double* dX = (double*)ctx->buf("proj.X", sizeof(double) * std::max<int64_t>(cmat, 1), s);
+  dV = (double*)ctx->buf("proj.V2", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+  int* dInfo = (int*)ctx->buf("proj.info", sizeof(int) * secs.size(), s);
+  BST_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int) * secs.size(), s));
+  {
+    ProfScope ps_svd(ctx, s, "svd_cusolver", 0.0, 0.0);
+    for (size_t i = 0; i < secs.size(); ++i) {
+      auto& x = secs[i];
+      const int mn = x.c;
+      double* Y = dX + x.cs->off;
+      if (x.N >= x.M) {
+        // row-major N_s [M x N] is col-major X = N_s^T [N x M]; X = Ux S VTx,
+        // right vectors of N_s = columns of Ux
+        BST_CUDA(cudaMemcpyAsync(Y, Nm + x.cs->off, sizeof(double) * int64_t(x.M) * x.N, cudaMemcpyDeviceToDevice, s));
+        BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.N, x.M, Y, x.N, dS + x.s_off, dU + u_off[i], x.N,
+                                      dVT + vt_off[i], mn, dW, lwork, dR, dInfo + i));
+        // V (row-major N x mn) from col-major Ux (N x mn): V[r][j] = Ux[r + j N]
+        launch_transpose(dU + u_off[i], dV + x.v_off, mn, x.N, s);
+      } else {
+        // col-major Y = N_s [M x N]; Y = Uy S VTy, right vectors = rows of VTy
+        launch_transpose(Nm + x.cs->off, Y, x.M, x.N, s);
+        BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.M, x.N, Y, x.M, dS + x.s_off, dU + u_off[i], x.M,
+                                      dVT + vt_off[i], mn, dW, lwork, dR, dInfo + i));
+        // V[r][j] = VTy[j + r mn]: the same memory order
+        BST_CUDA(cudaMemcpyAsync(dV + x.v_off, dVT + vt_off[i], sizeof(double) * int64_t(x.N) * mn,
+                                 cudaMemcpyDeviceToDevice, s));
+      }
+      count_launch(ctx, 2);
+    }
+  }
+  hSig.assign(stot, 0.0);
+  std::vector<int> hInfo(secs.size());
+  BST_CUDA(cudaMemcpyAsync(hSig.data(), dS, sizeof(double) * stot, cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaMemcpyAsync(hInfo.data(), dInfo, sizeof(int) * secs.size(), cudaMemcpyDeviceToHost, s));
+  BST_CUDA(cudaStreamSynchronize(s));
+  for (int v : hInfo) BST_REQUIRE(v == 0, BST_E_NUMERIC, "projector: gesvd did not converge");
+}
 
+ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
+                         int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
+                         cudaStream_t s) {
+  BST_REQUIRE(ncut >= 1 && ncut < Rt->rank && ncut < Rb->rank, BST_E_ARG, "bad ncut");
+  BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
+  BST_REQUIRE(new_flow == 1 || new_flow == -1, BST_E_ARG, "new_flow must be +1 or -1");
   std::vector<int> cut(ncut);
   std::iota(cut.begin(), cut.end(), 0);
   ContractPlan* pn = get_contract_plan(ctx, Rt, Rb, cut, cut);
@@ -112,85 +405,41 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   run_contract(ctx, pn, rt, rb, prec, 1.0, 0.0, nullptr, s, /*scatter=*/false, &Nm);
   const double* Am = (const double*)ctx->bufs["contract.A"].p;  // Rt as [beta x alpha]
   const double* Bm = (const double*)ctx->bufs["contract.B"].p;  // Rb as [beta' x alpha']
-  // copy A/B sector matrices: later GEMMs reuse the contract buffers
   double* At = (double*)ctx->buf("proj.A", sizeof(double) * std::max<int64_t>(pn->amat, 1), s);
   double* Bt = (double*)ctx->buf("proj.B", sizeof(double) * std::max<int64_t>(pn->bmat, 1), s);
   BST_CUDA(cudaMemcpyAsync(At, Am, sizeof(double) * pn->amat, cudaMemcpyDeviceToDevice, s));
   BST_CUDA(cudaMemcpyAsync(Bt, Bm, sizeof(double) * pn->bmat, cudaMemcpyDeviceToDevice, s));
 
-  struct Sec {
-    const MatSector* cs;
-    const MatSector* as;
-    const MatSector* bs;
-    int M, N, mn;
-    bool trans;  // decompose N^T (col-major view of the row-major matrix)
-    int64_t s_off, u_off, v_off;
-  };
-  std::vector<Sec> secs;
-  int64_t stot = 0, utot = 0, vtot = 0;
-  int lwork = 0;
+  std::vector<PSec> secs;
   for (auto& cs : pn->vc.secs) {
     const MatSector* as = pn->va.find(cs.key);
     const MatSector* bs = pn->vb.find(-cs.key);
     if (!as || !bs || as->cols == 0 || cs.rows == 0 || cs.cols == 0) continue;
-    Sec x{&cs, as, bs, int(cs.rows), int(cs.cols), int(std::min(cs.rows, cs.cols)), cs.cols >= cs.rows, 0, 0, 0};
-    x.s_off = stot;
-    stot += x.mn;
-    x.u_off = utot;
-    utot += int64_t(std::max(x.M, x.N)) * x.mn;
-    x.v_off = vtot;
-    vtot += int64_t(x.mn) * x.mn;
-    int m = x.trans ? x.N : x.M, n = x.trans ? x.M : x.N, lw = 0;
-    BST_CUSOLVER(cusolverDnDgesvd_bufferSize(h, m, n, &lw));
-    lwork = std::max(lwork, lw);
+    PSec x{};
+    x.cs = &cs;
+    x.as = as;
+    x.bs = bs;
+    x.M = int(cs.rows);
+    x.N = int(cs.cols);
     secs.push_back(x);
   }
   BST_REQUIRE(!secs.empty(), BST_E_NUMERIC, "projector: no non-empty sector");
-  double* dS = (double*)ctx->buf("proj.S", sizeof(double) * stot, s);
-  double* dU = (double*)ctx->buf("proj.U", sizeof(double) * utot, s);
-  double* dV = (double*)ctx->buf("proj.V", sizeof(double) * vtot, s);
-  double* dW = (double*)ctx->buf("proj.work", sizeof(double) * std::max(lwork, 1), s);
-  int maxmn = 1;
-  for (auto& x : secs) maxmn = std::max(maxmn, x.mn);
-  double* dR = (double*)ctx->buf("proj.rwork", sizeof(double) * maxmn, s);
-  double* dX = (double*)ctx->buf("proj.X", sizeof(double) * std::max<int64_t>(pn->cmat, 1), s);
-  int* dInfo = (int*)ctx->buf("proj.info", sizeof(int) * secs.size(), s);
-  BST_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int) * secs.size(), s));
-  {
-  ProfScope ps_svd(ctx, s, "svd_cusolver", 0.0, 0.0);
-  for (size_t i = 0; i < secs.size(); ++i) {
-    Sec& x = secs[i];
-    double* A = Nm + x.cs->off;
-    if (x.trans) {
-      // row-major N_s [M x N] is col-major X = N_s^T [N x M], N >= M
-      BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.N, x.M, A, x.N, dS + x.s_off, dU + x.u_off, x.N,
-                                    dV + x.v_off, x.mn, dW, lwork, dR, dInfo + i));
-    } else {
-      // need rows >= cols: transpose into col-major Y = N_s [M x N]
-      double* Y = dX + x.cs->off;
-      // transpose: Y[i + j*M] = A[i*N + j]
-      launch_transpose(A, Y, x.M, x.N, s);
-      count_launch(ctx);
-      BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.M, x.N, Y, x.M, dS + x.s_off, dU + x.u_off, x.M,
-                                    dV + x.v_off, x.mn, dW, lwork, dR, dInfo + i));
-    }
-    count_launch(ctx);
+  double* dV = nullptr;
+  std::vector<double> hSig;
+  bool done = false;
+  if (ctx->proj_method == 1) {
+    ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
+    done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
   }
-  }
-  std::vector<double> hS(stot);
-  std::vector<int> hInfo(secs.size());
-  BST_CUDA(cudaMemcpyAsync(hS.data(), dS, sizeof(double) * stot, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaMemcpyAsync(hInfo.data(), dInfo, sizeof(int) * secs.size(), cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaStreamSynchronize(s));
-  for (int v : hInfo) BST_REQUIRE(v == 0, BST_E_NUMERIC, "projector: gesvd did not converge");
+  if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
 
   // global truncation: sigma descending, |q| ascending, q ascending
   struct Cand { double sv; int q; int sec; int j; };
   std::vector<Cand> cand;
   double smax = 0, ssum = 0;
   for (size_t i = 0; i < secs.size(); ++i)
-    for (int j = 0; j < secs[i].mn; ++j) {
-      double v = hS[secs[i].s_off + j];
+    for (int j = 0; j < secs[i].c; ++j) {
+      const double v = hSig[secs[i].s_off + j];
       BST_REQUIRE(std::isfinite(v), BST_E_NUMERIC, "projector: non-finite singular value");
       cand.push_back({v, int(new_flow * secs[i].cs->key), int(i), j});
       smax = std::max(smax, v);
@@ -208,8 +457,6 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   for (auto& c : cand) {
     if (kept >= chi) break;
     if (!(c.sv > rel_cutoff * smax) || c.sv <= 0) break;
-    // singular values of one sector come sorted, so the kept ones of a
-    // sector are its leading ones
     kcount[c.sec]++;
     kept++;
     kept_sum += c.sv;
@@ -217,10 +464,13 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   }
   BST_REQUIRE(kept > 0, BST_E_NUMERIC, "projector: nothing above the cutoff");
   for (size_t i = 0; i < secs.size(); ++i)
-    for (int j = 0; j < kcount[i]; ++j)
-      BST_REQUIRE(hS[secs[i].s_off + j] >= hS[secs[i].s_off + kcount[i] - 1], BST_E_NUMERIC, "projector: unsorted");
+    for (int j = 1; j < kcount[i]; ++j)
+      BST_REQUIRE(hSig[secs[i].s_off + j] <= hSig[secs[i].s_off + j - 1], BST_E_NUMERIC, "projector: unsorted");
+  if (ctx->proj_method == 1)
+    for (size_t i = 0; i < secs.size(); ++i)
+      BST_REQUIRE(secs[i].direct || kcount[i] + 16 <= secs[i].c, BST_E_NUMERIC,
+                  "projector: kept states reach the edge of the iterated subspace");
 
-  // new leg: ascending charge
   std::vector<std::pair<int, int>> order;  // (charge, sec)
   for (size_t i = 0; i < secs.size(); ++i)
     if (kcount[i] > 0) order.push_back({int(new_flow * secs[i].cs->key), int(i)});
@@ -231,7 +481,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   for (auto& o : order) {
     nl.q.push_back(o.first);
     nl.d.push_back(kcount[o.second]);
-    for (int j = 0; j < kcount[o.second]; ++j) res.svals.push_back(hS[secs[o.second].s_off + j]);
+    for (int j = 0; j < kcount[o.second]; ++j) res.svals.push_back(hSig[secs[o.second].s_off + j]);
   }
   nl.finish();
   res.newleg = nl;
@@ -250,35 +500,43 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   ProjView* vp = get_projview(ctx, res.P, prow, pcol);
   ProjView* vpt = get_projview(ctx, res.Pt, ptrow, ptcol);
 
-  // gauge-fixed, S^-1/2-scaled factors, then P and Pt sector GEMMs
-  int64_t us_tot = 0, vs_tot = 0;
+  // kept sigma on the device, left vectors U = N V / sigma, gauge, scale
+  int64_t us_tot = 0, vs_tot = 0, sk_tot = 0;
+  std::vector<int64_t> sk_off(secs.size()), ur_off(secs.size());
   for (size_t i = 0; i < secs.size(); ++i) {
+    sk_off[i] = sk_tot;
+    sk_tot += kcount[i];
+    ur_off[i] = us_tot;
     us_tot += int64_t(secs[i].M) * kcount[i];
     vs_tot += int64_t(secs[i].N) * kcount[i];
   }
+  std::vector<double> hsk(std::max<int64_t>(sk_tot, 1));
+  for (size_t i = 0; i < secs.size(); ++i)
+    for (int j = 0; j < kcount[i]; ++j) hsk[sk_off[i] + j] = hSig[secs[i].s_off + j];
+  double* dSk = upload_cached(ctx, "proj.sk", hsk, s);
+  double* Ur = (double*)ctx->buf("proj.Ur", sizeof(double) * std::max<int64_t>(us_tot, 1), s);
   double* Us = (double*)ctx->buf("proj.Us", sizeof(double) * std::max<int64_t>(us_tot, 1), s);
   double* Vs = (double*)ctx->buf("proj.Vs", sizeof(double) * std::max<int64_t>(vs_tot, 1), s);
   double* Pm = (double*)ctx->buf("proj.Pm", sizeof(double) * std::max<int64_t>(vp->mv.total, 1), s);
   double* Ptm = (double*)ctx->buf("proj.Ptm", sizeof(double) * std::max<int64_t>(vpt->mv.total, 1), s);
   BST_CUDA(cudaMemsetAsync(Pm, 0, sizeof(double) * std::max<int64_t>(vp->mv.total, 1), s));
   BST_CUDA(cudaMemsetAsync(Ptm, 0, sizeof(double) * std::max<int64_t>(vpt->mv.total, 1), s));
-  std::vector<GemmProb> gp, gpt;
-  int64_t uo = 0, vo = 0;
+  std::vector<GemmProb> gu, gpp, gpt;
   for (size_t i = 0; i < secs.size(); ++i) {
-    const Sec& x = secs[i];
     const int k = kcount[i];
     if (k == 0) continue;
-    // left vectors of N_s (length M) and right vectors (length N)
-    const double *Ul, *Vr;
-    long long ui, uj, vi, vj;
-    if (x.trans) {  // X = N_s^T = Ux S VTx: left(N_s) = rows of VTx, right(N_s) = cols of Ux
-      Ul = dV + x.v_off; ui = x.mn; uj = 1;     // VTx[j + i*ldvt], ldvt = mn
-      Vr = dU + x.u_off; vi = 1; vj = x.N;      // Ux[i + j*N]
-    } else {        // Y = N_s = Uy S VTy
-      Ul = dU + x.u_off; ui = 1; uj = x.M;
-      Vr = dV + x.v_off; vi = x.mn; vj = 1;
-    }
-    gauge_scale_kernel<<<k, 256, 0, s>>>(Ul, ui, uj, x.M, Vr, vi, vj, x.N, dS + x.s_off, k, Us + uo, Vs + vo);
+    const PSec& x = secs[i];
+    // Ur = N V_k  ([M x k]; V row-major N x c)
+    gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
+  }
+  gemm_any(ctx, "proj.u", prec, gu, Nm, dV, Ur, s);
+  int64_t uo = 0, vo = 0;
+  for (size_t i = 0; i < secs.size(); ++i) {
+    const PSec& x = secs[i];
+    const int k = kcount[i];
+    if (k == 0) continue;
+    gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i], k,
+                                         Us + uo, Vs + vo, 1);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
     const int key = int(x.cs->key);
@@ -286,31 +544,15 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     const MatSector* pts = vpt->mv.find(key);
     BST_REQUIRE(ps && pts && ps->cols == k && pts->rows == k, BST_E_SHAPE, "projector: view mismatch");
     BST_REQUIRE(ps->rows == x.bs->cols && pts->cols == x.as->cols, BST_E_SHAPE, "projector: cut mismatch");
-    // P_s[a', j] = sum_b' Rb[a', b'] V~[b', j]  with Rb^T stored as Bmat [b' x a']
-    GemmProb g{};
-    g.M = int(ps->rows); g.N = k; g.K = x.N;
-    g.a_off = x.bs->off; g.a_m = 1; g.a_k = x.bs->cols;
-    g.b_off = vo; g.b_n = 1; g.b_k = k;
-    g.c_off = ps->off; g.c_m = k; g.c_n = 1;
-    gp.push_back(g);
-    // Pt_s[j, a] = sum_b U~[b, j] Rt[a, b]  with Rt^T stored as Amat [b x a]
-    GemmProb h2{};
-    h2.M = k; h2.N = int(pts->cols); h2.K = x.M;
-    h2.a_off = uo; h2.a_m = 1; h2.a_k = k;
-    h2.b_off = x.as->off; h2.b_n = 1; h2.b_k = x.as->cols;
-    h2.c_off = pts->off; h2.c_m = pts->cols; h2.c_n = 1;
-    gpt.push_back(h2);
+    // P_s[a', j] = sum_b' Rb[a', b'] V~[b', j], Rb^T stored as Bmat [b' x a']
+    gpp.push_back(gp(int(ps->rows), k, x.N, x.bs->off, 1, x.bs->cols, vo, 1, k, ps->off, k, 1));
+    // Pt_s[j, a] = sum_b U~[b, j] Rt[a, b], Rt^T stored as Amat [b x a]
+    gpt.push_back(gp(k, int(pts->cols), x.M, uo, 1, k, x.as->off, 1, x.as->cols, pts->off, pts->cols, 1));
     uo += int64_t(x.M) * k;
     vo += int64_t(x.N) * k;
   }
-  if (prec == BST_FP64) {
-    std::string base = std::to_string((uintptr_t)pn) + "/" + std::to_string(res.P->id);
-    launch_gemm_f64(ctx, *get_dev_gemm(ctx, "projP/" + base, gp), Bt, Vs, Pm, s);
-    launch_gemm_f64(ctx, *get_dev_gemm(ctx, "projPt/" + base, gpt), Us, At, Ptm, s);
-  } else {
-    run_gemm_ozaki_probs(ctx, "projP", gp, Bt, Vs, Pm, s);
-    run_gemm_ozaki_probs(ctx, "projPt", gpt, Us, At, Ptm, s);
-  }
+  gemm_any(ctx, "proj.P", prec, gpp, Bt, Vs, Pm, s);
+  gemm_any(ctx, "proj.Pt", prec, gpt, Us, At, Ptm, s);
   launch_relayout(ctx, vp->rel, p, Pm, 1, 1.0, 0.0, s);
   launch_relayout(ctx, vpt->rel, pt, Ptm, 1, 1.0, 0.0, s);
   return res;
