@@ -45,39 +45,43 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
   int* order = (int*)(red + 256);
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* H = in + pr.in_off;
+  // scale by the largest diagonal entry (in FP64) so FP32 cannot overflow
+  __shared__ double hscale;
+  if (tid == 0) {
+    double m = 0;
+    for (int i = 0; i < b; ++i) m = fmax(m, fabs(H[(long long)i * b + i]));
+    hscale = m > 0 ? m : 1.0;
+  }
+  __syncthreads();
+  const double inv = 1.0 / hscale;
   for (int e = tid; e < bp * bp; e += nt) {
     const int i = e / bp, j = e % bp;
-    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j]) : 0.0f;
+    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
     V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
   }
   __syncthreads();
   const int npair = bp / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence test: off-diagonal vs diagonal Frobenius mass
-    float off = 0.f, dia = 0.f;
-    for (int e = tid; e < b * b; e += nt) {
-      const int i = e / b, j = e % b;
+    // convergence test, relative to the diagonal (keeps small eigenvalues
+    // accurate): max_{i<j} a_ij^2 / |a_ii a_jj|
+    float worst = 0.f;
+    for (int q = tid; q < b * b; q += nt) {
+      const int i = q / b, j = q % b;
+      if (j <= i) continue;
       const float a = A[i * ld + j];
-      if (i == j) dia += a * a;
-      else off += a * a;
+      const float d = fabsf(A[i * ld + i] * A[j * ld + j]);
+      const float r = d > 0.f ? a * a / d : (a != 0.f ? 1.f : 0.f);
+      worst = fmaxf(worst, r);
     }
-    red[tid] = off;
+    red[tid] = worst;
     __syncthreads();
     for (int w = nt / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
+      if (tid < w) red[tid] = fmaxf(red[tid], red[tid + w]);
       __syncthreads();
     }
-    const float offs = red[0];
+    const float wmax = red[0];
     __syncthreads();
-    red[tid] = dia;
-    __syncthreads();
-    for (int w = nt / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
-      __syncthreads();
-    }
-    const float dias = red[0];
-    __syncthreads();
-    if (offs <= 1e-14f * dias) break;
+    if (wmax <= 1e-13f) break;
     for (int r = 0; r < bp - 1; ++r) {
       // round-robin pairing: index bp-1 fixed, the others rotate
       for (int k = tid; k < npair; k += nt) {
@@ -98,7 +102,8 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         qq[k] = q;
         const float apq = A[p * ld + q];
         float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-30f) {
+        const float dd = fabsf(A[p * ld + p] * A[q * ld + q]);
+        if (fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd) {
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           const float tau = (aqq - app) / (2.f * apq);
           const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
@@ -134,12 +139,15 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
       __syncthreads();
     }
   }
-  // descending order of the eigenvalues (ties: lower index first)
+  // descending order of the eigenvalues (ties and NaN: lower index first;
+  // NaN compares as -inf so the ranks stay a permutation)
   for (int i = tid; i < b; i += nt) {
-    const float ai = A[i * ld + i];
+    float ai = A[i * ld + i];
+    if (ai != ai) ai = -INFINITY;
     int rank = 0;
     for (int j = 0; j < b; ++j) {
-      const float aj = A[j * ld + j];
+      float aj = A[j * ld + j];
+      if (aj != aj) aj = -INFINITY;
       rank += (aj > ai) || (aj == ai && j < i);
     }
     order[rank] = i;
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
     const int i = e / b, jn = e % b;
     X[(long long)i * b + jn] = double(V[i * ld + order[jn]]);
   }
-  for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]);
+  for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]) * hscale;
 }
 
 size_t jacobi_smem(int b) {
@@ -160,8 +168,8 @@ size_t jacobi_smem(int b) {
 
 // Ogita-Aishima step, elementwise part.  In: XtX (b x b), S = X^T H X.
 // Out: E (b x b) and lam (b):  R = I - XtX, lam_i = S_ii / (1 - R_ii),
-// E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when |lam_i - lam_j| > delta,
-// else R_ij / 2.
+// E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when the pair is separated,
+// |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|), else R_ij / 2.
 __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __restrict__ XtX,
                           const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam,
                           double rel_delta) {
@@ -185,10 +193,10 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
     smax = m;
   }
   __syncthreads();
-  const double delta = rel_delta * smax;
   for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
     const int i = q / b, j = q % b;
     const double rij = (i == j ? 1.0 : 0.0) - xx[q];
+    const double delta = rel_delta * fmax(fabs(l[i]), fabs(l[j])) + 1e-300 * smax;
     double v;
     if (i == j || fabs(l[i] - l[j]) <= delta) v = 0.5 * rij;
     else v = (s[q] + l[j] * rij) / (l[j] - l[i]);
@@ -221,19 +229,30 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
   __syncthreads();
   for (int e = tid; e < b * b; e += nt) {
     const int i = e / b, j = e % b;
-    L[i * ld + j] = float(M[e]) * dsc[i] * dsc[j];
+    const double di = M[(long long)i * b + i], dj = M[(long long)j * b + j];
+    const double sc = (di > 0 && dj > 0) ? 1.0 / sqrt(di * dj) : 1.0;
+    L[i * ld + j] = float(M[e] * sc);
   }
   __syncthreads();
+  // columns whose pivot falls below kDrop (numerically dependent on the
+  // earlier ones at FP32 level) are dropped: their row and column of the
+  // factor become the identity and their column of Rinv is zero
+  int* drop = reinterpret_cast<int*>(dsc + b);
   for (int k = 0; k < b; ++k) {
     if (tid == 0) {
-      float d = L[k * ld + k];
-      if (!(d > 1e-30f)) {
-        d = 1e-30f;
-        atomicExch(err, int(BST_E_NUMERIC));
-      }
-      L[k * ld + k] = sqrtf(d);
+      const float d = L[k * ld + k];
+      drop[k] = !(d > 1e-6f);
+      L[k * ld + k] = drop[k] ? 1.0f : sqrtf(d);
     }
     __syncthreads();
+    if (drop[k]) {
+      for (int i = tid; i < b; i += nt) {
+        if (i > k) L[i * ld + k] = 0.f;
+        if (i < k) L[k * ld + i] = 0.f;
+      }
+      __syncthreads();
+      continue;
+    }
     const float dk = L[k * ld + k];
     for (int i = k + 1 + tid; i < b; i += nt) L[i * ld + k] /= dk;
     __syncthreads();
@@ -262,11 +281,12 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
   double* R = out + pr.out_off;
   for (int e = tid; e < b * b; e += nt) {
     const int i = e / b, j = e % b;
-    R[e] = double(dsc[i]) * double(Li[j * ld + i]);
+    const double di = M[(long long)i * b + i];
+    R[e] = (drop[i] || drop[j]) ? 0.0 : (di > 0 ? 1.0 / sqrt(di) : 1.0) * double(Li[j * ld + i]);
   }
 }
 
-size_t cholinv_smem(int b) { return sizeof(float) * (2 * b * (b + 1) + b); }
+size_t cholinv_smem(int b) { return sizeof(float) * (2 * b * (b + 1) + b) + sizeof(int) * b; }
 
 // out = alpha * I + beta * in (square blocks)
 __global__ void ident_combo(const SmallProb* __restrict__ probs, const double* __restrict__ in, double* __restrict__ out,

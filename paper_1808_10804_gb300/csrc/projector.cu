@@ -35,7 +35,8 @@ void launch_transpose(const double* A, double* Y, int M, int N, cudaStream_t s);
 // Vo[i*k + j] = sign*v/sqrt(s_j) (row-major [n x k]).
 __global__ void gauge_scale_kernel(const double* U, long long us_i, long long us_j, int m,
                                    const double* V, long long vs_i, long long vs_j, int n,
-                                   const double* S, int k, double* Uo, double* Vo, int u_div_sigma) {
+                                   const double* S, int k, double* Uo, double* Vo, int u_div_sigma,
+                                   double sscale) {
   const int j = blockIdx.x;
   if (j >= k) return;
   __shared__ double sv[256];
@@ -64,10 +65,16 @@ __global__ void gauge_scale_kernel(const double* U, long long us_i, long long us
     __syncthreads();
   }
   const double sgn = (U[(long long)si[0] * us_i + j * us_j] < 0) ? -1.0 : 1.0;
-  const double f = sgn / sqrt(S[j]);
+  const double f = sgn / sqrt(S[j] * sscale);
   const double fu = u_div_sigma ? f / S[j] : f;
   for (int i = threadIdx.x; i < m; i += blockDim.x) Uo[(long long)i * k + j] = fu * U[i * us_i + j * us_j];
   for (int i = threadIdx.x; i < n; i += blockDim.x) Vo[(long long)i * k + j] = f * V[i * vs_i + j * vs_j];
+}
+
+// out[r][j] = in[r][perm[j]] for a row-major block with c columns
+__global__ void permute_cols(const double* in, double* out, int c, const int* perm) {
+  const long long r = blockIdx.x;
+  for (int j = threadIdx.x; j < c; j += blockDim.x) out[r * c + j] = in[r * c + perm[j]];
 }
 
 // Views and scatter plans of a projector layout, cached by layout.
@@ -168,8 +175,8 @@ static void setup_attrs() {
   done = true;
 }
 
-// Symmetric eigenproblems (b <= 160) in FP64 accuracy: FP32 Jacobi, then
-// two Ogita-Aishima refinement steps.  H: inputs, X: vectors out, lam: values.
+// Symmetric eigenproblems (b <= 160) in FP64 accuracy: FP32 Jacobi (relative
+// convergence test), then three Ogita-Aishima refinement steps.  H: inputs, X: vectors out, lam: values.
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
                       int64_t smtot, int64_t valtot, cudaStream_t s) {
   if (sp.empty()) return;
@@ -196,11 +203,11 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     g_s.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));       // X^T T
     g_xe.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // X E
   }
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < 3; ++it) {
     gemm_any(ctx, "oa.xtx", prec, g_xtx, X, X, XtX, s);
     gemm_any(ctx, "oa.hx", prec, g_hx, H, X, T, s);
     gemm_any(ctx, "oa.s", prec, g_s, X, T, S, s);
-    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-10);
+    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9);
     gemm_any(ctx, "oa.xe", prec, g_xe, X, E, T, s);
     add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
     BST_CUDA(cudaGetLastError());
@@ -424,6 +431,11 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     secs.push_back(x);
   }
   BST_REQUIRE(!secs.empty(), BST_E_NUMERIC, "projector: no non-empty sector");
+  // normalise N (Frobenius) so every later stage, FP32 ones included, works
+  // on O(1) numbers; singular values are scaled back below
+  double* dss = (double*)ctx->buf("proj.nss", sizeof(double), s);
+  launch_sumsq(ctx, Nm, pn->cmat, dss, s);
+  launch_scale(ctx, Nm, pn->cmat, dss, s);
   double* dV = nullptr;
   std::vector<double> hSig;
   bool done = false;
@@ -432,6 +444,40 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
   }
   if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
+  double nss = 0;
+  BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
+  const double nscale = std::sqrt(nss);
+  BST_REQUIRE(std::isfinite(nscale) && nscale > 0, BST_E_NUMERIC, "projector: N is zero or not finite");
+  // per sector descending order of the candidates (refinement may swap
+  // values that agree to rounding); the vectors are permuted to match
+  {
+    std::vector<int> perm_all;
+    std::vector<int64_t> ptask;
+    bool any = false;
+    for (auto& x : secs) {
+      std::vector<int> ord(x.c);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int a, int b) { return hSig[x.s_off + a] > hSig[x.s_off + b]; });
+      for (int j = 0; j < x.c; ++j) any |= ord[j] != j;
+      std::vector<double> tmp(x.c);
+      for (int j = 0; j < x.c; ++j) tmp[j] = hSig[x.s_off + ord[j]];
+      for (int j = 0; j < x.c; ++j) hSig[x.s_off + j] = tmp[j];
+      perm_all.insert(perm_all.end(), ord.begin(), ord.end());
+    }
+    if (any) {
+      int64_t vtot = 0, po = 0;
+      for (auto& x : secs) vtot = std::max(vtot, x.v_off + int64_t(x.N) * x.c);
+      double* tmpv = (double*)ctx->buf("proj.Vperm", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+      int* dperm = upload_cached(ctx, "proj.perm", perm_all, s);
+      for (auto& x : secs) {
+        permute_cols<<<x.N, 128, 0, s>>>(dV + x.v_off, tmpv + x.v_off, x.c, dperm + po);
+        po += x.c;
+      }
+      BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
+      count_launch(ctx, int(secs.size()));
+    }
+  }
 
   // global truncation: sigma descending, |q| ascending, q ascending
   struct Cand { double sv; int q; int sec; int j; };
@@ -481,7 +527,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   for (auto& o : order) {
     nl.q.push_back(o.first);
     nl.d.push_back(kcount[o.second]);
-    for (int j = 0; j < kcount[o.second]; ++j) res.svals.push_back(hSig[secs[o.second].s_off + j]);
+    for (int j = 0; j < kcount[o.second]; ++j) res.svals.push_back(hSig[secs[o.second].s_off + j] * nscale);
   }
   nl.finish();
   res.newleg = nl;
@@ -536,7 +582,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     const int k = kcount[i];
     if (k == 0) continue;
     gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i], k,
-                                         Us + uo, Vs + vo, 1);
+                                         Us + uo, Vs + vo, 1, nscale);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
     const int key = int(x.cs->key);
