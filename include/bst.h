@@ -217,6 +217,16 @@ BST_API bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double*
                              bst_layout* P, double* p, bst_layout* Pt, double* pt,
                              double* svals, int64_t* kept, bst_stream stream);
 
+/* Batched dense symmetric eigendecomposition used by the projector: batch
+ * row-major n x n symmetric matrices H (device, back to back, n <= 160) ->
+ * eigenvectors X (device, same layout, column j = eigenvector j) and
+ * eigenvalues lam (device, n per matrix, descending).  FP32 Jacobi followed
+ * by three Ogita-Aishima refinement steps whose matrix products run in
+ * `prec`.  No counterpart in the paper (a building block of the SVD it
+ * uses). */
+BST_API bst_status bst_sym_eig(bst_ctx ctx, int32_t n, int32_t batch, const double* H, double* X,
+                               double* lam, bst_prec prec, bst_stream stream);
+
 /* One-site CTMRG environment: corners C1..C4 and edges T1..T4 (index 0..3).
  * Legs: C1[R,D] C2[L,D] C3[U,L] C4[U,R]  T1[L,D,R] T2[U,L,D] T3[L,U,R]
  * T4[U,R,D]; the site tensor is a[L,U,R,D].  c[i], t[i] are device buffers

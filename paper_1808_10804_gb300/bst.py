@@ -87,6 +87,7 @@ def lib():
         "bst_svd_projector": [vp, vp, vp, vp, vp, i32, i64, dbl, i32, C.c_int, P(vp), vp, P(vp), vp,
                               P(dbl), P(i64), vp],
         "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
+        "bst_sym_eig": [vp, i32, i32, vp, vp, vp, C.c_int, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -304,6 +305,15 @@ class Context:
                                        C.byref(kept), _stream(stream)))
         P, Pt = Layout(self, hp), Layout(self, hpt)
         return P, p[:P.nnz], Pt, pt[:Pt.nnz], list(sv)[:kept.value], kept.value
+
+    def sym_eig(self, H, prec="fp64", stream=None):
+        """H: (batch, n, n) float64 CUDA tensor -> (X, lam), eigenvalues descending."""
+        batch, n, _ = H.shape
+        H = H.contiguous()
+        X = torch.empty_like(H)
+        lam = torch.empty((batch, n), dtype=torch.float64, device=H.device)
+        _check(lib().bst_sym_eig(self.h, n, batch, _ptr(H), _ptr(X), _ptr(lam), PREC[prec], _stream(stream)))
+        return X, lam
 
     def ctm_move(self, env, a_layout, a, direction, chi, rel_cutoff=1e-14, prec="fp64", stream=None):
         """env: Env; renewed tensors are rewritten in place."""

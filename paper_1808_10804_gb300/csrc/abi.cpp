@@ -411,6 +411,16 @@ bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double* rtop, b
   });
 }
 
+bst_status bst_sym_eig(bst_ctx ctx, int32_t n, int32_t batch, const double* H, double* X, double* lam,
+                       bst_prec prec, bst_stream stream) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && H && X && lam, BST_E_ARG, "null argument");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    sym_eig_batched(c, n, batch, H, X, lam, prec, (cudaStream_t)stream);
+  });
+}
+
 bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a, bst_env* env, int64_t chi,
                         double rel_cutoff, bst_prec prec, bst_ctm_stats* stats, bst_stream stream) {
   return guarded([&] {

@@ -243,6 +243,9 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
                          int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
                          cudaStream_t s);
 
+void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, double* lam, bst_prec prec,
+                     cudaStream_t s);
+
 // ctm.cpp
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,
               bst_prec prec, bst_ctm_stats* stats, cudaStream_t s);

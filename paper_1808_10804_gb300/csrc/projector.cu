@@ -398,6 +398,16 @@ static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>&
   for (int v : hInfo) BST_REQUIRE(v == 0, BST_E_NUMERIC, "projector: gesvd did not converge");
 }
 
+// Batched symmetric eigendecomposition of `batch` n x n matrices (n <= 160),
+// row-major, back to back; eigenvalues descending.
+void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, double* lam, bst_prec prec,
+                     cudaStream_t s) {
+  BST_REQUIRE(n >= 1 && n <= kEigMax && batch >= 1, BST_E_ARG, "sym_eig: n must be 1..160");
+  std::vector<SmallProb> sp;
+  for (int i = 0; i < batch; ++i) sp.push_back({n, 0, int64_t(i) * n * n, int64_t(i) * n * n, int64_t(i) * n});
+  small_eig(ctx, prec, sp, H, X, lam, int64_t(batch) * n * n, int64_t(batch) * n, s);
+}
+
 ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
                          int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
                          cudaStream_t s) {

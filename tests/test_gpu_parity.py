@@ -84,6 +84,36 @@ def test_contract_matches_oracle(bst, ctx, seed, maxdeg):
 TOL_OZ = 1e-11
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 133, 160])
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_sym_eig_matches_lapack(bst, ctx, n, prec):
+    """Small dense eigensolver of the projector against LAPACK, with a
+    spectrum spread over ten decades (as in the projector's Gram matrices)."""
+    rng = np.random.default_rng(n)
+    batch = 3
+    Hs, ws = [], []
+    for _ in range(batch):
+        Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        w = np.sort(10.0 ** rng.uniform(-10, 0, size=n))[::-1]
+        Hs.append((Qm * w) @ Qm.T)
+        ws.append(w)
+    H = np.stack(Hs)
+    X, lam = ctx.sym_eig(dev(H), prec)
+    X, lam = X.cpu().numpy(), lam.cpu().numpy()
+    for i in range(batch):
+        w_ref, V_ref = np.linalg.eigh(H[i])
+        w_ref, V_ref = w_ref[::-1], V_ref[:, ::-1]
+        # eigenvalues to FP64 accuracy relative to the largest
+        assert np.abs(lam[i] - w_ref).max() < 1e-13 * w_ref[0]
+        # leading eigenvectors (well separated ones) up to sign
+        for j in range(min(n, 20)):
+            gap = min([abs(w_ref[j] - w_ref[k]) for k in range(n) if k != j] + [np.inf]) / w_ref[0]
+            if gap < 1e-6:
+                continue
+            d = abs(float(X[i][:, j] @ V_ref[:, j]))
+            assert abs(1 - d) < 1e-12 + 1e-15 / gap ** 2, (j, d, gap)
+
+
 @pytest.mark.parametrize("seed", range(6))
 @pytest.mark.parametrize("maxdeg", [3, 40, 90])
 def test_contract_ozaki_matches_oracle(bst, ctx, seed, maxdeg):
