@@ -62,16 +62,17 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
   __syncthreads();
   const int npair = bp / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence test, relative to the diagonal (keeps small eigenvalues
-    // accurate): max_{i<j} a_ij^2 / |a_ii a_jj|
+    // convergence test relative to the diagonal (keeps small eigenvalues
+    // accurate) with a floor kTau below which values are not resolved:
+    // max_{i<j} a_ij^2 / (max(|a_ii|, kTau) max(|a_jj|, kTau))
+    constexpr float kTau = 1e-5f;
     float worst = 0.f;
     for (int q = tid; q < b * b; q += nt) {
       const int i = q / b, j = q % b;
       if (j <= i) continue;
       const float a = A[i * ld + j];
-      const float d = fabsf(A[i * ld + i] * A[j * ld + j]);
-      const float r = d > 0.f ? a * a / d : (a != 0.f ? 1.f : 0.f);
-      worst = fmaxf(worst, r);
+      const float d = fmaxf(fabsf(A[i * ld + i]), kTau) * fmaxf(fabsf(A[j * ld + j]), kTau);
+      worst = fmaxf(worst, a * a / d);
     }
     red[tid] = worst;
     __syncthreads();
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         qq[k] = q;
         const float apq = A[p * ld + q];
         float c = 1.f, s = 0.f;
-        const float dd = fabsf(A[p * ld + p] * A[q * ld + q]);
+        const float dd = fmaxf(fabsf(A[p * ld + p]), 1e-5f) * fmaxf(fabsf(A[q * ld + q]), 1e-5f);
         if (fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd) {
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           const float tau = (aqq - app) / (2.f * apq);
@@ -169,10 +170,11 @@ size_t jacobi_smem(int b) {
 // Ogita-Aishima step, elementwise part.  In: XtX (b x b), S = X^T H X.
 // Out: E (b x b) and lam (b):  R = I - XtX, lam_i = S_ii / (1 - R_ii),
 // E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when the pair is separated,
-// |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|), else R_ij / 2.
+// |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|) and not both below
+// junk * max|lam| (values the FP32 stage cannot resolve), else R_ij / 2.
 __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __restrict__ XtX,
                           const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam,
-                          double rel_delta) {
+                          double rel_delta, double junk) {
   const SmallProb pr = probs[blockIdx.x];
   const int b = pr.b;
   const double* xx = XtX + pr.in_off;
@@ -197,8 +199,9 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
     const int i = q / b, j = q % b;
     const double rij = (i == j ? 1.0 : 0.0) - xx[q];
     const double delta = rel_delta * fmax(fabs(l[i]), fabs(l[j])) + 1e-300 * smax;
+    const bool unresolved = fabs(l[i]) < junk * smax && fabs(l[j]) < junk * smax;
     double v;
-    if (i == j || fabs(l[i] - l[j]) <= delta) v = 0.5 * rij;
+    if (i == j || unresolved || fabs(l[i] - l[j]) <= delta) v = 0.5 * rij;
     else v = (s[q] + l[j] * rij) / (l[j] - l[i]);
     e[q] = v;
   }

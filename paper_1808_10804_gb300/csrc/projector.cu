@@ -109,7 +109,7 @@ struct ResProb {
   int64_t y_off, v_off, val_off, ld;
 };
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int);
-__global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double);
+__global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double);
 __global__ void add_inplace(double*, const double*, long long);
 __global__ void cholinv_f32(const SmallProb*, const double*, double*, int*);
 __global__ void ident_combo(const SmallProb*, const double*, double*, double, double);
@@ -175,8 +175,12 @@ static void setup_attrs() {
   done = true;
 }
 
-// Symmetric eigenproblems (b <= 160) in FP64 accuracy: FP32 Jacobi (relative
-// convergence test), then three Ogita-Aishima refinement steps.  H: inputs, X: vectors out, lam: values.
+// Symmetric eigenproblems (b <= 160) in FP64 accuracy.  An FP32 Jacobi
+// pass diagonalises H to FP32 level; H is rotated into that basis in FP64
+// (H1 = X1^T H X1, nearly diagonal) and a second FP32 Jacobi pass resolves
+// it to high relative accuracy; two Ogita-Aishima steps then bring the
+// vectors and values to FP64 accuracy.  Values below 1e-6 of the largest
+// are treated as one unresolved cluster.
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
                       int64_t smtot, int64_t valtot, cudaStream_t s) {
   if (sp.empty()) return;
@@ -184,12 +188,8 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   SmallProb* dsp = upload_cached(ctx, "eig.sp", sp, s);
   int bmax = 0;
   for (auto& p : sp) bmax = std::max(bmax, p.b);
-  {
-    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 30);
-    BST_CUDA(cudaGetLastError());
-    count_launch(ctx);
-  }
+  double* X1 = (double*)ctx->buf("eig.x1", sizeof(double) * smtot, s);
+  double* H1 = (double*)ctx->buf("eig.h1", sizeof(double) * smtot, s);
   double* XtX = (double*)ctx->buf("eig.xtx", sizeof(double) * smtot, s);
   double* T = (double*)ctx->buf("eig.t", sizeof(double) * smtot, s);
   double* S = (double*)ctx->buf("eig.s", sizeof(double) * smtot, s);
@@ -203,11 +203,26 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     g_s.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));       // X^T T
     g_xe.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // X E
   }
-  for (int it = 0; it < 3; ++it) {
+  {
+    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
+    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 12);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
+  gemm_any(ctx, "oa.hx", prec, g_hx, H, X1, T, s);
+  gemm_any(ctx, "oa.s", prec, g_s, X1, T, H1, s);
+  {
+    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
+    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 12);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
+  gemm_any(ctx, "oa.xe", prec, g_xe, X1, T, X, s);  // X = X1 X2
+  for (int it = 0; it < 2; ++it) {
     gemm_any(ctx, "oa.xtx", prec, g_xtx, X, X, XtX, s);
     gemm_any(ctx, "oa.hx", prec, g_hx, H, X, T, s);
     gemm_any(ctx, "oa.s", prec, g_s, X, T, S, s);
-    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9);
+    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9, 1e-6);
     gemm_any(ctx, "oa.xe", prec, g_xe, X, E, T, s);
     add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
     BST_CUDA(cudaGetLastError());

@@ -103,15 +103,19 @@ def test_sym_eig_matches_lapack(bst, ctx, n, prec):
     for i in range(batch):
         w_ref, V_ref = np.linalg.eigh(H[i])
         w_ref, V_ref = w_ref[::-1], V_ref[:, ::-1]
-        # eigenvalues to FP64 accuracy relative to the largest
-        assert np.abs(lam[i] - w_ref).max() < 1e-13 * w_ref[0]
-        # leading eigenvectors (well separated ones) up to sign
-        for j in range(min(n, 20)):
+        # every eigenvalue to FP64 accuracy relative to the largest; the
+        # values above 1e-4 of the largest (the ones a projector keeps) to
+        # rounding level
+        assert np.abs(lam[i] - w_ref).max() < 1e-12 * w_ref[0]
+        top = w_ref >= 1e-4 * w_ref[0]
+        assert np.abs(lam[i] - w_ref)[top].max() < 1e-14 * w_ref[0]
+        # their eigenvectors up to sign, where the gap makes them well defined
+        for j in np.nonzero(top)[0]:
             gap = min([abs(w_ref[j] - w_ref[k]) for k in range(n) if k != j] + [np.inf]) / w_ref[0]
-            if gap < 1e-6:
+            if gap < 1e-8:
                 continue
-            d = abs(float(X[i][:, j] @ V_ref[:, j]))
-            assert abs(1 - d) < 1e-12 + 1e-15 / gap ** 2, (j, d, gap)
+            err = min(np.linalg.norm(X[i][:, j] - V_ref[:, j]), np.linalg.norm(X[i][:, j] + V_ref[:, j]))
+            assert err < 1e-13 + 1e-15 / gap, (j, err, gap)
 
 
 @pytest.mark.parametrize("seed", range(6))
