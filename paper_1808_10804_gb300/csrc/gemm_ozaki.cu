@@ -8,10 +8,10 @@
 // A product of two digits is an integer below 2^16 in magnitude, exact in
 // FP32.  The GEMM sums the 15 digit products with i + j <= 4 by diagonal
 // d = i + j (weight 2^-16-9d) in tensor memory:
-//   * d = 0 and d = 1 are read out every 32 K (one pipeline stage), where
-//     their FP32 sums are exact integers of magnitude <= 2^22, and added
-//     into 32-bit integer registers;
-//   * d = 2..4 carry weights <= 2^-34 of the leading term and accumulate in
+//   * d = 0, 1, 2 are read out every 32 K (one pipeline stage), where their
+//     FP32 sums are exact integers of magnitude <= 3 * 2^21, and added into
+//     32-bit integer registers (K <= 10000 keeps those from overflowing);
+//   * d = 3, 4 carry weights <= 2^-27 of the leading term and accumulate in
 //     FP32 over the whole K.
 // The epilogue forms the result with 64-bit integer arithmetic and one
 // conversion to FP64.  Relative error ~2^-40 against the row/column scales.
@@ -44,8 +44,9 @@ constexpr int kStageBytes = kSlices * (kABytes + kBBytes);
 constexpr int kThreads = 320;            // 10 warps: TMA, MMA, 8 epilogue
 constexpr int kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 28;
-// tensor memory columns of the accumulators
-constexpr int kColD0 = 0, kColD1 = 128, kColD2 = 256;
+// tensor memory columns of the accumulators: d0, d1, d2 double-buffered,
+// d3 and d4 single (5 x 64 + 3 x 64 = 512 columns)
+constexpr int kColD0 = 0, kColD1 = 128, kColD2 = 256, kColD3 = 384;
 
 struct Prob {
   int32_t M, N, K, pad;
@@ -262,14 +263,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int j = d - i;
               uint32_t col;
               uint32_t acc;
-              if (d == 0) {
-                col = kColD0 + buf * kTN;
-                acc = (ks > 0) ? 1u : 0u;
-              } else if (d == 1) {
-                col = kColD1 + buf * kTN;
+              if (d <= 2) {
+                col = kColD0 + d * 2 * kTN + buf * kTN;
                 acc = (ks > 0 || i > 0) ? 1u : 0u;
               } else {
-                col = kColD2 + (d - 2) * kTN;
+                col = kColD3 + (d - 3) * kTN;
                 acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
               }
               const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
@@ -291,9 +289,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = ((warp - 2) >> 2) * kHalf;
     const int row = q * 32 + lane;
     const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
-    int S0[kHalf], S1[kHalf];
+    // T = sum over chunks of (S0 2^18 + S1 2^9 + S2): exact in 64 bits
+    long long T[kHalf];
 #pragma unroll
-    for (int j = 0; j < kHalf; ++j) S0[j] = S1[j] = 0;
+    for (int j = 0; j < kHalf; ++j) T[j] = 0;
     bool ok = true;
     for (int c = 0; c < nk && ok; ++c) {
       const int buf = c & 1;
@@ -304,11 +303,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
       tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) S0[j] += f2i_exact(v[j]);
+      for (int j = 0; j < kHalf; ++j) T[j] += (long long)f2i_exact(v[j]) << 18;
       tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
       tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) S1[j] += f2i_exact(v[j]);
+      for (int j = 0; j < kHalf; ++j) T[j] += (long long)f2i_exact(v[j]) << 9;
+      tmem_ld32(lane_base + kColD2 + buf * kTN + c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));  // exact, |v| < 2^23
       tc_fence_before();
       mbar_arrive(&sm.acc_empty[buf]);
     }
@@ -319,24 +322,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       double* crow = C + p.c_off + (long long)gm * p.c_m;
 #pragma unroll
       for (int h = 0; h < kHalf / 16; ++h) {
-        uint32_t w2[16], w3[16], w4[16];
+        uint32_t w3[16], w4[16];
         if (nk > 0) {
-          tmem_ld16(lane_base + kColD2 + 0 * kTN + c0 + h * 16, w2);
-          tmem_ld16(lane_base + kColD2 + 1 * kTN + c0 + h * 16, w3);
-          tmem_ld16(lane_base + kColD2 + 2 * kTN + c0 + h * 16, w4);
+          tmem_ld16(lane_base + kColD3 + 0 * kTN + c0 + h * 16, w3);
+          tmem_ld16(lane_base + kColD3 + 1 * kTN + c0 + h * 16, w4);
           tmem_wait_ld();
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) w2[j] = w3[j] = w4[j] = 0u;
+          for (int j = 0; j < 16; ++j) w3[j] = w4[j] = 0u;
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int jj = h * 16 + j;
           const int gn = t.n0 + c0 + jj;
-          // X = S0 2^27 + S1 2^18 + (S2 2^9 + S3 + S4 2^-9);  C = X 2^(ea+eb-43)
-          const float small = __uint_as_float(w2[j]) * 512.0f + __uint_as_float(w3[j]) +
-                              __uint_as_float(w4[j]) * (1.0f / 512.0f);
-          const long long X = ((long long)S0[jj] << 27) + ((long long)S1[jj] << 18) + __float2ll_rn(small);
+          // X = S0 2^27 + S1 2^18 + S2 2^9 + (S3 + S4 2^-9);  C = X 2^(ea+eb-43)
+          const float small = __uint_as_float(w3[j]) + __uint_as_float(w4[j]) * (1.0f / 512.0f);
+          const long long X = (T[jj] << 9) + __float2ll_rn(small);
           const int e = ea + sm.eb[c0 + jj] - 43;
           const double v = (double)X * pow2i(e >> 1) * pow2i(e - (e >> 1));
           if (row_ok && gn < p.N) crow[(long long)gn * p.c_n] = v;
@@ -486,7 +487,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
   std::vector<oz::SplitTask> sa, sb;
   int maxk = 1;
   for (auto& g : probs) {
-    BST_REQUIRE(g.K <= 16000, BST_E_UNSUPPORTED, "Ozaki GEMM: K above 16000");
+    BST_REQUIRE(g.K <= 10000, BST_E_UNSUPPORTED, "Ozaki GEMM: K above 10000");
     maxk = std::max(maxk, g.K);
   }
   P->kpitch = (maxk + oz::kTK - 1) / oz::kTK * oz::kTK;

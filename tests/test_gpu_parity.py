@@ -106,16 +106,18 @@ def test_sym_eig_matches_lapack(bst, ctx, n, prec):
         # every eigenvalue to FP64 accuracy relative to the largest; the
         # values above 1e-4 of the largest (the ones a projector keeps) to
         # rounding level
-        assert np.abs(lam[i] - w_ref).max() < 1e-12 * w_ref[0]
+        # (the mixed path carries ~44-bit products: a looser bound)
+        tol_all, tol_top = (1e-12, 1e-14) if prec == "fp64" else (1e-11, 1e-12)
+        assert np.abs(lam[i] - w_ref).max() < tol_all * w_ref[0]
         top = w_ref >= 1e-4 * w_ref[0]
-        assert np.abs(lam[i] - w_ref)[top].max() < 1e-14 * w_ref[0]
+        assert np.abs(lam[i] - w_ref)[top].max() < tol_top * w_ref[0]
         # their eigenvectors up to sign, where the gap makes them well defined
         for j in np.nonzero(top)[0]:
             gap = min([abs(w_ref[j] - w_ref[k]) for k in range(n) if k != j] + [np.inf]) / w_ref[0]
             if gap < 1e-8:
                 continue
             err = min(np.linalg.norm(X[i][:, j] - V_ref[:, j]), np.linalg.norm(X[i][:, j] + V_ref[:, j]))
-            assert err < 1e-13 + 1e-15 / gap, (j, err, gap)
+            assert err < (1e-13 + 1e-15 / gap) * (1 if prec == "fp64" else 100), (j, err, gap)
 
 
 @pytest.mark.parametrize("seed", range(6))
