@@ -181,6 +181,28 @@ BST_API bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a,
                         bst_prec prec, double alpha, double beta,
                         bst_layout C, double* c, bst_stream stream);
 
+/* bst_contract for callers that cannot allocate device memory, e.g. code
+ * that runs while a stream is being captured into a CUDA graph, or a process
+ * whose device memory is owned and pre-sized by another runtime.  The paper
+ * has no counterpart: this is a packaging of the same contraction.
+ *
+ * Same arguments and result as bst_contract with prec = BST_FP64, but the
+ * call allocates nothing: its intermediates (relayout and GEMM tables, the
+ * three sector matrices) live in one static device array of 64 MiB that the
+ * library module carries, which every GPU that loads the library holds until
+ * the process exits.  Runs on the current CUDA device.  The first call on a
+ * device looks up that array's device address (once per device); make the
+ * first call before any stream capture begins.  A contraction whose tables
+ * and sector matrices need more than 64 MiB fails with BST_E_SHAPE.  All
+ * calls share the array, so calls that overlap on the GPU (different streams
+ * without ordering between them) race.  The layouts may come from a host-only
+ * context (bst_ctx_create with device -1), whose use allocates no device
+ * memory at all; C must be the layout bst_contract_layout returns. */
+BST_API bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double* a, bst_layout B,
+                                        const double* b, int32_t npairs, const int32_t* legsA,
+                                        const int32_t* legsB, double alpha, double beta,
+                                        bst_layout C, double* c, bst_stream stream);
+
 /* Double layer of a site tensor A[p,l,u,r,d] (Sec. 3.2): a = sum_p A (x) A*,
  * ket and bra legs fused pairwise into rank-4 legs [l,u,r,d] (fused charge
  * q_ket - q_bra).  If R is non-NULL it is a remover R[r,l',s] (Sec. 3.1,

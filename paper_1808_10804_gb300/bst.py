@@ -84,6 +84,7 @@ def lib():
         "bst_contract_layout": [vp, vp, vp, i32, P(i32), P(i32), P(vp)],
         "bst_contract": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), C.c_int, dbl, dbl, vp, vp, vp],
         "bst_double_layer": [vp, vp, vp, vp, vp, P(vp), vp, vp],
+        "bst_contract_noalloc": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), dbl, dbl, vp, vp, vp],
         "bst_svd_projector": [vp, vp, vp, vp, vp, i32, i64, dbl, i32, C.c_int, P(vp), vp, P(vp), vp,
                               P(dbl), P(i64), vp],
         "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
@@ -275,6 +276,13 @@ class Context:
             c = torch.empty(Cl.nnz, dtype=torch.float64, device=a.device)
         _check(lib().bst_contract(self.h, A.h, _ptr(a), B.h, _ptr(b), len(legsA), _i32(legsA), _i32(legsB),
                                   PREC[prec], alpha, beta, Cl.h, _ptr(c), _stream(stream)))
+        return Cl, c
+
+    def contract_noalloc(self, A, a, B, b, legsA, legsB, Cl, c, alpha=1.0, beta=0.0, stream=None):
+        """FP64 contraction into a caller-provided output with no device
+        allocation (scratch in the library's static device array)."""
+        _check(lib().bst_contract_noalloc(self.h, A.h, _ptr(a), B.h, _ptr(b), len(legsA), _i32(legsA),
+                                          _i32(legsB), alpha, beta, Cl.h, _ptr(c), _stream(stream)))
         return Cl, c
 
     def double_layer(self, A, a, R=None, r=None, stream=None):

@@ -322,6 +322,17 @@ bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a, bst_layout B
   });
 }
 
+bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double* a, bst_layout B, const double* b,
+                                int32_t npairs, const int32_t* legsA, const int32_t* legsB, double alpha,
+                                double beta, bst_layout C, double* c, bst_stream stream) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && A && B && C && npairs >= 0, BST_E_ARG, "bad argument");
+    BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
+    std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    contract_noalloc(C_(ctx), L_(A), a, L_(B), b, la, lb, alpha, beta, L_(C), c, (cudaStream_t)stream);
+  });
+}
+
 bst_status bst_double_layer(bst_ctx ctx, bst_layout A, const double* A_data, bst_layout R, const double* R_data,
                             bst_layout* a_layout, double* a, bst_stream stream) {
   return guarded([&] {

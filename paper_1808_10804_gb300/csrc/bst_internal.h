@@ -212,6 +212,7 @@ void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, b
                   double** cmat_out = nullptr);
 
 // relayout.cu
+std::vector<int2> relayout_chunks(const std::vector<RelTask>& t);  // chunk table of a task list
 void launch_relayout(Ctx* ctx, const DevRelayout& r, const double* blk, double* mat, int dir,
                      double alpha, double beta, cudaStream_t s);
 
@@ -245,6 +246,10 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
 
 void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, double* lam, bst_prec prec,
                      cudaStream_t s);
+
+// contract_noalloc.cu
+void contract_noalloc(Ctx* ctx, Layout* A, const double* a, Layout* B, const double* b, const std::vector<int>& la,
+                      const std::vector<int>& lb, double alpha, double beta, Layout* C, double* c, cudaStream_t s);
 
 // ctm.cpp
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,

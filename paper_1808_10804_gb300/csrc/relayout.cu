@@ -32,6 +32,13 @@ ProfScope::~ProfScope() {
 constexpr int kChunk = 2048;
 constexpr int kRelThreads = 256;
 
+std::vector<int2> relayout_chunks(const std::vector<RelTask>& t) {
+  std::vector<int2> ch;
+  for (int i = 0; i < int(t.size()); ++i)
+    for (int s = 0; s < t[i].n; s += kChunk) ch.push_back(make_int2(i, s));
+  return ch;
+}
+
 void DevRelayout::upload(const std::vector<RelTask>& t) {
   free_all();
   ntasks = int(t.size());
