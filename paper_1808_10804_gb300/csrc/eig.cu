@@ -54,25 +54,26 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
   }
   __syncthreads();
   const double inv = 1.0 / hscale;
-  for (int e = tid; e < bp * bp; e += nt) {
-    const int i = e / bp, j = e % bp;
-    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
-    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
-  }
+  for (int i = 0; i < bp; ++i)
+    for (int j = tid; j < bp; j += nt) {
+      A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
+      V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+    }
   __syncthreads();
   const int npair = bp / 2;
+  constexpr float kTau = 1e-5f;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test relative to the diagonal (keeps small eigenvalues
     // accurate) with a floor kTau below which values are not resolved:
-    // max_{i<j} a_ij^2 / (max(|a_ii|, kTau) max(|a_jj|, kTau))
-    constexpr float kTau = 1e-5f;
+    // max_{i<j} a_ij^2 / (max(|a_ii|, kTau) max(|a_jj|, kTau)); one thread
+    // per row
     float worst = 0.f;
-    for (int q = tid; q < b * b; q += nt) {
-      const int i = q / b, j = q % b;
-      if (j <= i) continue;
-      const float a = A[i * ld + j];
-      const float d = fmaxf(fabsf(A[i * ld + i]), kTau) * fmaxf(fabsf(A[j * ld + j]), kTau);
-      worst = fmaxf(worst, a * a / d);
+    for (int i = tid; i < b; i += nt) {
+      const float di = fmaxf(fabsf(A[i * ld + i]), kTau);
+      for (int j = i + 1; j < b; ++j) {
+        const float a = A[i * ld + j];
+        worst = fmaxf(worst, a * a / (di * fmaxf(fabsf(A[j * ld + j]), kTau)));
+      }
     }
     red[tid] = worst;
     __syncthreads();
@@ -91,8 +92,10 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
           p = bp - 1;
           q = r;
         } else {
-          p = (r + k) % (bp - 1);
-          q = (r - k + (bp - 1)) % (bp - 1);
+          p = r + k;
+          if (p >= bp - 1) p -= bp - 1;
+          q = r - k;
+          if (q < 0) q += bp - 1;
         }
         if (p > q) {
           int x = p;
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         qq[k] = q;
         const float apq = A[p * ld + q];
         float c = 1.f, s = 0.f;
-        const float dd = fmaxf(fabsf(A[p * ld + p]), 1e-5f) * fmaxf(fabsf(A[q * ld + q]), 1e-5f);
+        const float dd = fmaxf(fabsf(A[p * ld + p]), kTau) * fmaxf(fabsf(A[q * ld + q]), kTau);
         if (fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd) {
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           const float tau = (aqq - app) / (2.f * apq);
@@ -115,27 +118,31 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         sn[k] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < npair * bp; e += nt) {
-        const int k = e / bp, j = e % bp;
-        const int p = pp[k], q = qq[k];
-        const float c = cs[k], s = sn[k];
-        const float ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
+      // rows: A <- J^T A (one thread per column j)
+      for (int j = tid; j < bp; j += nt) {
+        for (int k = 0; k < npair; ++k) {
+          const float c = cs[k], s = sn[k];
+          if (s == 0.f) continue;
+          const int p = pp[k], q = qq[k];
+          const float ap = A[p * ld + j], aq = A[q * ld + j];
+          A[p * ld + j] = c * ap - s * aq;
+          A[q * ld + j] = s * ap + c * aq;
+        }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = tid; e < npair * bp; e += nt) {
-        const int k = e / bp, i = e % bp;
-        const int p = pp[k], q = qq[k];
-        const float c = cs[k], s = sn[k];
-        const float ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
-        const float vp = V[i * ld + p], vq = V[i * ld + q];
-        V[i * ld + p] = c * vp - s * vq;
-        V[i * ld + q] = s * vp + c * vq;
+      // columns: A <- A J, V <- V J (one thread per row i)
+      for (int i = tid; i < bp; i += nt) {
+        for (int k = 0; k < npair; ++k) {
+          const float c = cs[k], s = sn[k];
+          if (s == 0.f) continue;
+          const int p = pp[k], q = qq[k];
+          const float ap = A[i * ld + p], aq = A[i * ld + q];
+          A[i * ld + p] = c * ap - s * aq;
+          A[i * ld + q] = s * ap + c * aq;
+          const float vp = V[i * ld + p], vq = V[i * ld + q];
+          V[i * ld + p] = c * vp - s * vq;
+          V[i * ld + q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }
@@ -155,10 +162,8 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
   }
   __syncthreads();
   double* X = out + pr.out_off;
-  for (int e = tid; e < b * b; e += nt) {
-    const int i = e / b, jn = e % b;
-    X[(long long)i * b + jn] = double(V[i * ld + order[jn]]);
-  }
+  for (int i = 0; i < b; ++i)
+    for (int jn = tid; jn < b; jn += nt) X[(long long)i * b + jn] = double(V[i * ld + order[jn]]);
   for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]) * hscale;
 }
 
@@ -230,11 +235,13 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
     dsc[i] = d > 0 ? float(1.0 / sqrt(d)) : 1.0f;
   }
   __syncthreads();
-  for (int e = tid; e < b * b; e += nt) {
-    const int i = e / b, j = e % b;
-    const double di = M[(long long)i * b + i], dj = M[(long long)j * b + j];
-    const double sc = (di > 0 && dj > 0) ? 1.0 / sqrt(di * dj) : 1.0;
-    L[i * ld + j] = float(M[e] * sc);
+  for (int i = 0; i < b; ++i) {
+    const double di = M[(long long)i * b + i];
+    for (int j = tid; j < b; j += nt) {
+      const double dj = M[(long long)j * b + j];
+      const double sc = (di > 0 && dj > 0) ? 1.0 / sqrt(di * dj) : 1.0;
+      L[i * ld + j] = float(M[(long long)i * b + j] * sc);
+    }
   }
   __syncthreads();
   // columns whose pivot falls below kDrop (numerically dependent on the
@@ -259,10 +266,10 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
     const float dk = L[k * ld + k];
     for (int i = k + 1 + tid; i < b; i += nt) L[i * ld + k] /= dk;
     __syncthreads();
-    const int m = b - k - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) L[i * ld + j] -= L[i * ld + k] * L[j * ld + k];
+    // trailing update of the lower triangle, one thread per column j
+    for (int j = k + 1 + tid; j < b; j += nt) {
+      const float ljk = L[j * ld + k];
+      for (int i = j; i < b; ++i) L[i * ld + j] -= L[i * ld + k] * ljk;
     }
     __syncthreads();
   }
@@ -282,10 +289,11 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
   // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
   // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
   double* R = out + pr.out_off;
-  for (int e = tid; e < b * b; e += nt) {
-    const int i = e / b, j = e % b;
+  for (int i = 0; i < b; ++i) {
     const double di = M[(long long)i * b + i];
-    R[e] = (drop[i] || drop[j]) ? 0.0 : (di > 0 ? 1.0 / sqrt(di) : 1.0) * double(Li[j * ld + i]);
+    const double si = di > 0 ? 1.0 / sqrt(di) : 1.0;
+    for (int j = tid; j < b; j += nt)
+      R[(long long)i * b + j] = (drop[i] || drop[j]) ? 0.0 : si * double(Li[j * ld + i]);
   }
 }
 
