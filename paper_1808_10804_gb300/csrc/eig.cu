@@ -27,7 +27,7 @@ struct SmallProb {
 };
 
 // One CTA per problem.  A and V live in shared memory as FP32.
-__global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
+__global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
                                                       double* __restrict__ out, double* __restrict__ vals,
                                                       int max_sweeps) {
   extern __shared__ float sh[];
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
   int* pp = (int*)(sn + bp / 2);
   int* qq = pp + bp / 2;
   float* red = (float*)(qq + bp / 2);
-  int* order = (int*)(red + 256);
+  int* order = (int*)(red + 1024);
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* H = in + pr.in_off;
   // scale by the largest diagonal entry (in FP64) so FP32 cannot overflow
@@ -118,9 +118,13 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         sn[k] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A (one thread per column j)
-      for (int j = tid; j < bp; j += nt) {
-        for (int k = 0; k < npair; ++k) {
+      // rows: A <- J^T A; thread (column j, pair group g) applies the
+      // rotations k = g, g + G, ... (disjoint rows, so no conflicts)
+      const int G = nt / bp > 0 ? nt / bp : 1;
+      const int jcol = tid % bp, grp = tid / bp;
+      if (grp < G) {
+        const int j = jcol;
+        for (int k = grp; k < npair; k += G) {
           const float c = cs[k], s = sn[k];
           if (s == 0.f) continue;
           const int p = pp[k], q = qq[k];
@@ -130,9 +134,10 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
         }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J (one thread per row i)
-      for (int i = tid; i < bp; i += nt) {
-        for (int k = 0; k < npair; ++k) {
+      // columns: A <- A J, V <- V J; thread (row i, pair group g)
+      if (grp < G) {
+        const int i = jcol;
+        for (int k = grp; k < npair; k += G) {
           const float c = cs[k], s = sn[k];
           if (s == 0.f) continue;
           const int p = pp[k], q = qq[k];
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_f32(const SmallProb* __restric
 
 size_t jacobi_smem(int b) {
   const int bp = b + (b & 1);
-  return sizeof(float) * (2 * bp * (bp + 1) + bp + 256) + sizeof(int) * (bp + bp);
+  return sizeof(float) * (2 * bp * (bp + 1) + bp + 1024) + sizeof(int) * (bp + bp);
 }
 
 // Ogita-Aishima step, elementwise part.  In: XtX (b x b), S = X^T H X.
@@ -219,7 +224,7 @@ __global__ void add_inplace(double* __restrict__ X, const double* __restrict__ X
 }
 
 // FP32 Cholesky of M (b x b, FP64 in) and Rinv = (L^T)^-1 (upper, FP64 out).
-__global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
+__global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
                                                    double* __restrict__ out, int* err) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
@@ -266,10 +271,17 @@ __global__ void __launch_bounds__(256) cholinv_f32(const SmallProb* __restrict__
     const float dk = L[k * ld + k];
     for (int i = k + 1 + tid; i < b; i += nt) L[i * ld + k] /= dk;
     __syncthreads();
-    // trailing update of the lower triangle, one thread per column j
-    for (int j = k + 1 + tid; j < b; j += nt) {
-      const float ljk = L[j * ld + k];
-      for (int i = j; i < b; ++i) L[i * ld + j] -= L[i * ld + k] * ljk;
+    // trailing update of the lower triangle: thread (column j, row phase ph)
+    // updates rows i = j + ph, j + ph + P, ...
+    const int m = b - k - 1;
+    if (m > 0) {
+      const int P = nt / m > 0 ? nt / m : 1;
+      const int jj = tid % m, ph = tid / m;
+      if (ph < P) {
+        const int j = k + 1 + jj;
+        const float ljk = L[j * ld + k];
+        for (int i = j + ph; i < b; i += P) L[i * ld + j] -= L[i * ld + k] * ljk;
+      }
     }
     __syncthreads();
   }

@@ -205,7 +205,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   }
   {
     ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
@@ -213,7 +213,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   gemm_any(ctx, "oa.s", prec, g_s, X1, T, H1, s);
   {
     ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 256, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
@@ -296,7 +296,10 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     auto orth = [&](const char* tag) {
       // CholQR with an FP32 factor: Y <- Y R^-1 (Y lives in Q)
       gemm_any(ctx, std::string("ss.gram") + tag, prec, g_gram, Q, Q, Msm, s);
-      cholinv_f32<<<int(sp_it.size()), 256, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+      {
+        ProfScope ps(ctx, s, "cholinv_f32", 0.0, 0.0);
+        cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+      }
       count_launch(ctx);
       BST_CUDA(cudaGetLastError());
       gemm_any(ctx, std::string("ss.qr") + tag, prec, g_qr, Q, Rinv, Y, s);
