@@ -233,20 +233,19 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
   float* Li = L + b * ld;   // b x ld, inverse of L
   const double* M = in + pr.in_off;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // scale by the diagonal so the factorisation sees unit diagonal
+  // scale by the diagonal so the factorisation sees unit diagonal; the
+  // scales are formed once per row in FP64 (one square root and division
+  // each), the matrix entries then need two FP64 products
   float* dsc = Li + b * ld;
+  double* dscd = reinterpret_cast<double*>(dsc + b + b);  // float offset 2b(b+1)+2b: 8-byte aligned
   for (int i = tid; i < b; i += nt) {
     const double d = M[(long long)i * b + i];
-    dsc[i] = d > 0 ? float(1.0 / sqrt(d)) : 1.0f;
+    dscd[i] = d > 0 ? 1.0 / sqrt(d) : 1.0;
   }
   __syncthreads();
   for (int i = 0; i < b; ++i) {
-    const double di = M[(long long)i * b + i];
-    for (int j = tid; j < b; j += nt) {
-      const double dj = M[(long long)j * b + j];
-      const double sc = (di > 0 && dj > 0) ? 1.0 / sqrt(di * dj) : 1.0;
-      L[i * ld + j] = float(M[(long long)i * b + j] * sc);
-    }
+    const double si = dscd[i];
+    for (int j = tid; j < b; j += nt) L[i * ld + j] = float(M[(long long)i * b + j] * si * dscd[j]);
   }
   __syncthreads();
   // columns whose pivot falls below kDrop (numerically dependent on the
@@ -302,14 +301,16 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
   // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
   double* R = out + pr.out_off;
   for (int i = 0; i < b; ++i) {
-    const double di = M[(long long)i * b + i];
-    const double si = di > 0 ? 1.0 / sqrt(di) : 1.0;
+    const double si = dscd[i];
     for (int j = tid; j < b; j += nt)
       R[(long long)i * b + j] = (drop[i] || drop[j]) ? 0.0 : si * double(Li[j * ld + i]);
   }
 }
 
-size_t cholinv_smem(int b) { return sizeof(float) * (2 * b * (b + 1) + b) + sizeof(int) * b; }
+size_t cholinv_smem(int b) {
+  // L, Li (b x (b+1) floats), dsc (b floats), drop (b ints), pad, dscd (b doubles)
+  return sizeof(float) * (2 * b * (b + 1) + 2 * b) + sizeof(double) * b;
+}
 
 // out = alpha * I + beta * in (square blocks)
 __global__ void ident_combo(const SmallProb* __restrict__ probs, const double* __restrict__ in, double* __restrict__ out,
