@@ -248,62 +248,131 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
     for (int j = tid; j < b; j += nt) L[i * ld + j] = float(M[(long long)i * b + j] * si * dscd[j]);
   }
   __syncthreads();
-  // columns whose pivot falls below kDrop (numerically dependent on the
-  // earlier ones at FP32 level) are dropped: their row and column of the
-  // factor become the identity and their column of Rinv is zero
+  // Blocked right-looking factorisation with 32-wide panels: warp 0
+  // factors the diagonal block (warp-synchronous), all threads then solve
+  // the panel below it and update the trailing lower triangle.
+  // Columns whose pivot falls below 1e-6 (numerically dependent on earlier
+  // ones at FP32 level) are dropped: their row and column of the factor
+  // become the identity and their column of Rinv is zero.
   int* drop = reinterpret_cast<int*>(dsc + b);
-  for (int k = 0; k < b; ++k) {
-    if (tid == 0) {
-      const float d = L[k * ld + k];
-      drop[k] = !(d > 1e-6f);
-      L[k * ld + k] = drop[k] ? 1.0f : sqrtf(d);
-    }
-    __syncthreads();
-    if (drop[k]) {
-      for (int i = tid; i < b; i += nt) {
-        if (i > k) L[i * ld + k] = 0.f;
-        if (i < k) L[k * ld + i] = 0.f;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int kb = 0; kb < b; kb += 32) {
+    const int w = min(32, b - kb);
+    if (warp == 0) {
+      for (int c = 0; c < w; ++c) {
+        const int k = kb + c;
+        if (lane == 0) {
+          const float d = L[k * ld + k];
+          drop[k] = !(d > 1e-6f);
+          L[k * ld + k] = drop[k] ? 1.0f : sqrtf(d);
+        }
+        __syncwarp();
+        const int dk = drop[k];
+        const float lkk = L[k * ld + k];
+        // column k inside the block, and row k left of the diagonal if dropped
+        for (int i = k + 1 + lane; i < kb + w; i += 32) L[i * ld + k] = dk ? 0.f : L[i * ld + k] / lkk;
+        if (dk)
+          for (int j = kb + lane; j < k; j += 32) L[k * ld + j] = 0.f;
+        __syncwarp();
+        if (!dk)
+          for (int i = k + 1 + lane; i < kb + w; i += 32) {
+            const float lik = L[i * ld + k];
+            for (int j = k + 1; j <= i; ++j) L[i * ld + j] -= lik * L[j * ld + k];
+          }
+        __syncwarp();
       }
-      __syncthreads();
-      continue;
     }
-    const float dk = L[k * ld + k];
-    for (int i = k + 1 + tid; i < b; i += nt) L[i * ld + k] /= dk;
     __syncthreads();
-    // trailing update of the lower triangle: thread (column j, row phase ph)
-    // updates rows i = j + ph, j + ph + P, ...
-    const int m = b - k - 1;
+    // dropped columns of this block: zero their rows left of the block too
+    for (int c = 0; c < w; ++c)
+      if (drop[kb + c])
+        for (int j = tid; j < kb; j += nt) L[(kb + c) * ld + j] = 0.f;
+    // panel solve: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T
+    for (int i = kb + w + tid; i < b; i += nt) {
+      for (int c = 0; c < w; ++c) {
+        const int k = kb + c;
+        if (drop[k]) {
+          L[i * ld + k] = 0.f;
+          continue;
+        }
+        float v = L[i * ld + k];
+        for (int cc = 0; cc < c; ++cc) v -= L[i * ld + kb + cc] * L[k * ld + kb + cc];
+        L[i * ld + k] = v / L[k * ld + k];
+      }
+    }
+    __syncthreads();
+    // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i
+    const int m = b - kb - w;
     if (m > 0) {
       const int P = nt / m > 0 ? nt / m : 1;
       const int jj = tid % m, ph = tid / m;
       if (ph < P) {
-        const int j = k + 1 + jj;
-        const float ljk = L[j * ld + k];
-        for (int i = j + ph; i < b; i += P) L[i * ld + j] -= L[i * ld + k] * ljk;
+        const int j = kb + w + jj;
+        float lj[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) lj[c] = c < w ? L[j * ld + kb + c] : 0.f;
+        for (int i = j + ph; i < b; i += P) {
+          float acc = 0.f;
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc += L[i * ld + kb + (c < w ? c : 0)] * lj[c];
+          L[i * ld + j] -= acc;
+        }
       }
     }
     __syncthreads();
   }
-  // inverse of the lower factor, one column per thread
-  for (int j = tid; j < b; j += nt) {
-    for (int i = 0; i < b; ++i) {
-      if (i < j) {
-        Li[i * ld + j] = 0.f;
-        continue;
+  // inverse of the lower factor, blocked: diagonal 32x32 blocks by one warp
+  // each, then block rows in order, Li[I][J] = -Li[I][I] sum_K L[I][K] Li[K][J]
+  const int nb = (b + 31) / 32;
+  for (int q = tid; q < b * b; q += nt) {
+    const int i = q / b, j = q - i * b;
+    Li[i * ld + j] = 0.f;
+  }
+  __syncthreads();
+  if (warp < nb) {
+    const int kb = warp * 32, w = min(32, b - kb);
+    // column lane of the diagonal block's inverse by forward substitution
+    if (lane < w) {
+      const int j = kb + lane;
+      for (int i = j; i < kb + w; ++i) {
+        float acc = (i == j) ? 1.f : 0.f;
+        for (int k = j; k < i; ++k) acc -= L[i * ld + k] * Li[k * ld + j];
+        Li[i * ld + j] = acc / L[i * ld + i];
       }
-      float acc = (i == j) ? 1.f : 0.f;
-      for (int k = j; k < i; ++k) acc -= L[i * ld + k] * Li[k * ld + j];
-      Li[i * ld + j] = acc / L[i * ld + i];
     }
   }
   __syncthreads();
+  for (int I = 1; I < nb; ++I) {
+    const int ib = I * 32, wi = min(32, b - ib);
+    // T[I][J] = sum_{K=J}^{I-1} L[I][K] Li[K][J] for all J < I, stored in the
+    // (still zero) upper part of Li at [J][I] transposed... kept in registers:
+    // each thread owns one (row i, column j) entry of the block row
+    for (int q = tid; q < wi * ib; q += nt) {
+      const int r = q / ib, j = q - r * ib;
+      const int i = ib + r;
+      const int jb = (j / 32) * 32;
+      float acc = 0.f;
+      for (int k = jb; k < ib; ++k) acc += L[i * ld + k] * Li[k * ld + j];
+      // stash in the upper triangle (unused) of Li: position [j][i]
+      Li[j * ld + i] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < wi * ib; q += nt) {
+      const int r = q / ib, j = q - r * ib;
+      const int i = ib + r;
+      float acc = 0.f;
+      for (int k = ib; k <= i; ++k) acc -= Li[i * ld + k] * Li[j * ld + k];
+      Li[i * ld + j] = acc;
+    }
+    __syncthreads();
+  }
   // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
   // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
   double* R = out + pr.out_off;
   for (int i = 0; i < b; ++i) {
     const double si = dscd[i];
     for (int j = tid; j < b; j += nt)
-      R[(long long)i * b + j] = (drop[i] || drop[j]) ? 0.0 : si * double(Li[j * ld + i]);
+      R[(long long)i * b + j] = (drop[i] || drop[j] || j < i) ? 0.0 : si * double(Li[j * ld + i]);
   }
 }
 
