@@ -255,13 +255,15 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   }
   dV = (double*)ctx->buf("proj.V2", sizeof(double) * std::max<int64_t>(vtot, 1), s);
   double* Q = (double*)ctx->buf("proj.Q", sizeof(double) * std::max<int64_t>(qtot, 1), s);
-  double* Z = (double*)ctx->buf("proj.Z", sizeof(double) * std::max<int64_t>(ztot, 1), s);
   double* Y = (double*)ctx->buf("proj.Y", sizeof(double) * std::max<int64_t>(qtot, 1), s);
+  double* Z = (double*)ctx->buf("proj.Z", sizeof(double) * std::max<int64_t>(ztot, 1), s);
+  double* Z2 = (double*)ctx->buf("proj.Z2", sizeof(double) * std::max<int64_t>(ztot, 1), s);
   double* Msm = (double*)ctx->buf("proj.M", sizeof(double) * std::max<int64_t>(smtot, 1), s);
   double* Rinv = (double*)ctx->buf("proj.Rinv", sizeof(double) * std::max<int64_t>(smtot, 1), s);
   double* Xv = (double*)ctx->buf("proj.X2", sizeof(double) * std::max<int64_t>(smtot, 1), s);
   double* lam = (double*)ctx->buf("proj.lam", sizeof(double) * std::max<int64_t>(valtot, 1), s);
-  std::vector<GemmProb> g_z, g_y, g_gram, g_qr, g_h, g_v, g_direct;
+  // row-major blocks: Q, Y [N x b] at q_off; Z, Z2 [M x b] at z_off
+  std::vector<GemmProb> g_z, g_gz, g_qz, g_y, g_gy, g_qy, g_h, g_v, g_direct, g_polish;
   std::vector<SmallProb> sp_it, sp_all;
   for (auto& x : secs) {
     SmallProb sp{x.b, 0, x.sm_off, x.sm_off, x.val_off};
@@ -274,10 +276,12 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     sp_it.push_back(sp);
     const int b = x.b;
     g_z.push_back(gp(x.M, b, x.N, no, x.N, 1, x.q_off, 1, b, x.z_off, b, 1));          // Z = N Q
-    g_y.push_back(gp(x.N, b, x.M, no, 1, x.N, x.z_off, 1, b, x.q_off, b, 1));          // Y = N^T Z
-    g_gram.push_back(gp(b, b, x.N, x.q_off, 1, b, x.q_off, 1, b, x.sm_off, b, 1));     // Y^T Y
-    g_qr.push_back(gp(x.N, b, b, x.q_off, b, 1, x.sm_off, 1, b, x.q_off, b, 1));       // Y Rinv
-    g_h.push_back(gp(b, b, x.M, x.z_off, 1, b, x.z_off, 1, b, x.sm_off, b, 1));        // Z^T Z
+    g_gz.push_back(gp(b, b, x.M, x.z_off, 1, b, x.z_off, 1, b, x.sm_off, b, 1));       // Z^T Z
+    g_qz.push_back(gp(x.M, b, b, x.z_off, b, 1, x.sm_off, 1, b, x.z_off, b, 1));       // Z2 = Z Rinv
+    g_y.push_back(gp(x.N, b, x.M, no, 1, x.N, x.z_off, 1, b, x.q_off, b, 1));          // Y = N^T Z2
+    g_gy.push_back(gp(b, b, x.N, x.q_off, 1, b, x.q_off, 1, b, x.sm_off, b, 1));       // Y^T Y
+    g_qy.push_back(gp(x.N, b, b, x.q_off, b, 1, x.sm_off, 1, b, x.q_off, b, 1));       // Q = Y Rinv
+    g_h.push_back(gp(b, b, x.M, x.z_off, 1, b, x.z_off, 1, b, x.sm_off, b, 1));        // H = Z^T Z
     g_v.push_back(gp(x.N, b, b, x.q_off, b, 1, x.sm_off, 1, b, x.v_off, b, 1));        // V = Q W
   }
   SmallProb* dsp_it = sp_it.empty() ? nullptr : upload_cached(ctx, "proj.spit", sp_it, s);
@@ -293,31 +297,37 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                                                                               0x5eed0000ull + uint64_t(x.cs->key + 4096));
         count_launch(ctx);
       }
-    auto orth = [&](const char* tag) {
-      // CholQR with an FP32 factor: Y <- Y R^-1 (Y lives in Q)
-      gemm_any(ctx, std::string("ss.gram") + tag, prec, g_gram, Q, Q, Msm, s);
-      {
-        ProfScope ps(ctx, s, "cholinv_f32", 0.0, 0.0);
-        cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
-      }
-      count_launch(ctx);
+    auto cholinv = [&]() {
+      ProfScope ps(ctx, s, "cholinv_f32", 0.0, 0.0);
+      cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
       BST_CUDA(cudaGetLastError());
-      gemm_any(ctx, std::string("ss.qr") + tag, prec, g_qr, Q, Rinv, Y, s);
-      std::swap(Q, Y);
+      count_launch(ctx);
     };
+    // CholQR with an FP32 factor after each half step: the blocks N Q and
+    // N^T Z carry the condition number sigma_1/sigma_b once, not squared
     for (int t = 0; t < iters; ++t) {
       gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
-      gemm_any(ctx, "ss.y", prec, g_y, Nm, Z, Y, s);
-      std::swap(Q, Y);
-      orth("");
+      gemm_any(ctx, "ss.gz", prec, g_gz, Z, Z, Msm, s);
+      cholinv();
+      gemm_any(ctx, "ss.qz", prec, g_qz, Z, Rinv, Z2, s);
+      gemm_any(ctx, "ss.y", prec, g_y, Nm, Z2, Y, s);
+      gemm_any(ctx, "ss.gy", prec, g_gy, Y, Y, Msm, s);
+      cholinv();
+      gemm_any(ctx, "ss.qy", prec, g_qy, Y, Rinv, Q, s);
     }
-    // second CholQR pass and a first-order polish: orthonormal to FP64
-    orth("2");
-    gemm_any(ctx, "ss.gram3", prec, g_gram, Q, Q, Msm, s);
-    ident_combo<<<int(sp_it.size()), 256, 0, s>>>(dsp_it, Msm, Rinv, 1.5, -0.5);
-    count_launch(ctx);
-    gemm_any(ctx, "ss.qr3", prec, g_qr, Q, Rinv, Y, s);
-    std::swap(Q, Y);
+    // second CholQR pass and two first-order polishes: orthonormal to FP64
+    gemm_any(ctx, "ss.gy", prec, g_gy, Q, Q, Msm, s);
+    cholinv();
+    gemm_any(ctx, "ss.qy", prec, g_qy, Q, Rinv, Y, s);
+    for (int r = 0; r < 2; ++r) {
+      double* src = (r == 0) ? Y : Q;
+      double* dst = (r == 0) ? Q : Y;
+      gemm_any(ctx, "ss.gy", prec, g_gy, src, src, Msm, s);
+      ident_combo<<<int(sp_it.size()), 256, 0, s>>>(dsp_it, Msm, Rinv, 1.5, -0.5);
+      count_launch(ctx);
+      gemm_any(ctx, "ss.qy", prec, g_qy, src, Rinv, dst, s);
+    }
+    std::swap(Q, Y);  // the polished block is in Y
     // Rayleigh-Ritz: H = (N Q)^T (N Q)
     gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
     gemm_any(ctx, "ss.h", prec, g_h, Z, Z, Msm, s);
