@@ -292,3 +292,13 @@ def test_full_move_ozaki_d6chi72(bst, ctx):
     ctx.ctm_move(env, aL, ad, 4, cfg["chi"], prec="ozaki")
     ctx.sync()
     compare_env(env, ref, ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4"), TOL_MOVE_OZ)
+
+
+def test_full_move_fp64_d6chi72(bst, ctx):
+    """The benchmark step on the plain FP64 path: every direction's renewed
+    tensors within 1e-12 of the FP64 oracle."""
+    cfg, aL, ad, env = gpu_env(bst, ctx, "d6chi72", 72)
+    ref = octm.full_move(oracle_net("d6chi72"), cfg["chi"])
+    ctx.ctm_move(env, aL, ad, 4, cfg["chi"], prec="fp64")
+    ctx.sync()
+    compare_env(env, ref, ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4"), TOL64)
