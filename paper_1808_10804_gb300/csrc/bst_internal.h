@@ -131,6 +131,18 @@ struct GemmProb {
   int64_t a_m, a_k, b_n, b_k, c_m, c_n;
 };
 
+// 64-bit FNV-1a hash of a problem list (plan-cache key)
+inline uint64_t probs_hash(const std::vector<GemmProb>& probs) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(probs.data());
+  const size_t n = probs.size() * sizeof(GemmProb);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h ^ (uint64_t(probs.size()) << 1);
+}
+
 struct DevGemm {
   GemmProb* probs = nullptr;
   int32_t* tile_prob = nullptr;   // tile -> problem

@@ -581,12 +581,7 @@ void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<Ge
                           const double* B, double* C, cudaStream_t s) {
   static std::mutex mu;
   static std::map<std::string, std::unique_ptr<OzakiPlan>> cache;
-  std::string key = std::to_string((uintptr_t)ctx) + "/" + tag + "/";
-  for (auto& g : probs)
-    key += std::to_string(g.M) + "," + std::to_string(g.N) + "," + std::to_string(g.K) + "," +
-           std::to_string(g.a_off) + "," + std::to_string(g.a_m) + "," + std::to_string(g.a_k) + "," +
-           std::to_string(g.b_off) + "," + std::to_string(g.b_n) + "," + std::to_string(g.b_k) + "," +
-           std::to_string(g.c_off) + "," + std::to_string(g.c_m) + "," + std::to_string(g.c_n) + ";";
+  const std::string key = std::to_string((uintptr_t)ctx) + "/" + tag + "/" + std::to_string(probs_hash(probs));
   OzakiPlan* P;
   {
     std::lock_guard<std::mutex> g(mu);

@@ -130,13 +130,7 @@ static GemmProb gp(int M, int N, int K, int64_t ao, int64_t am, int64_t ak, int6
 }
 
 static std::string probs_key(const std::vector<GemmProb>& probs) {
-  std::string k;
-  for (auto& g : probs)
-    k += std::to_string(g.M) + "," + std::to_string(g.N) + "," + std::to_string(g.K) + "," +
-         std::to_string(g.a_off) + "," + std::to_string(g.a_m) + "," + std::to_string(g.a_k) + "," +
-         std::to_string(g.b_off) + "," + std::to_string(g.b_n) + "," + std::to_string(g.b_k) + "," +
-         std::to_string(g.c_off) + "," + std::to_string(g.c_m) + "," + std::to_string(g.c_n) + ";";
-  return k;
+  return std::to_string(probs_hash(probs));
 }
 
 // FP64-accurate grouped GEMM in the requested arithmetic.
