@@ -212,7 +212,7 @@ class Context:
     def launches(self):
         return lib().bst_ctx_launch_count(self.h)
 
-    def set_projector(self, method="subspace", iters=14):
+    def set_projector(self, method="subspace", iters=9):
         m = {"gesvd": 0, "subspace": 1}[method]
         _check(lib().bst_ctx_set_projector(self.h, m, iters))
 

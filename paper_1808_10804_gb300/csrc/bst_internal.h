@@ -199,7 +199,7 @@ struct Ctx {
   std::atomic<int64_t> launches{0};
   void* cusolver = nullptr;
   int proj_method = 1;   // 0: cuSOLVER gesvd per sector, 1: subspace iteration + small eigensolver
-  int proj_iters = 14;   // subspace iterations
+  int proj_iters = 9;    // subspace iterations
   double* d_scratch_small = nullptr;
   ~Ctx();
   void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
