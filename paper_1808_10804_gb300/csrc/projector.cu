@@ -199,7 +199,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   }
   {
     ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 5);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
@@ -207,7 +207,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   gemm_any(ctx, "oa.s", prec, g_s, X1, T, H1, s);
   {
     ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 5);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
