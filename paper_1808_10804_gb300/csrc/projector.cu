@@ -230,6 +230,10 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
 // sector needs more candidates than the small eigensolver holds.
 static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int64_t chi, bst_prec prec, int iters,
                              double*& dV, std::vector<double>& hSig, cudaStream_t s) {
+  // The iterations only have to converge the subspace, so they run in the
+  // call's arithmetic; the Rayleigh-Ritz stage fixes the individual vectors,
+  // whose error is amplified by 1/gap, and always runs in FP64.
+  const bst_prec rr = BST_FP64;
   int64_t vtot = 0, qtot = 0, ztot = 0, smtot = 0, valtot = 0;
   for (auto& x : secs) {
     x.direct = x.N <= kEigMax;
@@ -323,13 +327,13 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     }
     std::swap(Q, Y);  // the polished block is in Y
     // Rayleigh-Ritz: H = (N Q)^T (N Q)
-    gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
-    gemm_any(ctx, "ss.h", prec, g_h, Z, Z, Msm, s);
+    gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
+    gemm_any(ctx, "ss.h", rr, g_h, Z, Z, Msm, s);
   }
-  gemm_any(ctx, "ss.direct", prec, g_direct, Nm, Nm, Msm, s);
-  small_eig(ctx, prec, sp_all, Msm, Xv, lam, smtot, valtot, s);
+  gemm_any(ctx, "ss.direct", rr, g_direct, Nm, Nm, Msm, s);
+  small_eig(ctx, rr, sp_all, Msm, Xv, lam, smtot, valtot, s);
   // V = Q W (iterative) or W (direct)
-  if (!g_v.empty()) gemm_any(ctx, "ss.v", prec, g_v, Q, Xv, dV, s);
+  if (!g_v.empty()) gemm_any(ctx, "ss.v", rr, g_v, Q, Xv, dV, s);
   for (auto& x : secs)
     if (x.direct)
       BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
@@ -607,7 +611,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     // Ur = N V_k  ([M x k]; V row-major N x c)
     gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
   }
-  gemm_any(ctx, "proj.u", prec, gu, Nm, dV, Ur, s);
+  gemm_any(ctx, "proj.u", BST_FP64, gu, Nm, dV, Ur, s);  // left vectors in FP64 (see factors_subspace)
   int64_t uo = 0, vo = 0;
   for (size_t i = 0; i < secs.size(); ++i) {
     const PSec& x = secs[i];
