@@ -464,6 +464,7 @@ struct OzakiPlan {
   int *eA = nullptr, *eB = nullptr;
   CUtensorMap mapA, mapB;
   double flops = 0;
+  double split_bytes = 0;  // FP64 read + 5 BF16 digits written per element, exponent per row
   bool zero_only = false;  // every problem has K == 0
   std::vector<GemmProb> zprobs;  // K == 0 problems, written as zeros
   ~OzakiPlan() {
@@ -510,6 +511,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
     for (int m0 = 0; m0 < g.M; m0 += oz::kTM)
       for (int n0 = 0; n0 < g.N; n0 += oz::kTN) ht.push_back({pi, m0, n0, 0});
     P->flops += 2.0 * double(g.M) * g.N * g.K;
+    P->split_bytes += double(g.M + g.N) * g.K * (8.0 + 2.0 * oz::kSlices) + 4.0 * (g.M + g.N);
   }
   P->nprobs = int(hp.size());
   P->ntiles = int(ht.size());
@@ -551,7 +553,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
 static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s) {
   if (P->ntiles == 0) return;
   {
-    ProfScope ps(ctx, s, "split_bf16", 0.0, 0.0);
+    ProfScope ps(ctx, s, "split_bf16", 0.0, P->split_bytes);
     const int wa = P->rowsA, wb = P->rowsB;
     if (wa) oz::ozaki_split_kernel<<<(wa + 7) / 8, 256, 0, s>>>(P->d_sa, P->nsa, A, P->SA, P->eA, P->rowsA,
                                                                P->kpitch);

@@ -197,8 +197,12 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     g_s.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));       // X^T T
     g_xe.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // X E
   }
+  // nominal work of one Jacobi launch at its sweep limit: per sweep b-1
+  // rounds of b/2 rotations, each touching 2 rows and 2 columns of A and V
+  double jac_flops = 0;
+  for (auto& p : sp) jac_flops += 7.0 * double(p.b) * p.b * 18.0 * p.b / 2.0;
   {
-    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
+    ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
     jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
@@ -206,7 +210,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   gemm_any(ctx, "oa.hx", prec, g_hx, H, X1, T, s);
   gemm_any(ctx, "oa.s", prec, g_s, X1, T, H1, s);
   {
-    ProfScope ps(ctx, s, "jacobi_f32", 0.0, 0.0);
+    ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
     jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
@@ -295,8 +299,10 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                                                                               0x5eed0000ull + uint64_t(x.cs->key + 4096));
         count_launch(ctx);
       }
+    double chol_flops = 0;
+    for (auto& x : sp_it) chol_flops += 2.0 * 2.0 * double(x.b) * x.b * x.b / 3.0;  // factor + inverse, FMA = 2
     auto cholinv = [&]() {
-      ProfScope ps(ctx, s, "cholinv_f32", 0.0, 0.0);
+      ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
       cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
       BST_CUDA(cudaGetLastError());
       count_launch(ctx);
