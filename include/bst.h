@@ -203,6 +203,30 @@ BST_API bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double*
                                         const int32_t* legsB, double alpha, double beta,
                                         bst_layout C, double* c, bst_stream stream);
 
+/* A batch of independent contractions (Sec. 2: contracting two symmetric
+ * tensors is a set of independent dense block products, so products from
+ * many contractions can share one launch):
+ *     c[i] = alpha * contract(a[i], b[i]) + beta * c[i],   i < nbatch,
+ * every one over the same leg pairs (legsA, legsB), each exactly as
+ * bst_contract would compute it.  A, a, B, b, C, c are HOST arrays of
+ * nbatch entries: layouts (A[i], B[i] any structure; C[i] the layout
+ * bst_contract_layout returns for A[i], B[i]) and device data pointers.
+ * All sector matrices of all contractions go through one gather launch per
+ * operand, one grouped GEMM (FP64 or the mixed-precision tensor-core GEMM,
+ * per `prec`) and one scatter, whatever nbatch is.  The first call with a
+ * given list of layouts builds and caches the plan, and the first call with
+ * a given list of data pointers uploads a pointer table (both allocate and
+ * synchronise); a repeated call launches four kernels (six for BST_OZAKI:
+ * the two operand splits come in addition) and nothing else, so it may be
+ * captured into a CUDA graph and replayed.
+ * The c[i] must not overlap one another or any input (they are written
+ * concurrently).  Errors: BST_E_ARG (NULL entries, nbatch < 1),
+ * BST_E_SYMMETRY (a leg pair does not match), BST_E_SHAPE (C[i] wrong). */
+BST_API bst_status bst_contract_batched(bst_ctx ctx, int32_t nbatch, const bst_layout* A, const double* const* a,
+                                        const bst_layout* B, const double* const* b, int32_t npairs,
+                                        const int32_t* legsA, const int32_t* legsB, bst_prec prec, double alpha,
+                                        double beta, const bst_layout* C, double* const* c, bst_stream stream);
+
 /* Double layer of a site tensor A[p,l,u,r,d] (Sec. 3.2): a = sum_p A (x) A*,
  * ket and bra legs fused pairwise into rank-4 legs [l,u,r,d] (fused charge
  * q_ket - q_bra).  If R is non-NULL it is a remover R[r,l',s] (Sec. 3.1,

@@ -85,6 +85,8 @@ def lib():
         "bst_contract": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), C.c_int, dbl, dbl, vp, vp, vp],
         "bst_double_layer": [vp, vp, vp, vp, vp, P(vp), vp, vp],
         "bst_contract_noalloc": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), dbl, dbl, vp, vp, vp],
+        "bst_contract_batched": [vp, i32, P(vp), P(vp), P(vp), P(vp), i32, P(i32), P(i32), C.c_int, dbl, dbl,
+                                 P(vp), P(vp), vp],
         "bst_svd_projector": [vp, vp, vp, vp, vp, i32, i64, dbl, i32, C.c_int, P(vp), vp, P(vp), vp,
                               P(dbl), P(i64), vp],
         "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
@@ -284,6 +286,22 @@ class Context:
         _check(lib().bst_contract_noalloc(self.h, A.h, _ptr(a), B.h, _ptr(b), len(legsA), _i32(legsA),
                                           _i32(legsB), alpha, beta, Cl.h, _ptr(c), _stream(stream)))
         return Cl, c
+
+    def contract_batched(self, As, as_, Bs, bs, legsA, legsB, prec="fp64", alpha=1.0, beta=0.0, Cls=None,
+                         cs=None, stream=None):
+        """Independent contractions cs[i] = alpha*As[i]·Bs[i] + beta*cs[i] in
+        one launch per stage (gather A, gather B, grouped GEMM, scatter)."""
+        n = len(As)
+        if Cls is None:
+            Cls = [self.contract_layout(A, B, legsA, legsB) for A, B in zip(As, Bs)]
+        if cs is None:
+            cs = [torch.empty(L.nnz, dtype=torch.float64, device=a.device) for L, a in zip(Cls, as_)]
+        arr = C.c_void_p * n
+        _check(lib().bst_contract_batched(
+            self.h, n, arr(*[L.h for L in As]), arr(*[_ptr(x) for x in as_]), arr(*[L.h for L in Bs]),
+            arr(*[_ptr(x) for x in bs]), len(legsA), _i32(legsA), _i32(legsB), PREC[prec], alpha, beta,
+            arr(*[L.h for L in Cls]), arr(*[_ptr(x) for x in cs]), _stream(stream)))
+        return Cls, cs
 
     def double_layer(self, A, a, R=None, r=None, stream=None):
         h = C.c_void_p()

@@ -41,6 +41,8 @@ static bst_status guarded(F&& f) {
 
 namespace bst {
 Ctx::~Ctx() {
+  bplans.clear();
+  ozplans.clear();
   cplans.clear();
   rplans.clear();
   for (auto& kv : gplans) kv.second->free_all();
@@ -330,6 +332,33 @@ bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double* a, bst_
     BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
     std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
     contract_noalloc(C_(ctx), L_(A), a, L_(B), b, la, lb, alpha, beta, L_(C), c, (cudaStream_t)stream);
+  });
+}
+
+bst_status bst_contract_batched(bst_ctx ctx, int32_t nbatch, const bst_layout* A, const double* const* a,
+                                const bst_layout* B, const double* const* b, int32_t npairs, const int32_t* legsA,
+                                const int32_t* legsB, bst_prec prec, double alpha, double beta, const bst_layout* C,
+                                double* const* c, bst_stream stream) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && nbatch >= 1 && A && a && B && b && C && c && npairs >= 0, BST_E_ARG, "bad argument");
+    BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
+    BST_REQUIRE(prec == BST_FP64 || prec == BST_OZAKI, BST_E_ARG, "unknown precision mode");
+    Ctx* cx = C_(ctx);
+    set_dev(cx);
+    std::vector<Layout*> la_(nbatch), lb_(nbatch), lc_(nbatch);
+    std::vector<const double*> pa(nbatch), pb(nbatch);
+    std::vector<double*> pc(nbatch);
+    for (int i = 0; i < nbatch; ++i) {
+      BST_REQUIRE(A[i] && B[i] && C[i], BST_E_ARG, "layout handle is NULL");
+      la_[i] = L_(A[i]);
+      lb_[i] = L_(B[i]);
+      lc_[i] = L_(C[i]);
+      pa[i] = a[i];
+      pb[i] = b[i];
+      pc[i] = c[i];
+    }
+    std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    contract_batched(cx, la_, pa, lb_, pb, la, lb, prec, alpha, beta, lc_, pc, (cudaStream_t)stream);
   });
 }
 

@@ -154,6 +154,7 @@ struct DevGemm {
 };
 
 struct OzakiPlan;  // mixed-precision GEMM plan (gemm_ozaki.cu)
+struct BatchPlan;  // batched-contraction plan (batch.cu)
 
 // Contraction plan (cached per (A, B, pairs)).
 struct ContractPlan {
@@ -195,6 +196,8 @@ struct Ctx {
   std::map<std::string, std::unique_ptr<DevRelayout>> rplans;
   std::map<std::string, DevBuf> bufs;
   std::map<std::string, std::unique_ptr<DevGemm>> gplans;
+  std::map<std::string, std::shared_ptr<BatchPlan>> bplans;  // deleter bound in batch.cu
+  std::map<std::string, std::shared_ptr<OzakiPlan>> ozplans;  // deleter bound in gemm_ozaki.cu
   int* d_err = nullptr;                     // device error word
   std::atomic<int64_t> launches{0};
   void* cusolver = nullptr;
@@ -262,6 +265,12 @@ void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, dou
 // contract_noalloc.cu
 void contract_noalloc(Ctx* ctx, Layout* A, const double* a, Layout* B, const double* b, const std::vector<int>& la,
                       const std::vector<int>& lb, double alpha, double beta, Layout* C, double* c, cudaStream_t s);
+
+// batch.cu
+void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector<const double*>& a,
+                      const std::vector<Layout*>& B, const std::vector<const double*>& b, const std::vector<int>& la,
+                      const std::vector<int>& lb, bst_prec prec, double alpha, double beta,
+                      const std::vector<Layout*>& C, const std::vector<double*>& c, cudaStream_t s);
 
 // ctm.cpp
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,

@@ -581,19 +581,19 @@ void ozaki_free(OzakiPlan* oz) { delete oz; }
 
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
                           const double* B, double* C, cudaStream_t s) {
-  static std::mutex mu;
-  static std::map<std::string, std::unique_ptr<OzakiPlan>> cache;
-  const std::string key = std::to_string((uintptr_t)ctx) + "/" + tag + "/" + std::to_string(probs_hash(probs));
+  // plans live in the context (freed with it), keyed by caller tag and problem list
+  const std::string key = tag + "/" + std::to_string(probs_hash(probs));
   OzakiPlan* P;
   {
-    std::lock_guard<std::mutex> g(mu);
-    auto it = cache.find(key);
-    if (it == cache.end()) {
-      P = build_plan(ctx, probs);
-      cache[key].reset(P);
-    } else {
-      P = it->second.get();
-    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->ozplans.find(key);
+    P = it == ctx->ozplans.end() ? nullptr : it->second.get();
+  }
+  if (!P) {
+    std::shared_ptr<OzakiPlan> np(build_plan(ctx, probs));
+    P = np.get();
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->ozplans[key] = std::move(np);
   }
   run_plan(ctx, P, A, B, C, s);
 }

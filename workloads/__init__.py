@@ -22,7 +22,7 @@ import numpy as np
 
 # tensor ids for the per-tensor random streams
 TID = {"A": 0, "R": 1, "C1": 2, "C2": 3, "C3": 4, "C4": 5,
-       "T1": 6, "T2": 7, "T3": 8, "T4": 9, "B": 10}
+       "T1": 6, "T2": 7, "T3": 8, "T4": 9, "B": 10, "X2": 11}
 IN, OUT = 1, -1
 
 
@@ -109,16 +109,16 @@ def u1_config(name):
     }
 
 
-def batched_u1_configs(count=64, seed=0):
+def batched_u1_configs(count=64, seed=0, d_range=(4, 8), chis=(32, 64, 96, 128)):
     """Recipe for the batch of independent corner contractions: bond
-    dimension D ~ U{4..8}, chi ~ U{32,64,96,128}; odd leg {-1,+1} and even
+    dimension D ~ U{d_range}, chi ~ U{chis}; odd leg {-1,+1} and even
     leg {-2,0,2} get a seeded random composition summing to D; the env
     bond is the Gaussian split of chi with a +-1 symmetric jitter."""
     out = []
     for i in range(count):
         rng = np.random.default_rng([seed, 1000 + i])
-        D = int(rng.integers(4, 9))
-        chi = int(rng.choice([32, 64, 96, 128]))
+        D = int(rng.integers(d_range[0], d_range[1] + 1))
+        chi = int(rng.choice(list(chis)))
         a = int(rng.integers(1, D))            # odd leg: a states at -1, D-a at +1
         c0 = int(rng.integers(1, D - 1)) if D > 2 else 1   # even leg: c0 at 0, rest split over +-2
         rest = D - c0
@@ -135,7 +135,17 @@ def batched_u1_configs(count=64, seed=0):
             if xd[j] + jit > 0 and xd[-1 - j] + jit > 0:
                 xd[j] += jit
                 xd[-1 - j] += jit
-        out.append({"name": f"batch{i}", "seed": i, "D": D, "chi": chi,
+        out.append({"name": f"batch{i}", "seed": seed * 100000 + i, "D": D, "chi": chi,
                     "phys": ((-1, 1), (1, 1)), "odd": odd, "even": even,
                     "x": (tuple(xq), tuple(xd))})
     return out
+
+
+def batched_site_legs(cfg):
+    """Site tensor A[p, l, u, r, d] of one batched instance (p, l, u
+    incoming; r, d outgoing).  The instance contracts the corner-edge-edge
+    block X2[k_u, x_r, k_l, x_d] (legs: the duals of the double layer's u
+    and l legs, and two outgoing env bonds; values from stream "X2") with
+    the double layer a[k_l, k_u, k_r, k_d] of A over (k_u, k_l)."""
+    return [leg(IN, *cfg["phys"]), leg(IN, *cfg["odd"]), leg(IN, *cfg["even"]),
+            leg(OUT, *cfg["even"]), leg(OUT, *cfg["even"])]
