@@ -206,7 +206,8 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
            "contractions_per_s": len(inst) / (ms / 1e3), "ms_per_step": ms, "fp64_path_ms_per_step": ms64,
            "algorithmic_gflop": flops / 1e9, "rel_err_vs_fp64_path": err, "gpu_launches": int(nl),
            "timing": "median of CUDA-graph replays, L2 flushed between replays",
-           "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}}
+           "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()},
+           "autotune": [ln.split(" ", 2)[2] for ln in ctx.tuning_log().splitlines() if "chosen" in ln]}
     tms = prof[gk][1] / 1e3
     if prec == "ozaki":
         a = 15.0 * flops / tms / 1e12

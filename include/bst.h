@@ -107,6 +107,18 @@ BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
  *   BST_PROJ_GESVD: full FP64 SVD of every sector with cuSOLVER gesvd. */
 typedef enum { BST_PROJ_GESVD = 0, BST_PROJ_SUBSPACE = 1 } bst_proj_method;
 BST_API bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters);
+/* Autotuner of bst_contract_batched (on by default).  When on, the first
+ * call of a new batch (per arithmetic) times every candidate schedule on
+ * the call's own data, keeps the fastest for all later calls and appends
+ * one line per timing to the context's tuning log.  Candidates: elements
+ * per CTA of the gather and scatter launches (1024, 2048, 4096, 8192) and
+ * the GEMM tile schedule (problem order, longest K first, or - for the
+ * tensor-core GEMM - column tiles outer).  The schedule does not change any
+ * result bit.  Tuning writes only the plan's own buffers. */
+BST_API bst_status bst_ctx_set_autotune(bst_ctx ctx, int32_t enable);
+/* Copies the tuning log (NUL-terminated, truncated to cap bytes) into buf
+ * and its full length into *len (either may be NULL). */
+BST_API bst_status bst_ctx_tuning_log(bst_ctx ctx, char* buf, size_t cap, size_t* len);
 /* Per-kernel-class timing: enable != 0 starts recording a CUDA event pair
  * around every launch of the library's kernels on its stream (and clears
  * earlier records); 0 stops.  Synchronises the device. */

@@ -71,6 +71,8 @@ def lib():
         "bst_ctx_launch_count": [vp],
         "bst_ctx_profile": [vp, i32],
         "bst_ctx_set_projector": [vp, i32, i32],
+        "bst_ctx_set_autotune": [vp, i32],
+        "bst_ctx_tuning_log": [vp, C.c_char_p, C.c_size_t, P(C.c_size_t)],
         "bst_ctx_profile_read": [vp, i32, C.c_char_p, i32, P(i64), P(dbl), P(dbl), P(dbl)],
         "bst_layout_create": [vp, C.c_int, i32, P(_Leg), P(vp)],
         "bst_layout_retain": [vp],
@@ -217,6 +219,16 @@ class Context:
     def set_projector(self, method="subspace", iters=9):
         m = {"gesvd": 0, "subspace": 1}[method]
         _check(lib().bst_ctx_set_projector(self.h, m, iters))
+
+    def set_autotune(self, enable=True):
+        _check(lib().bst_ctx_set_autotune(self.h, 1 if enable else 0))
+
+    def tuning_log(self):
+        n = C.c_size_t()
+        _check(lib().bst_ctx_tuning_log(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        _check(lib().bst_ctx_tuning_log(self.h, buf, n.value + 1, None))
+        return buf.value.decode()
 
     def profile(self, enable=True):
         _check(lib().bst_ctx_profile(self.h, 1 if enable else 0))

@@ -146,6 +146,26 @@ bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters) {
   });
 }
 
+bst_status bst_ctx_set_autotune(bst_ctx ctx, int32_t enable) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    C_(ctx)->autotune = enable != 0;
+  });
+}
+
+bst_status bst_ctx_tuning_log(bst_ctx ctx, char* buf, size_t cap, size_t* len) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    const std::string& log = C_(ctx)->tune_log;
+    if (len) *len = log.size();
+    if (buf && cap > 0) {
+      const size_t n = std::min(cap - 1, log.size());
+      std::memcpy(buf, log.data(), n);
+      buf[n] = 0;
+    }
+  });
+}
+
 bst_status bst_ctx_profile(bst_ctx ctx, int32_t enable) {
   return guarded([&] {
     BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");

@@ -29,7 +29,15 @@ struct BatchRel {
   BatchTask* tasks = nullptr;
   int2* chunks = nullptr;
   int nchunks = 0;
+  int chunk = 2048;  // elements per CTA
   double elems = 0;
+  std::vector<BatchTask> host;
+  void free_all() {
+    cudaFree(tasks);
+    cudaFree(chunks);
+    tasks = nullptr;
+    chunks = nullptr;
+  }
 };
 
 struct BatchPlan {
@@ -38,6 +46,10 @@ struct BatchPlan {
   BatchRel ra, rb, rc;
   std::vector<GemmProb> probs;
   DevGemm g;
+  // schedule chosen by the autotuner (defaults until tuned)
+  bool tuned_rel = false;
+  bool tuned[2] = {false, false};  // per arithmetic (BST_FP64, BST_OZAKI)
+  int order[2] = {0, 0};
   // data pointers (a[0..n), b[0..n), c[0..n)) -> device copy of that table
   std::map<std::vector<const void*>, double**> tables;
   // the plan's own sector-matrix buffers: a captured graph of this batch
@@ -47,26 +59,23 @@ struct BatchPlan {
     cudaFree(Am);
     cudaFree(Bm);
     cudaFree(Cm);
-    cudaFree(ra.tasks);
-    cudaFree(ra.chunks);
-    cudaFree(rb.tasks);
-    cudaFree(rb.chunks);
-    cudaFree(rc.tasks);
-    cudaFree(rc.chunks);
+    ra.free_all();
+    rb.free_all();
+    rc.free_all();
     for (auto& kv : tables) cudaFree(kv.second);
     g.free_all();
   }
 };
 
-constexpr int kBatchChunk = 2048;
 constexpr int kBatchThreads = 256;
+constexpr int kChunkChoices[] = {1024, 2048, 4096, 8192};
 
 // Same element mapping as relayout_kernel, with a per-task base pointer.
 __global__ void __launch_bounds__(kBatchThreads) relayout_batch_kernel(const BatchTask* __restrict__ tasks,
                                                                        const int2* __restrict__ chunks,
                                                                        double* const* __restrict__ bases,
                                                                        double* mat, int dir, double alpha,
-                                                                       double beta) {
+                                                                       double beta, int chunk) {
   const int2 c = chunks[blockIdx.x];
   const BatchTask& bt = tasks[c.x];
   const RelTask& t = bt.t;
@@ -79,7 +88,7 @@ __global__ void __launch_bounds__(kBatchThreads) relayout_batch_kernel(const Bat
     shape[i] = i < r ? t.shape[i] : 1;
     ms[i] = i < r ? t.mstride[i] : 0;
   }
-  const int end = min(t.n, c.y + kBatchChunk);
+  const int end = min(t.n, c.y + chunk);
   for (int e = c.y + threadIdx.x; e < end; e += kBatchThreads) {
     int rem = e;
     long long mo = t.mat_base;
@@ -102,17 +111,20 @@ __global__ void __launch_bounds__(kBatchThreads) relayout_batch_kernel(const Bat
   }
 }
 
-static void upload_rel(BatchRel& r, const std::vector<BatchTask>& tasks) {
+// (Re)build the chunk table of a relayout for `chunk` elements per CTA.
+static void upload_rel(BatchRel& r, int chunk) {
+  r.free_all();
+  r.chunk = chunk;
   std::vector<int2> ch;
   r.elems = 0;
-  for (int i = 0; i < int(tasks.size()); ++i) {
-    r.elems += tasks[i].t.n;
-    for (int s = 0; s < tasks[i].t.n; s += kBatchChunk) ch.push_back(make_int2(i, s));
+  for (int i = 0; i < int(r.host.size()); ++i) {
+    r.elems += r.host[i].t.n;
+    for (int s = 0; s < r.host[i].t.n; s += chunk) ch.push_back(make_int2(i, s));
   }
   r.nchunks = int(ch.size());
-  if (!tasks.empty()) {
-    BST_CUDA(cudaMalloc(&r.tasks, sizeof(BatchTask) * tasks.size()));
-    BST_CUDA(cudaMemcpy(r.tasks, tasks.data(), sizeof(BatchTask) * tasks.size(), cudaMemcpyHostToDevice));
+  if (!r.host.empty()) {
+    BST_CUDA(cudaMalloc(&r.tasks, sizeof(BatchTask) * r.host.size()));
+    BST_CUDA(cudaMemcpy(r.tasks, r.host.data(), sizeof(BatchTask) * r.host.size(), cudaMemcpyHostToDevice));
   }
   if (!ch.empty()) {
     BST_CUDA(cudaMalloc(&r.chunks, sizeof(int2) * ch.size()));
@@ -124,9 +136,95 @@ static void launch_rel(Ctx* ctx, const BatchRel& r, double* const* bases, double
                        double beta, cudaStream_t s) {
   if (r.nchunks == 0) return;
   ProfScope ps(ctx, s, "relayout", 0.0, 16.0 * r.elems);
-  relayout_batch_kernel<<<r.nchunks, kBatchThreads, 0, s>>>(r.tasks, r.chunks, bases, mat, dir, alpha, beta);
+  relayout_batch_kernel<<<r.nchunks, kBatchThreads, 0, s>>>(r.tasks, r.chunks, bases, mat, dir, alpha, beta,
+                                                            r.chunk);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
+}
+
+// Median over `reps` timed runs of f (after one untimed run), in ms.
+template <class F>
+static float time_ms(cudaStream_t s, int reps, F&& f) {
+  cudaEvent_t a, b;
+  BST_CUDA(cudaEventCreate(&a));
+  BST_CUDA(cudaEventCreate(&b));
+  std::vector<float> t;
+  f();
+  for (int i = 0; i < reps; ++i) {
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+// Autotuner: on the first call of a plan (per arithmetic), time every
+// candidate schedule on the call's own data and keep the fastest.  Only the
+// plan's own buffers are written while tuning; the caller's outputs are not.
+//   relayout: elements per CTA of the gathers and the scatter (1K..8K);
+//   GEMM: tile schedule (problem order / longest K first / column tiles
+//   outer for the tensor-core GEMM; problem order / longest K first for FP64).
+static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bst_prec prec, const std::string& tag,
+                     cudaStream_t s) {
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  char line[256];
+  if (!bp->tuned_rel) {
+    float best = 1e30f;
+    int bc = 2048;
+    for (int c : kChunkChoices) {
+      upload_rel(bp->ra, c);
+      upload_rel(bp->rb, c);
+      const float t = time_ms(s, 3, [&] {
+        launch_rel(ctx, bp->ra, bases, bp->Am, 0, 1.0, 0.0, s);
+        launch_rel(ctx, bp->rb, bases + n, bp->Bm, 0, 1.0, 0.0, s);
+      });
+      snprintf(line, sizeof(line), "batch %p relayout chunk %d: %.4f ms\n", (void*)bp, c, t);
+      ctx->tune_log += line;
+      if (t < best) best = t, bc = c;
+    }
+    upload_rel(bp->ra, bc);
+    upload_rel(bp->rb, bc);
+    upload_rel(bp->rc, bc);
+    snprintf(line, sizeof(line), "batch %p relayout chunk chosen %d\n", (void*)bp, bc);
+    ctx->tune_log += line;
+    bp->tuned_rel = true;
+  }
+  const int pi = prec == BST_FP64 ? 0 : 1;
+  if (!bp->tuned[pi]) {
+    launch_rel(ctx, bp->ra, bases, bp->Am, 0, 1.0, 0.0, s);
+    launch_rel(ctx, bp->rb, bases + n, bp->Bm, 0, 1.0, 0.0, s);
+    const int norders = prec == BST_FP64 ? 2 : 3;
+    float best = 1e30f;
+    int bo = 0;
+    for (int o = 0; o < norders; ++o) {
+      float t;
+      if (prec == BST_FP64) {
+        bp->g.upload(bp->probs, kF64TileM, kF64TileN, o);
+        t = time_ms(s, 3, [&] { launch_gemm_f64(ctx, bp->g, bp->Am, bp->Bm, bp->Cm, s); });
+      } else {
+        t = time_ms(s, 3, [&] { run_gemm_ozaki_probs(ctx, tag, bp->probs, bp->Am, bp->Bm, bp->Cm, s, o); });
+      }
+      snprintf(line, sizeof(line), "batch %p %s tile order %d: %.4f ms\n", (void*)bp,
+               prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki", o, t);
+      ctx->tune_log += line;
+      if (t < best) best = t, bo = o;
+    }
+    if (prec == BST_FP64) bp->g.upload(bp->probs, kF64TileM, kF64TileN, bo);
+    bp->order[pi] = bo;
+    bp->tuned[pi] = true;
+    snprintf(line, sizeof(line), "batch %p %s tile order chosen %d\n", (void*)bp,
+             prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki", bo);
+    ctx->tune_log += line;
+  }
+  ctx->prof = prof;
 }
 
 static BatchPlan* get_batch_plan(Ctx* ctx, const std::vector<Layout*>& A, const std::vector<Layout*>& B,
@@ -145,20 +243,19 @@ static BatchPlan* get_batch_plan(Ctx* ctx, const std::vector<Layout*>& A, const 
   }
   auto bp = std::make_shared<BatchPlan>();
   bp->plans = plans;
-  std::vector<BatchTask> ta, tb, tc;
   for (size_t i = 0; i < plans.size(); ++i) {
     ContractPlan* p = plans[i];
     for (auto t : p->va.tasks) {
       t.mat_base += bp->amat;
-      ta.push_back({t, int32_t(i), 0});
+      bp->ra.host.push_back({t, int32_t(i), 0});
     }
     for (auto t : p->vb.tasks) {
       t.mat_base += bp->bmat;
-      tb.push_back({t, int32_t(i), 0});
+      bp->rb.host.push_back({t, int32_t(i), 0});
     }
     for (auto t : p->vc.tasks) {
       t.mat_base += bp->cmat;
-      tc.push_back({t, int32_t(i), 0});
+      bp->rc.host.push_back({t, int32_t(i), 0});
     }
     for (auto g : p->probs) {
       g.a_off += bp->amat;
@@ -170,9 +267,9 @@ static BatchPlan* get_batch_plan(Ctx* ctx, const std::vector<Layout*>& A, const 
     bp->bmat += p->bmat;
     bp->cmat += p->cmat;
   }
-  upload_rel(bp->ra, ta);
-  upload_rel(bp->rb, tb);
-  upload_rel(bp->rc, tc);
+  upload_rel(bp->ra, 2048);
+  upload_rel(bp->rb, 2048);
+  upload_rel(bp->rc, 2048);
   bp->g.upload(bp->probs, kF64TileM, kF64TileN);
   BST_CUDA(cudaMalloc(&bp->Am, sizeof(double) * std::max<int64_t>(bp->amat, 1)));
   BST_CUDA(cudaMalloc(&bp->Bm, sizeof(double) * std::max<int64_t>(bp->bmat, 1)));
@@ -211,6 +308,8 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
     BST_CUDA(cudaMemcpy(bases, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice));
     bp->tables[ptrs] = bases;
   }
+  const std::string tag = "batch/" + std::to_string(uintptr_t(bp));
+  if (ctx->autotune) autotune(ctx, bp, bases, n, prec, tag, s);
   double *Am = bp->Am, *Bm = bp->Bm, *Cm = bp->Cm;
   launch_rel(ctx, bp->ra, bases, Am, 0, 1.0, 0.0, s);
   launch_rel(ctx, bp->rb, bases + n, Bm, 0, 1.0, 0.0, s);
@@ -219,7 +318,7 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
   } else {
     // the same grouped tensor-core GEMM as a single contraction, over the
     // problems of all contractions
-    run_gemm_ozaki_probs(ctx, "batch/" + std::to_string(uintptr_t(bp)), bp->probs, Am, Bm, Cm, s);
+    run_gemm_ozaki_probs(ctx, tag, bp->probs, Am, Bm, Cm, s, bp->order[1]);
   }
   launch_rel(ctx, bp->rc, bases + 2 * n, Cm, 1, alpha, beta, s);
 }

@@ -149,7 +149,8 @@ struct DevGemm {
   int32_t* tile_idx = nullptr;    // tile -> linear tile index inside its problem
   int ntiles = 0, nprobs = 0;
   double flops = 0;  // algorithmic 2*M*N*K summed over the problems
-  void upload(const std::vector<GemmProb>& p, int tm, int tn);
+  // order 0: problem order; 1: tiles of the longest-K problems first
+  void upload(const std::vector<GemmProb>& p, int tm, int tn, int order = 0);
   void free_all();
 };
 
@@ -204,6 +205,8 @@ struct Ctx {
   int proj_method = 1;   // 0: cuSOLVER gesvd per sector, 1: subspace iteration + small eigensolver
   int proj_iters = 9;    // subspace iterations
   double* d_scratch_small = nullptr;
+  bool autotune = true;      // time schedule candidates on the first batched call of a plan
+  std::string tune_log;      // one line per tuning decision
   ~Ctx();
   void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
 };
@@ -243,8 +246,10 @@ void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double*
                     cudaStream_t s);
 void ozaki_free(OzakiPlan* oz);
 // generic Ozaki GEMM over a problem list (used by the projector)
+// `order` selects the tile schedule (0 problem order, 1 longest K first,
+// 2 column tiles outer); each schedule is its own cached plan
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs,
-                          const double* A, const double* B, double* C, cudaStream_t s);
+                          const double* A, const double* B, double* C, cudaStream_t s, int order = 0);
 
 // projector.cu
 struct ProjResult {

@@ -14,7 +14,7 @@ const int kF64TileN = 64;
 constexpr int kBK = 16;
 constexpr int kPad = 2;
 
-void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn) {
+void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn, int order) {
   free_all();
   nprobs = int(p.size());
   flops = 0;
@@ -28,6 +28,18 @@ void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn) {
     }
   }
   ntiles = int(tp.size());
+  if (order == 1) {
+    std::vector<int> idx(ntiles);
+    for (int i = 0; i < ntiles; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return p[tp[x]].K > p[tp[y]].K; });
+    std::vector<int32_t> tp2(ntiles), ti2(ntiles);
+    for (int i = 0; i < ntiles; ++i) {
+      tp2[i] = tp[idx[i]];
+      ti2[i] = ti[idx[i]];
+    }
+    tp.swap(tp2);
+    ti.swap(ti2);
+  }
   if (nprobs) {
     BST_CUDA(cudaMalloc(&probs, sizeof(GemmProb) * nprobs));
     BST_CUDA(cudaMemcpy(probs, p.data(), sizeof(GemmProb) * nprobs, cudaMemcpyHostToDevice));

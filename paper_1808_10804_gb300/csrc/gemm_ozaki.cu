@@ -481,7 +481,11 @@ struct OzakiPlan {
 
 static size_t smem_bytes() { return sizeof(oz::Smem) + 1024; }
 
-static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
+// Tile schedule of a plan (the order in which CTAs pick up output tiles):
+// 0 problem order, row tiles outer; 1 longest K first (the tiles that take
+// longest start first, so the last wave is short); 2 problem order, column
+// tiles outer (CTAs that run together share B slices in L2).
+static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int order = 0) {
   auto* P = new OzakiPlan();
   std::vector<oz::Prob> hp;
   std::vector<oz::Tile> ht;
@@ -508,11 +512,19 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs) {
     P->rowsB += g.N;
     const int pi = int(hp.size());
     hp.push_back(q);
-    for (int m0 = 0; m0 < g.M; m0 += oz::kTM)
-      for (int n0 = 0; n0 < g.N; n0 += oz::kTN) ht.push_back({pi, m0, n0, 0});
+    if (order == 2) {
+      for (int n0 = 0; n0 < g.N; n0 += oz::kTN)
+        for (int m0 = 0; m0 < g.M; m0 += oz::kTM) ht.push_back({pi, m0, n0, 0});
+    } else {
+      for (int m0 = 0; m0 < g.M; m0 += oz::kTM)
+        for (int n0 = 0; n0 < g.N; n0 += oz::kTN) ht.push_back({pi, m0, n0, 0});
+    }
     P->flops += 2.0 * double(g.M) * g.N * g.K;
     P->split_bytes += double(g.M + g.N) * g.K * (8.0 + 2.0 * oz::kSlices) + 4.0 * (g.M + g.N);
   }
+  if (order == 1)
+    std::stable_sort(ht.begin(), ht.end(),
+                     [&](const oz::Tile& x, const oz::Tile& y) { return hp[x.prob].K > hp[y.prob].K; });
   P->nprobs = int(hp.size());
   P->ntiles = int(ht.size());
   P->nsa = int(sa.size());
@@ -580,9 +592,10 @@ void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double*
 void ozaki_free(OzakiPlan* oz) { delete oz; }
 
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
-                          const double* B, double* C, cudaStream_t s) {
-  // plans live in the context (freed with it), keyed by caller tag and problem list
-  const std::string key = tag + "/" + std::to_string(probs_hash(probs));
+                          const double* B, double* C, cudaStream_t s, int order) {
+  // plans live in the context (freed with it), keyed by caller tag, problem
+  // list and tile schedule
+  const std::string key = tag + "/" + std::to_string(probs_hash(probs)) + "/" + std::to_string(order);
   OzakiPlan* P;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -590,7 +603,7 @@ void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<Ge
     P = it == ctx->ozplans.end() ? nullptr : it->second.get();
   }
   if (!P) {
-    std::shared_ptr<OzakiPlan> np(build_plan(ctx, probs));
+    std::shared_ptr<OzakiPlan> np(build_plan(ctx, probs, order));
     P = np.get();
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->ozplans[key] = std::move(np);

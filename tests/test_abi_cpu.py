@@ -70,3 +70,23 @@ def test_layout_interning_and_bad_legs(hctx):
         hctx.layout([bst.Leg(1, (-1, 1), (0, 2))])     # zero degeneracy
     with pytest.raises(bst.BstError):
         hctx.layout([bst.Leg(2, (-1, 1), (1, 2))])     # bad flow
+
+
+def test_batched_call_checks_and_tuning_switch(hctx):
+    """Argument checks of the batched contraction and the autotuner switch
+    run on the host: a host-only context rejects device work with BST_E_ARG
+    before touching any pointer; the tuning log starts empty."""
+    import ctypes as C
+    L = hctx.layout([bst.Leg(1, (-1, 1), (2, 2)), bst.Leg(-1, (-1, 1), (2, 2))])
+    arr = C.c_void_p * 1
+    legs = (C.c_int32 * 1)(1)
+    legs0 = (C.c_int32 * 1)(0)
+    st = bst.lib().bst_contract_batched(hctx.h, 0, arr(L.h), arr(None), arr(L.h), arr(None), 1, legs, legs0,
+                                        0, 1.0, 0.0, arr(L.h), arr(None), None)
+    assert st == 1   # nbatch < 1
+    st = bst.lib().bst_contract_batched(hctx.h, 1, arr(L.h), arr(None), arr(L.h), arr(None), 1, legs, legs0,
+                                        0, 1.0, 0.0, arr(L.h), arr(None), None)
+    assert st == 1   # host-only context
+    hctx.set_autotune(False)
+    hctx.set_autotune(True)
+    assert hctx.tuning_log() == ""

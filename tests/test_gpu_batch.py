@@ -198,3 +198,26 @@ def test_full_batch_sampled_oracle(full_batch, pick):
         got = c.cpu().numpy()[sel]
         scale = np.linalg.norm(ref)
         assert np.linalg.norm(got - ref) <= tol * scale, (pick, np.linalg.norm(got - ref) / scale)
+
+
+def test_autotune_changes_no_bit(bst, ctx):
+    """The tuned schedule (chunk size, tile order) gives the same bits as the
+    untuned default schedule, and every decision is logged."""
+    cfgs = small_configs(8)
+    inst = [gpu_instance(bst, ctx, c) for c in cfgs]
+    plain = bst.Context(0)
+    try:
+        plain.set_autotune(False)
+        inst2 = [gpu_instance(bst, plain, c) for c in cfgs]
+        for prec in ("fp64", "ozaki"):
+            _, tuned = run_batch(ctx, inst, prec)
+            _, untuned = run_batch(plain, inst2, prec)
+            torch.cuda.synchronize()
+            for a, b in zip(tuned, untuned):
+                assert torch.equal(a, b), prec
+        assert plain.tuning_log() == ""
+    finally:
+        plain.close()
+    log = ctx.tuning_log()
+    assert "relayout chunk chosen" in log
+    assert "gemm_f64 tile order chosen" in log and "gemm_ozaki tile order chosen" in log
