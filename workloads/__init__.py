@@ -149,3 +149,23 @@ def batched_site_legs(cfg):
     the double layer a[k_l, k_u, k_r, k_d] of A over (k_u, k_l)."""
     return [leg(IN, *cfg["phys"]), leg(IN, *cfg["odd"]), leg(IN, *cfg["even"]),
             leg(OUT, *cfg["even"]), leg(OUT, *cfg["even"])]
+
+
+def su2_config(name):
+    """Leg recipes of the SU(2) workload (spins doubled, reduced
+    degeneracies): virtual bond D=10 as j=0 x1 + j=1/2 x3 + j=1 x1 (d=5),
+    physical j=1/2, the double-layer leg k it fuses to (total 100, reduced
+    42), and the env bond of total X=150 over j=0..3 (chi=50 reduced)."""
+    if name == "D10chi150":
+        return {"name": name,
+                "virtual": ((0, 1, 2), (1, 3, 1)),
+                "phys": ((1,), (1,)),
+                "k": ((0, 1, 2, 3, 4), (11, 12, 12, 6, 1)),
+                "x": ((0, 1, 2, 3, 4, 5, 6), (11, 12, 10, 7, 5, 3, 2))}
+    if name == "small":
+        return {"name": name,
+                "virtual": ((0, 1), (1, 1)),
+                "phys": ((1,), (1,)),
+                "k": ((0, 1, 2), (2, 2, 1)),
+                "x": ((0, 1, 2), (2, 2, 1))}
+    raise KeyError(name)
