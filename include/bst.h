@@ -61,7 +61,22 @@ typedef enum {
   BST_E_UNSUPPORTED = 8   /* valid request the library does not implement */
 } bst_status;
 
-typedef enum { BST_U1 = 1 } bst_group;
+/* Symmetry group of a layout.
+ *   BST_U1:  charges are integers (2 S_z); a block is one sector per leg with
+ *            sum_i flow_i q_i = 0; its data is the dense block.
+ *   BST_SU2: charges are doubled spins 2j >= 0; degeneracies count
+ *            multiplets (reduced dimensions).  A block is one sector per leg
+ *            plus a fusion tree, and stores only the reduced tensor; its
+ *            full form is reduced (x) CGC tensor (Sec. 2, Eq. "tensor-cgc").
+ *            The CGC tensor of a block maps its outgoing legs to its
+ *            incoming legs through one coupled spin J:
+ *              c[m_in; m_out] = sum_M <in-tree m_in|J M> <out-tree m_out|J M>,
+ *            each tree coupling its legs left to right (leg order) with
+ *            Condon-Shortley Clebsch-Gordan coefficients (no leg: J = 0; one
+ *            leg: J = its spin).  Tree labels (bst_layout_tree): the in-tree
+ *            intermediates, J, the out-tree intermediates, as doubled spins.
+ *            Blocks are ordered by sector indices, then tree labels. */
+typedef enum { BST_U1 = 1, BST_SU2 = 2 } bst_group;
 
 /* Arithmetic of the block GEMMs.
  *   BST_FP64:  plain FP64 (DMMA) grouped GEMM;
@@ -149,6 +164,15 @@ BST_API bst_status bst_layout_leg(bst_layout l, int32_t i, int32_t* flow, int32_
  * element offset into the data array, per-leg extents (rank entries). */
 BST_API bst_status bst_layout_block(bst_layout l, int64_t i, int32_t* sector_idx,
                             int64_t* offset, int64_t* shape);
+/* Tree labels of block i of an SU(2) layout: *ntree labels (doubled spins:
+ * in-tree intermediates, the coupled J, out-tree intermediates) into
+ * `labels` if non-NULL.  U(1) layouts report *ntree = 0. */
+BST_API bst_status bst_layout_tree(bst_layout l, int64_t i, int32_t* ntree, int32_t* labels);
+/* Clebsch-Gordan coefficient <j1 m1 j2 m2 | J M> with every argument doubled
+ * (Condon-Shortley phases), as the library uses it for SU(2) blocks.  Host
+ * only; 0 for forbidden arguments. */
+BST_API bst_status bst_su2_cg(int32_t tj1, int32_t tm1, int32_t tj2, int32_t tm2, int32_t tJ, int32_t tM,
+                              double* out);
 /* The dual layout: every flow reversed, same blocks, same storage order
  * (the conjugate tensor of Sec. 3.2's double layer A*). */
 BST_API bst_status bst_layout_dual(bst_layout l, bst_layout* out);
@@ -186,7 +210,14 @@ BST_API bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, 
  * charge through the cut, so every group is one dense GEMM whose result is
  * already reduced (Sec. 2, grouping by output quantum numbers so the
  * unreduced result never exists).  `prec` selects the GEMM arithmetic.
- * beta == 0 ignores the previous contents of c (NaN-safe). */
+ * beta == 0 ignores the previous contents of c (NaN-safe).
+ * SU(2) tensors (both A and B BST_SU2): every pair of blocks that agree on
+ * the contracted legs contributes m_A . m_B, expanded into the output's
+ * canonical blocks with X = <c_C, c_A . c_B> / (2 J_C + 1) (Sec. 2: the CGC
+ * of a pair product is the product of the CGCs, then parallel blocks are
+ * reduced).  The pair products of one contracted sector tuple form one GEMM;
+ * a recoupling launch adds them with their X into the output blocks.  The
+ * other tensor operations below are U(1)-only (BST_E_UNSUPPORTED). */
 BST_API bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a,
                         bst_layout B, const double* b,
                         int32_t npairs, const int32_t* legsA, const int32_t* legsB,

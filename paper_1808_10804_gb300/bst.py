@@ -81,6 +81,8 @@ def lib():
         "bst_layout_leg": [vp, i32, P(i32), P(i32), P(i32), P(i64)],
         "bst_layout_block": [vp, i64, P(i32), P(i64), P(i64)],
         "bst_layout_dual": [vp, P(vp)],
+        "bst_layout_tree": [vp, i64, P(i32), P(i32)],
+        "bst_su2_cg": [i32, i32, i32, i32, i32, i32, P(dbl)],
         "bst_permute": [vp, vp, vp, P(i32), P(vp), vp, vp],
         "bst_fuse": [vp, vp, vp, i32, P(i32), P(vp), vp, vp],
         "bst_contract_layout": [vp, vp, vp, i32, P(i32), P(i32), P(vp)],
@@ -103,6 +105,13 @@ def lib():
     L.bst_last_error.argtypes = []
     _lib = L
     return L
+
+
+def su2_cg(tj1, tm1, tj2, tm2, tJ, tM):
+    """<j1 m1 j2 m2|J M> (doubled arguments) as the library computes it."""
+    v = C.c_double()
+    _check(lib().bst_su2_cg(tj1, tm1, tj2, tm2, tJ, tM, C.byref(v)))
+    return v.value
 
 
 def _check(st):
@@ -187,6 +196,17 @@ class Layout:
             out.append((tuple(s), off.value, tuple(sh)))
         return out
 
+    def trees(self):
+        """Tree labels of every block (empty tuples for U(1))."""
+        n = C.c_int32()
+        _check(lib().bst_layout_tree(self.h, 0, C.byref(n), None)) if self.nblocks else None
+        out = []
+        lab = (C.c_int32 * max(1, n.value))()
+        for b in range(self.nblocks):
+            _check(lib().bst_layout_tree(self.h, b, None, lab))
+            out.append(tuple(lab[:n.value]))
+        return out
+
     def dual(self):
         h = C.c_void_p()
         _check(lib().bst_layout_dual(self.h, C.byref(h)))
@@ -247,7 +267,10 @@ class Context:
             i += 1
         return out
 
-    def layout(self, legs):
+    def layout(self, legs, group="u1"):
+        """Layout of the given legs; group "u1" (charges 2Sz) or "su2"
+        (charges 2j, degeneracies = multiplet counts)."""
+        g = {"u1": 1, "su2": 2}[group]
         legs = [l if isinstance(l, Leg) else Leg(int(l["flow"]), tuple(l["charges"]), tuple(l["degs"]))
                 for l in legs]
         arr = (_Leg * len(legs))()
@@ -258,7 +281,7 @@ class Context:
             keep += [q, d]
             arr[i] = _Leg(l.flow, len(l.charges), q, d)
         h = C.c_void_p()
-        _check(lib().bst_layout_create(self.h, 1, len(legs), arr, C.byref(h)))
+        _check(lib().bst_layout_create(self.h, g, len(legs), arr, C.byref(h)))
         return Layout(self, h)
 
     # ---- operations ------------------------------------------------------------

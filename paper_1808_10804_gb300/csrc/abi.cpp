@@ -41,6 +41,7 @@ static bst_status guarded(F&& f) {
 
 namespace bst {
 Ctx::~Ctx() {
+  su2plans.clear();
   bplans.clear();
   ozplans.clear();
   cplans.clear();
@@ -263,6 +264,23 @@ bst_status bst_layout_block(bst_layout l, int64_t i, int32_t* sector_idx, int64_
   });
 }
 
+bst_status bst_layout_tree(bst_layout l, int64_t i, int32_t* ntree, int32_t* labels) {
+  return guarded([&] {
+    BST_REQUIRE(l, BST_E_ARG, "layout is NULL");
+    Layout* L = L_(l);
+    BST_REQUIRE(i >= 0 && i < L->nblocks, BST_E_ARG, "block index out of range");
+    if (ntree) *ntree = L->ntree;
+    if (labels && L->ntree) std::copy(&L->tree[i * L->ntree], &L->tree[i * L->ntree] + L->ntree, labels);
+  });
+}
+
+bst_status bst_su2_cg(int32_t tj1, int32_t tm1, int32_t tj2, int32_t tm2, int32_t tJ, int32_t tM, double* out) {
+  return guarded([&] {
+    BST_REQUIRE(out, BST_E_ARG, "out is NULL");
+    *out = su2_cg(tj1, tm1, tj2, tm2, tJ, tM);
+  });
+}
+
 bst_status bst_layout_dual(bst_layout l, bst_layout* out) {
   return guarded([&] {
     BST_REQUIRE(l && out, BST_E_ARG, "null argument");
@@ -277,6 +295,7 @@ bst_status bst_permute(bst_ctx ctx, bst_layout src, const double* src_data, cons
                        double* dst_data, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && src && perm && dst, BST_E_ARG, "null argument");
+    require_u1(L_(src));
     Ctx* c = C_(ctx);
     set_dev(c);
     Layout* S = L_(src);
@@ -298,6 +317,7 @@ bst_status bst_fuse(bst_ctx ctx, bst_layout src, const double* src_data, int32_t
                     bst_layout* dst, double* dst_data, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && src && group_sizes && dst && ngroups >= 1, BST_E_ARG, "bad argument");
+    require_u1(L_(src));
     Ctx* c = C_(ctx);
     set_dev(c);
     std::vector<int> g(group_sizes, group_sizes + ngroups);
@@ -320,6 +340,13 @@ bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, int32_t 
     BST_REQUIRE(ctx && A && B && C && npairs >= 0, BST_E_ARG, "bad argument");
     BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
     std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    BST_REQUIRE(L_(A)->group == L_(B)->group, BST_E_ARG, "A and B belong to different symmetry groups");
+    if (L_(A)->group == BST_SU2) {
+      Layout* out = su2_contract_layout(C_(ctx), L_(A), L_(B), la, lb);
+      retain(out);
+      *C = H_(out);
+      return;
+    }
     ContractPlan* p = get_contract_plan(C_(ctx), L_(A), L_(B), la, lb);
     retain(p->C);
     *C = H_(p->C);
@@ -336,6 +363,11 @@ bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a, bst_layout B
     Ctx* cx = C_(ctx);
     set_dev(cx);
     std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    BST_REQUIRE(L_(A)->group == L_(B)->group, BST_E_ARG, "A and B belong to different symmetry groups");
+    if (L_(A)->group == BST_SU2) {
+      su2_contract(cx, L_(A), a, L_(B), b, la, lb, prec, alpha, beta, L_(C), c, (cudaStream_t)stream);
+      return;
+    }
     ContractPlan* p = get_contract_plan(cx, L_(A), L_(B), la, lb);
     BST_REQUIRE(p->C == L_(C), BST_E_SHAPE, "C is not the layout of this contraction");
     BST_REQUIRE((L_(A)->nnz == 0 || a) && (L_(B)->nnz == 0 || b) && (p->C->nnz == 0 || c), BST_E_ARG,
@@ -349,6 +381,7 @@ bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double* a, bst_
                                 double beta, bst_layout C, double* c, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && A && B && C && npairs >= 0, BST_E_ARG, "bad argument");
+    require_u1(L_(A));
     BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
     std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
     contract_noalloc(C_(ctx), L_(A), a, L_(B), b, la, lb, alpha, beta, L_(C), c, (cudaStream_t)stream);
@@ -370,6 +403,8 @@ bst_status bst_contract_batched(bst_ctx ctx, int32_t nbatch, const bst_layout* A
     std::vector<double*> pc(nbatch);
     for (int i = 0; i < nbatch; ++i) {
       BST_REQUIRE(A[i] && B[i] && C[i], BST_E_ARG, "layout handle is NULL");
+      require_u1(L_(A[i]));
+      require_u1(L_(B[i]));
       la_[i] = L_(A[i]);
       lb_[i] = L_(B[i]);
       lc_[i] = L_(C[i]);
@@ -386,6 +421,7 @@ bst_status bst_double_layer(bst_ctx ctx, bst_layout A, const double* A_data, bst
                             bst_layout* a_layout, double* a, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && A && a_layout, BST_E_ARG, "null argument");
+    require_u1(L_(A));
     Ctx* c = C_(ctx);
     set_dev(c);
     cudaStream_t s = (cudaStream_t)stream;
@@ -459,6 +495,7 @@ bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double* rtop, b
                              bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && Rtop && Rbot && rtop && rbot && P && p && Pt && pt && kept, BST_E_ARG, "null argument");
+    require_u1(L_(Rtop));
     Ctx* c = C_(ctx);
     set_dev(c);
     ProjResult r = svd_projector(c, L_(Rtop), rtop, L_(Rbot), rbot, ncut, chi, rel_cutoff, new_flow, prec, p, pt,
@@ -485,6 +522,7 @@ bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const dou
                         double rel_cutoff, bst_prec prec, bst_ctm_stats* stats, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && a_layout && a && env, BST_E_ARG, "null argument");
+    require_u1(L_(a_layout));
     BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
     Ctx* c = C_(ctx);
     set_dev(c);

@@ -66,7 +66,11 @@ struct Layout {
   std::vector<int32_t> sect;    // nblocks * rank sector indices
   std::vector<int64_t> offset;  // nblocks element offsets
   std::vector<int64_t> shape;   // nblocks * rank extents
-  std::unordered_map<uint64_t, int64_t> index;  // packed sector tuple -> block
+  // SU(2): tree labels of every block (ntree per block: in-tree
+  // intermediates, coupled J, out-tree intermediates; doubled spins)
+  int ntree = 0;
+  std::vector<int32_t> tree;
+  std::unordered_map<uint64_t, int64_t> index;  // packed sector tuple -> (first) block
   std::string key;              // structural key used for interning
 
   int64_t block_of(const int32_t* s) const;
@@ -156,6 +160,7 @@ struct DevGemm {
 
 struct OzakiPlan;  // mixed-precision GEMM plan (gemm_ozaki.cu)
 struct BatchPlan;  // batched-contraction plan (batch.cu)
+struct Su2Plan;    // SU(2) contraction plan (su2.cu)
 
 // Contraction plan (cached per (A, B, pairs)).
 struct ContractPlan {
@@ -199,6 +204,7 @@ struct Ctx {
   std::map<std::string, std::unique_ptr<DevGemm>> gplans;
   std::map<std::string, std::shared_ptr<BatchPlan>> bplans;  // deleter bound in batch.cu
   std::map<std::string, std::shared_ptr<OzakiPlan>> ozplans;  // deleter bound in gemm_ozaki.cu
+  std::map<std::string, std::shared_ptr<Su2Plan>> su2plans;   // deleter bound in su2.cu
   int* d_err = nullptr;                     // device error word
   std::atomic<int64_t> launches{0};
   void* cusolver = nullptr;
@@ -276,6 +282,18 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
                       const std::vector<Layout*>& B, const std::vector<const double*>& b, const std::vector<int>& la,
                       const std::vector<int>& lb, bst_prec prec, double alpha, double beta,
                       const std::vector<Layout*>& C, const std::vector<double*>& c, cudaStream_t s);
+
+// su2.cu
+double su2_cg(int tj1, int tm1, int tj2, int tm2, int tJ, int tM);  // doubled spins
+int su2_ntree(const std::vector<Leg>& legs);
+void su2_enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& sect, std::vector<int32_t>& tree);
+Layout* su2_contract_layout(Ctx* ctx, Layout* A, Layout* B, const std::vector<int>& la, const std::vector<int>& lb);
+void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double* b, const std::vector<int>& la,
+                  const std::vector<int>& lb, bst_prec prec, double alpha, double beta, Layout* C, double* c,
+                  cudaStream_t s);
+inline void require_u1(const Layout* L) {
+  if (L->group != BST_U1) throw Error(BST_E_UNSUPPORTED, "this operation is implemented for U(1) tensors only");
+}
 
 // ctm.cpp
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,

@@ -70,7 +70,7 @@ static void enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& out)
 }
 
 Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
-  BST_REQUIRE(group == BST_U1, BST_E_UNSUPPORTED, "only U(1) layouts are implemented");
+  BST_REQUIRE(group == BST_U1 || group == BST_SU2, BST_E_ARG, "group must be BST_U1 or BST_SU2");
   BST_REQUIRE(!legs_in.empty() && legs_in.size() <= kMaxRank, BST_E_ARG, "rank must be 1..8");
   std::vector<Leg> legs = legs_in;
   for (auto& l : legs) {
@@ -80,6 +80,7 @@ Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
     for (size_t i = 0; i < l.q.size(); ++i) {
       BST_REQUIRE(l.d[i] > 0, BST_E_ARG, "degeneracies must be positive");
       if (i) BST_REQUIRE(l.q[i] > l.q[i - 1], BST_E_ARG, "charges must be strictly ascending");
+      if (group == BST_SU2) BST_REQUIRE(l.q[i] >= 0 && l.q[i] <= 64, BST_E_ARG, "SU(2) labels 2j must be 0..64");
     }
     l.finish();
   }
@@ -97,7 +98,12 @@ Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
   L->rank = int(legs.size());
   L->legs = legs;
   L->key = key;
-  enum_blocks(legs, L->sect);
+  if (group == BST_SU2) {
+    L->ntree = su2_ntree(legs);
+    su2_enum_blocks(legs, L->sect, L->tree);
+  } else {
+    enum_blocks(legs, L->sect);
+  }
   L->nblocks = int64_t(L->sect.size()) / L->rank;
   L->offset.resize(L->nblocks);
   L->shape.resize(L->nblocks * L->rank);
@@ -112,7 +118,7 @@ Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
     BST_REQUIRE(n < (int64_t(1) << 31), BST_E_SHAPE, "block larger than 2^31 elements");
     L->offset[b] = off;
     off += n;
-    L->index[Layout::pack(&L->sect[b * L->rank], L->rank)] = b;
+    L->index.emplace(Layout::pack(&L->sect[b * L->rank], L->rank), b);  // first block of a tuple
   }
   L->nnz = off;
   L->refs = 2;  // one for the caller, one for the intern table
