@@ -225,6 +225,135 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     return out
 
 
+def su2_corner_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
+    """SU(2) enlarged corner of the D=10 (d=5), X=150 (chi=50) workload:
+    X1 = C1.T1, X2 = X1.T4, Q1 = X2.a on seeded reduced blocks.  One step =
+    the three contractions."""
+    import torch
+    from workloads import su2_config, values
+    cfg = su2_config("D10chi150")
+    K = bst.Leg(1, *cfg["k"])
+    X = bst.Leg(1, *cfg["x"])
+    legs = {"C1": [X.dual(), X.dual()], "T1": [X, K.dual(), X.dual()], "T4": [X, K.dual(), X.dual()],
+            "A": [K, K, K.dual(), K.dual()]}
+    L = {n: ctx.layout(l, group="su2") for n, l in legs.items()}
+    d = {n: torch.tensor(values(0, n, L[n].nnz), dtype=torch.float64, device=dev) for n in L}
+
+    def corner(p):
+        LX1, x1 = ctx.contract(L["C1"], d["C1"], L["T1"], d["T1"], (0,), (0,), prec=p)
+        LX2, x2 = ctx.contract(LX1, x1, L["T4"], d["T4"], (0,), (0,), prec=p)
+        return ctx.contract(LX2, x2, L["A"], d["A"], (0, 2), (1, 0), prec=p)
+
+    _, q64 = corner("fp64")
+    _, q = corner(prec)
+    torch.cuda.synchronize()
+    err = float(torch.linalg.norm(q - q64) / torch.linalg.norm(q64))
+    stream = torch.cuda.current_stream()
+
+    def timed(p, n):
+        for _ in range(warmup):
+            corner(p)
+        ev = []
+        for i in range(n):
+            flush.fill_(float(i))
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            corner(p)
+            b_.record(stream)
+            ev.append((a, b_))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b_) for a, b_ in ev)
+
+    ms = timed(prec, steps)
+    ms64 = timed("fp64", max(3, steps // 2))
+    ctx.profile(True)
+    corner(prec)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    gk = "gemm_ozaki" if prec == "ozaki" else "gemm_f64"
+    flops = prof[gk][2]
+    out = {"workload": "su2_D10_X150_enlarged_corner", "value": 1e3 / ms, "unit": "corners/s",
+           "ms_per_step": ms, "fp64_path_ms_per_step": ms64, "algorithmic_gflop": flops / 1e9,
+           "block_sparse_tflops": flops / (ms / 1e3) / 1e12, "rel_err_vs_fp64_path": err,
+           "reduced_nnz_Q1": int(q.numel()),
+           "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}}
+    rc = prof.get("recouple")
+    if rc:
+        a = rc[3] / (rc[1] / 1e3) / 1e9
+        out["roofline_recouple"] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                    "frac": a / pk["hbm_gbs"]}
+    return out
+
+
+def single_layer_bench(bst, dev, local, prec, steps, warmup, flush, pk):
+    """Large U(1) single-layer LEFT move: D=8 (odd {-1:4,+1:4}, even
+    {-2:2,0:4,+2:2}), chi=256 over charges -8..8, three-spin physical leg
+    {-3:1,-1:3,1:3,3:1}; the double layer is never formed.  One step = the
+    single-layer site (A with the remover absorbed) and one LEFT move."""
+    import numpy as np
+    import torch
+    from paper_1808_10804_gb300.ctmrg import Network
+    from workloads import u1_config, values
+    cfg = u1_config("d8chi256")
+    ctx = bst.Context(local)
+    try:
+        net = Network(ctx, {"A": cfg["A"], "R": cfg["R"]}, cfg["x"], cfg["chi"], lambda n, k: values(0, n, k),
+                      device=dev, single_layer=True)
+        stream = torch.cuda.current_stream()
+
+        def run(p):
+            net.reset()
+            return net.step(p, direction=bst.LEFT)
+
+        run("fp64")
+        ref = {r: net.env.data(r).cpu().numpy() for r in ("C1", "T4", "C4")}
+        stats = run(prec)
+        torch.cuda.synchronize()
+        err = max(float(np.linalg.norm(net.env.data(r).cpu().numpy() - ref[r]) / np.linalg.norm(ref[r]))
+                  for r in ref)
+
+        def timed(p, n, w):
+            for _ in range(w):
+                run(p)
+            ev = []
+            for i in range(n):
+                flush.fill_(float(i))
+                a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                run(p)
+                b_.record(stream)
+                ev.append((a, b_))
+            torch.cuda.synchronize()
+            return statistics.median(a.elapsed_time(b_) for a, b_ in ev)
+
+        ms = timed(prec, max(3, steps // 3), max(1, warmup // 3))
+        ms64 = timed("fp64", 1, 0)
+        ctx.profile(True)
+        run(prec)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        gk = "gemm_ozaki" if prec == "ozaki" else "gemm_f64"
+        flops = sum(v[2] for k, v in prof.items() if k.startswith("gemm"))
+        out = {"workload": "u1_D8_chi256_single_layer_left_move", "value": 1e3 / ms, "unit": "moves/s",
+               "ms_per_step": ms, "fp64_path_ms_per_step": ms64, "rel_err_vs_fp64_path": err,
+               "kept": stats["kept"][0], "algorithmic_gflop": flops / 1e9,
+               "block_sparse_tflops": flops / (ms / 1e3) / 1e12,
+               "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()}}
+        g = prof.get(gk)
+        if g:
+            a = (15.0 if prec == "ozaki" else 1.0) * g[2] / (g[1] / 1e3) / 1e12
+            peak = pk["bf16_tflops"] if prec == "ozaki" else pk["bf16_tflops"] * 1.25 / 2250.0
+            out["roofline"] = {"kernel": gk, "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+                               "frac": a / peak}
+        del net
+        return out
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -336,9 +465,11 @@ def run_ours(args):
         fp64_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev2)
 
     pk = peaks()
-    batched = None
+    batched = su2 = large = None
     if not args.no_batch:
         batched = batch_bench(bst, ctx, dev, prec, args.steps, args.warmup, flush, pk)
+        su2 = su2_corner_bench(bst, ctx, dev, prec, args.steps, args.warmup, flush, pk)
+        large = single_layer_bench(bst, dev, local, prec, args.steps, args.warmup, flush, pk)
 
     if rank != 0:
         return
@@ -399,6 +530,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "batched": batched,
+        "su2_corner": su2,
+        "single_layer_large": large,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -113,12 +113,16 @@ BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
 BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
 /* Eigensolver behind bst_svd_projector and bst_ctm_move.
  *   BST_PROJ_SUBSPACE (default): per sector of N, subspace iteration on
- *     N^T N with a block of up to 160 vectors (iters steps, CholQR
- *     orthonormalisation), a Rayleigh-Ritz step solved by an FP32 Jacobi
- *     eigensolver and refined to FP64 by Ogita-Aishima steps; sectors of
- *     dimension <= 160 are decomposed directly.  Every matrix product runs
- *     in the call's bst_prec arithmetic.  Falls back to BST_PROJ_GESVD when
- *     chi + 16 exceeds the block.
+ *     N^T N with a block of 160 vectors (CholQR orthonormalisation), in
+ *     rounds of `iters` steps, each closed by a Rayleigh-Ritz step in FP64
+ *     (FP32 Jacobi eigensolver refined by Ogita-Aishima steps); sectors of
+ *     dimension <= 160 are decomposed directly.  A round is accepted when
+ *     every Ritz pair the truncation keeps has a residual
+ *     ||N^T N v - lambda v|| <= tol * lambda_max (tol 3e-14 for BST_FP64,
+ *     4e-12 for BST_OZAKI, whose iterations run on the tensor cores), or
+ *     when the residual has stopped falling within 100 tol.  Falls back to
+ *     BST_PROJ_GESVD after 480 steps, or when the truncation keeps states
+ *     within 16 of a sector's block edge.
  *   BST_PROJ_GESVD: full FP64 SVD of every sector with cuSOLVER gesvd. */
 typedef enum { BST_PROJ_GESVD = 0, BST_PROJ_SUBSPACE = 1 } bst_proj_method;
 BST_API bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters);

@@ -348,6 +348,13 @@ class Context:
                                       C.byref(h), _ptr(out), _stream(stream)))
         return L, out
 
+    def double_layer_layout(self, A, R=None):
+        """Layout of the double layer of A (with the remover R) without
+        computing it."""
+        h = C.c_void_p()
+        _check(lib().bst_double_layer(self.h, A.h, None, R.h if R else None, None, C.byref(h), None, None))
+        return Layout(self, h)
+
     def svd_projector(self, Rt, rt, Rb, rb, ncut, chi, rel_cutoff=1e-14, new_flow=-1, prec="fp64",
                       stream=None):
         na = 1

@@ -41,6 +41,7 @@ static bst_status guarded(F&& f) {
 
 namespace bst {
 Ctx::~Ctx() {
+  projviews.clear();
   su2plans.clear();
   bplans.clear();
   ozplans.clear();

@@ -161,6 +161,7 @@ struct DevGemm {
 struct OzakiPlan;  // mixed-precision GEMM plan (gemm_ozaki.cu)
 struct BatchPlan;  // batched-contraction plan (batch.cu)
 struct Su2Plan;    // SU(2) contraction plan (su2.cu)
+struct ProjView;   // projector layout view (projector.cu)
 
 // Contraction plan (cached per (A, B, pairs)).
 struct ContractPlan {
@@ -205,6 +206,7 @@ struct Ctx {
   std::map<std::string, std::shared_ptr<BatchPlan>> bplans;  // deleter bound in batch.cu
   std::map<std::string, std::shared_ptr<OzakiPlan>> ozplans;  // deleter bound in gemm_ozaki.cu
   std::map<std::string, std::shared_ptr<Su2Plan>> su2plans;   // deleter bound in su2.cu
+  std::map<std::string, std::shared_ptr<ProjView>> projviews; // deleter bound in projector.cu
   int* d_err = nullptr;                     // device error word
   std::atomic<int64_t> launches{0};
   void* cusolver = nullptr;

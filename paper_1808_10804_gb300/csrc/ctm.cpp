@@ -96,24 +96,97 @@ void normalise(Ctx* ctx, double* x, int64_t n, cudaStream_t s) {
   launch_scale(ctx, x, n, ss, s);
 }
 
+// Contraction with the double layer a = sum_P A (x) A* over X's legs lx[0],
+// lx[1] and a's legs la[0], la[1] (directions 0..3 = L, U, R, D); output legs
+// [X's other legs, a's two other legs], as contract(X, a, lx, la) gives.
+// With the double layer given (rank-4 site) this is that one contraction.
+// With a single-layer site A[P, L, U, R, D] (rank 5) a is never formed: X's
+// two legs are split into their (ket, bra) parts (the fused double-layer
+// leg of direction x is fuse(A.x, A.x^dual), so X's leg is
+// fuse(A.x^dual, A.x)), the ket parts are contracted with A, the bra parts
+// and P with A* (the dual layout, same data), and the open ket/bra pairs are
+// fused again.  Same result up to rounding, fewer FLOPs (Sec. 3.2 forms the
+// rank-4 double layer; this is the single-layer variant of the same sum).
+T absorb(Ctx* ctx, const std::string& name, T X, std::vector<int> lx, std::vector<int> la, T site,
+         Layout* site_dual, bst_prec prec, cudaStream_t s) {
+  if (site.L->rank == 4) return contract(ctx, name.c_str(), X, site, lx, la, prec, s);
+  Layout* A = site.L;
+  const int rx = X.L->rank;
+  std::vector<Leg> ul;
+  std::vector<int> groups;
+  int kpos[2], bpos[2];
+  for (int j = 0; j < rx; ++j) {
+    const int w = j == lx[0] ? 0 : j == lx[1] ? 1 : -1;
+    if (w >= 0) {
+      const Leg& sl = A->legs[la[w] + 1];
+      kpos[w] = int(ul.size());
+      ul.push_back(sl.dual());
+      bpos[w] = int(ul.size());
+      ul.push_back(sl);
+      groups.push_back(2);
+    } else {
+      ul.push_back(X.L->legs[j]);
+      groups.push_back(1);
+    }
+  }
+  Layout* XuL = make_layout(ctx, BST_U1, ul);
+  Layout* fused = nullptr;
+  DevRelayout* up = get_fuse_plan(ctx, XuL, groups, &fused);
+  release(fused);
+  BST_REQUIRE(fused == X.L, BST_E_SHAPE, "edge leg does not match the fused ket/bra legs of the site");
+  double* xu = (double*)ctx->buf("sl.Xu", sizeof(double) * std::max<int64_t>(XuL->nnz, 1), s);
+  launch_relayout(ctx, *up, xu, const_cast<double*>(X.d), 1, 1.0, 0.0, s);  // split: Xu <- X
+  T Xu{XuL, xu};
+  T Y = contract(ctx, "sl.Y", Xu, site, {kpos[0], kpos[1]}, {la[0] + 1, la[1] + 1}, prec, s);
+  auto ypos = [&](int p) {
+    int c = 0;
+    for (int q = 0; q < p; ++q) c += (q != kpos[0] && q != kpos[1]);
+    return c;
+  };
+  const int pP = int(ul.size()) - 2;  // A's P leg opens A's part of Y
+  T Q = contract(ctx, "sl.Q", Y, T{site_dual, site.d}, {ypos(bpos[0]), ypos(bpos[1]), pP}, {la[0] + 1, la[1] + 1, 0},
+                 prec, s);
+  // Q = [X's other legs, ket d1, ket d2, bra d1, bra d2] -> pair up and fuse
+  const int no = rx - 2;
+  std::vector<int> perm;
+  for (int i = 0; i < no; ++i) perm.push_back(i);
+  for (int i : {no, no + 2, no + 1, no + 3}) perm.push_back(i);
+  Layout* QpL = nullptr;
+  DevRelayout* pp = get_permute_plan(ctx, Q.L, perm, &QpL);
+  double* qp = (double*)ctx->buf("sl.Qp", sizeof(double) * std::max<int64_t>(QpL->nnz, 1), s);
+  launch_relayout(ctx, *pp, Q.d, qp, 0, 1.0, 0.0, s);
+  std::vector<int> g2(no, 1);
+  g2.push_back(2);
+  g2.push_back(2);
+  Layout* OL = nullptr;
+  DevRelayout* fp = get_fuse_plan(ctx, QpL, g2, &OL);
+  double* out = (double*)ctx->buf(name, sizeof(double) * std::max<int64_t>(OL->nnz, 1), s);
+  launch_relayout(ctx, *fp, qp, out, 0, 1.0, 0.0, s);
+  // the intern table keeps the layouts alive
+  release(QpL);
+  release(OL);
+  release(XuL);
+  return {OL, out};
+}
+
 }  // namespace
 
-static void left_move(Ctx* ctx, T* r, int64_t chi, double cutoff, bst_prec prec, T out[3], ProjResult* pres,
-                      cudaStream_t s) {
+static void left_move(Ctx* ctx, T* r, Layout* site_dual, int64_t chi, double cutoff, bst_prec prec, T out[3],
+                      ProjResult* pres, cudaStream_t s) {
   T a = r[SITE];
   T X1 = contract(ctx, "ctm.X1", r[C1], r[T1], {0}, {0}, prec, s);        // [C1.D, T1.D, T1.R]
   T X2 = contract(ctx, "ctm.X2", X1, r[T4], {0}, {0}, prec, s);           // [T1.D, T1.R, T4.R, T4.D]
-  T Q1 = contract(ctx, "ctm.Q1", X2, a, {0, 2}, {1, 0}, prec, s);         // [T1.R, T4.D, a.R, a.D]
+  T Q1 = absorb(ctx, "ctm.Q1", X2, {0, 2}, {1, 0}, a, site_dual, prec, s);         // [T1.R, T4.D, a.R, a.D]
   T Y1 = contract(ctx, "ctm.Y1", r[T1], r[C2], {2}, {0}, prec, s);        // [T1.L, T1.D, C2.D]
   T Y2 = contract(ctx, "ctm.Y2", Y1, r[T2], {2}, {0}, prec, s);           // [T1.L, T1.D, T2.L, T2.D]
-  T Q2 = contract(ctx, "ctm.Q2", Y2, a, {1, 2}, {1, 2}, prec, s);         // [T1.L, T2.D, a.L, a.D]
+  T Q2 = absorb(ctx, "ctm.Q2", Y2, {1, 2}, {1, 2}, a, site_dual, prec, s);         // [T1.L, T2.D, a.L, a.D]
   T Rt = contract(ctx, "ctm.Rt", Q1, Q2, {0, 2}, {0, 2}, prec, s);        // [T4.D, a.D | T2.D, a.D]
   T Z1 = contract(ctx, "ctm.Z1", r[T4], r[C4], {2}, {0}, prec, s);        // [T4.U, T4.R, C4.R]
   T Z2 = contract(ctx, "ctm.Z2", Z1, r[T3], {2}, {0}, prec, s);           // [T4.U, T4.R, T3.U, T3.R]
-  T Q4 = contract(ctx, "ctm.Q4", Z2, a, {1, 2}, {0, 3}, prec, s);         // [T4.U, T3.R, a.U, a.R]
+  T Q4 = absorb(ctx, "ctm.Q4", Z2, {1, 2}, {0, 3}, a, site_dual, prec, s);         // [T4.U, T3.R, a.U, a.R]
   T W1 = contract(ctx, "ctm.W1", r[T2], r[C3], {2}, {0}, prec, s);        // [T2.U, T2.L, C3.L]
   T W2 = contract(ctx, "ctm.W2", W1, r[T3], {2}, {2}, prec, s);           // [T2.U, T2.L, T3.L, T3.U]
-  T Q3 = contract(ctx, "ctm.Q3", W2, a, {1, 3}, {2, 3}, prec, s);         // [T2.U, T3.L, a.L, a.U]
+  T Q3 = absorb(ctx, "ctm.Q3", W2, {1, 3}, {2, 3}, a, site_dual, prec, s);         // [T2.U, T3.L, a.L, a.U]
   T Rb = contract(ctx, "ctm.Rb", Q4, Q3, {1, 3}, {1, 2}, prec, s);        // [T4.U, a.U | T2.U, a.U]
   const int new_flow = r[C1].L->legs[1].flow;
   int64_t pcap = Rb.L->legs[0].dim * Rb.L->legs[1].dim * chi;
@@ -125,7 +198,7 @@ static void left_move(Ctx* ctx, T* r, int64_t chi, double cutoff, bst_prec prec,
   // renormalise: C1' = X1 P, T4' = ((Pt T4) a) P, C4' = Pt (C4 T3)
   out[0] = contract(ctx, "ctm.C1n", X1, tP, {0, 1}, {0, 1}, prec, s);    // [T1.R, new]
   T W = contract(ctx, "ctm.W", tPt, r[T4], {1}, {0}, prec, s);             // [new^, a.D, T4.R, T4.D]
-  T Z = contract(ctx, "ctm.Z", W, a, {2, 1}, {0, 1}, prec, s);             // [new^, T4.D, a.R, a.D]
+  T Z = absorb(ctx, "ctm.Z", W, {2, 1}, {0, 1}, a, site_dual, prec, s);             // [new^, T4.D, a.R, a.D]
   out[1] = contract(ctx, "ctm.T4n", Z, tP, {1, 3}, {0, 1}, prec, s);     // [new^, a.R, new]
   T Y = contract(ctx, "ctm.Y", r[C4], r[T3], {1}, {0}, prec, s);           // [C4.U, T3.U, T3.R]
   out[2] = contract(ctx, "ctm.C4n", tPt, Y, {1, 2}, {0, 1}, prec, s);    // [new^, T3.R]
@@ -135,7 +208,8 @@ static void left_move(Ctx* ctx, T* r, int64_t chi, double cutoff, bst_prec prec,
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double cutoff,
               bst_prec prec, bst_ctm_stats* stats, cudaStream_t s) {
   BST_REQUIRE(dir >= 0 && dir <= 4, BST_E_ARG, "dir must be 0..4");
-  BST_REQUIRE(a->rank == 4, BST_E_ARG, "site tensor must have rank 4");
+  BST_REQUIRE(a->rank == 4 || a->rank == 5, BST_E_ARG,
+              "site tensor must be the double layer a[L,U,R,D] or a single-layer A[P,L,U,R,D]");
   for (int i = 0; i < 4; ++i) {
     BST_REQUIRE(env->C[i] && env->T[i] && env->c[i] && env->t[i], BST_E_ARG, "env has a null entry");
     BST_REQUIRE(L_(env->C[i])->rank == 2 && L_(env->T[i])->rank == 3, BST_E_ARG,
@@ -159,11 +233,16 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
     T r[NROLE];
     for (int n = 0; n < NROLE; ++n) {
       const Src& src = rot[n];
-      if (is_identity(src.perm)) {
+      std::vector<int> perm = src.perm;
+      if (n == SITE && a->rank == 5) {  // the P leg stays first
+        perm.insert(perm.begin(), -1);
+        for (auto& x : perm) ++x;
+      }
+      if (is_identity(perm)) {
         r[n] = orig[src.role];
       } else {
         Layout* dst = nullptr;
-        DevRelayout* rp = get_permute_plan(ctx, orig[src.role].L, src.perm, &dst);
+        DevRelayout* rp = get_permute_plan(ctx, orig[src.role].L, perm, &dst);
         std::string nm = "ctm.rot" + std::to_string(n);
         double* buf = (double*)ctx->buf(nm, sizeof(double) * std::max<int64_t>(dst->nnz, 1), s);
         launch_relayout(ctx, *rp, orig[src.role].d, buf, 0, 1.0, 0.0, s);
@@ -173,7 +252,14 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
     }
     T out[3];
     ProjResult pr;
-    left_move(ctx, r, chi, cutoff, prec, out, &pr, s);
+    Layout* site_dual = nullptr;
+    if (a->rank == 5) {
+      std::vector<Leg> dl;
+      for (auto& l : r[SITE].L->legs) dl.push_back(l.dual());
+      site_dual = make_layout(ctx, BST_U1, dl);
+      release(site_dual);  // interned
+    }
+    left_move(ctx, r, site_dual, chi, cutoff, prec, out, &pr, s);
     // map renewed rotated roles C1, T4, C4 back to the original frame
     const int renewed[3] = {C1, T4, C4};
     for (int i = 0; i < 3; ++i) {

@@ -81,20 +81,24 @@ __global__ void permute_cols(const double* in, double* out, int c, const int* pe
 struct ProjView {
   MatView mv;
   DevRelayout rel;
+  ~ProjView() { rel.free_all(); }
 };
 
+// Sector-matrix view of a projector layout, cached in the context (freed
+// with it) by layout id and row legs.
 static ProjView* get_projview(Ctx* ctx, Layout* L, const std::vector<int>& rows, const std::vector<int>& cols) {
-  static std::mutex mu;
-  static std::map<std::string, std::unique_ptr<ProjView>> cache;  // keyed by ctx+layout
-  std::string key = std::to_string((uintptr_t)ctx) + "/" + std::to_string(L->id);
-  std::lock_guard<std::mutex> g(mu);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second.get();
-  auto pv = std::make_unique<ProjView>();
+  std::string key = std::to_string(L->id) + "/" + std::to_string(rows.size());
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->projviews.find(key);
+    if (it != ctx->projviews.end()) return it->second.get();
+  }
+  auto pv = std::make_shared<ProjView>();
   pv->mv = make_matview(L, rows, cols);
   pv->rel.upload(pv->mv.tasks);
   ProjView* raw = pv.get();
-  cache[key] = std::move(pv);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->projviews[key] = std::move(pv);
   return raw;
 }
 
@@ -242,7 +246,6 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   for (auto& x : secs) {
     x.direct = x.N <= kEigMax;
     x.b = x.direct ? x.N : kEigMax;
-    if (!x.direct && std::min<int64_t>(chi, x.N) + 16 > x.b) return false;
     x.c = x.b;
     x.v_off = vtot;
     vtot += int64_t(x.N) * x.c;
@@ -290,26 +293,18 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   setup_attrs();
   int bmax = 1;
   for (auto& x : secs) bmax = std::max(bmax, x.b);
-  if (!sp_it.empty()) {
-    // deterministic random start
-    for (auto& x : secs)
-      if (!x.direct) {
-        const int64_t n = int64_t(x.N) * x.b;
-        randn_fill<<<int(std::min<int64_t>((n + 255) / 256, 1216)), 256, 0, s>>>(Q + x.q_off, n,
-                                                                              0x5eed0000ull + uint64_t(x.cs->key + 4096));
-        count_launch(ctx);
-      }
-    double chol_flops = 0;
-    for (auto& x : sp_it) chol_flops += 2.0 * 2.0 * double(x.b) * x.b * x.b / 3.0;  // factor + inverse, FMA = 2
-    auto cholinv = [&]() {
-      ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
-      cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
-      BST_CUDA(cudaGetLastError());
-      count_launch(ctx);
-    };
-    // CholQR with an FP32 factor after each half step: the blocks N Q and
-    // N^T Z carry the condition number sigma_1/sigma_b once, not squared
-    for (int t = 0; t < iters; ++t) {
+  double chol_flops = 0;
+  for (auto& x : sp_it) chol_flops += 2.0 * 2.0 * double(x.b) * x.b * x.b / 3.0;  // factor + inverse, FMA = 2
+  auto cholinv = [&]() {
+    ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
+    cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  };
+  // CholQR with an FP32 factor after each half step: the blocks N Q and
+  // N^T Z carry the condition number sigma_1/sigma_b once, not squared
+  auto iterate = [&](int n) {
+    for (int t = 0; t < n; ++t) {
       gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
       gemm_any(ctx, "ss.gz", prec, g_gz, Z, Z, Msm, s);
       cholinv();
@@ -319,7 +314,9 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       cholinv();
       gemm_any(ctx, "ss.qy", prec, g_qy, Y, Rinv, Q, s);
     }
-    // second CholQR pass and two first-order polishes: orthonormal to FP64
+  };
+  // second CholQR pass and two first-order polishes: orthonormal to FP64
+  auto orthonormalise = [&]() {
     gemm_any(ctx, "ss.gy", prec, g_gy, Q, Q, Msm, s);
     cholinv();
     gemm_any(ctx, "ss.qy", prec, g_qy, Q, Rinv, Y, s);
@@ -332,21 +329,107 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       gemm_any(ctx, "ss.qy", prec, g_qy, src, Rinv, dst, s);
     }
     std::swap(Q, Y);  // the polished block is in Y
-    // Rayleigh-Ritz: H = (N Q)^T (N Q)
-    gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
-    gemm_any(ctx, "ss.h", rr, g_h, Z, Z, Msm, s);
+  };
+  if (!sp_it.empty()) {
+    // deterministic random start
+    for (auto& x : secs)
+      if (!x.direct) {
+        const int64_t n = int64_t(x.N) * x.b;
+        randn_fill<<<int(std::min<int64_t>((n + 255) / 256, 1216)), 256, 0, s>>>(Q + x.q_off, n,
+                                                                              0x5eed0000ull + uint64_t(x.cs->key + 4096));
+        count_launch(ctx);
+      }
   }
-  gemm_any(ctx, "ss.direct", rr, g_direct, Nm, Nm, Msm, s);
-  small_eig(ctx, rr, sp_all, Msm, Xv, lam, smtot, valtot, s);
-  // V = Q W (iterative) or W (direct)
-  if (!g_v.empty()) gemm_any(ctx, "ss.v", rr, g_v, Q, Xv, dV, s);
-  for (auto& x : secs)
-    if (x.direct)
-      BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
-                               cudaMemcpyDeviceToDevice, s));
-  std::vector<double> hl(valtot);
-  BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
-  BST_CUDA(cudaStreamSynchronize(s));
+  // Rounds of `iters` iterations, each closed by a Rayleigh-Ritz step.  A
+  // round is accepted when every Ritz pair that the truncation would keep
+  // (plus a few below it) has a residual ||N^T N v - lambda v|| at most
+  // tol * lambda_max, or when the residual has stopped falling (less than
+  // halved by a round) while within 100 tol: the floor that the iterations'
+  // arithmetic sets (the mixed-precision products) has been reached.
+  // Otherwise iteration resumes from the Ritz vectors; after max_total
+  // iterations the caller falls back to the full SVD.
+  const double tol = prec == BST_FP64 ? 3e-14 : 4e-12;
+  double prev_worst = 0;
+  const int max_total = std::max(iters, 480);
+  std::vector<double> hl(valtot), hres(valtot);
+  double* res = (double*)ctx->buf("proj.res", sizeof(double) * std::max<int64_t>(valtot, 1), s);
+  int total = 0;
+  for (int round = 0;; ++round) {
+    if (!sp_it.empty()) {
+      iterate(iters);
+      total += iters;
+      orthonormalise();
+      // Rayleigh-Ritz: H = (N Q)^T (N Q)
+      gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
+      gemm_any(ctx, "ss.h", rr, g_h, Z, Z, Msm, s);
+    }
+    gemm_any(ctx, "ss.direct", rr, g_direct, Nm, Nm, Msm, s);
+    small_eig(ctx, rr, sp_all, Msm, Xv, lam, smtot, valtot, s);
+    // V = Q W (iterative) or W (direct)
+    if (!g_v.empty()) gemm_any(ctx, "ss.v", rr, g_v, Q, Xv, dV, s);
+    for (auto& x : secs)
+      if (x.direct)
+        BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
+                                 cudaMemcpyDeviceToDevice, s));
+    BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+    BST_CUDA(cudaStreamSynchronize(s));
+    if (sp_it.empty()) break;
+    // the Ritz pairs the truncation would keep
+    double lmax = 0;
+    std::vector<std::pair<double, int>> all;
+    for (size_t i = 0; i < secs.size(); ++i)
+      for (int j = 0; j < secs[i].c; ++j) {
+        const double v = hl[secs[i].val_off + j];
+        lmax = std::max(lmax, v);
+        all.push_back({v, int(i)});
+      }
+    std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<int> kc(secs.size(), 0);
+    for (size_t t = 0; t < all.size() && int64_t(t) < chi; ++t) kc[all[t].second]++;
+    std::vector<GemmProb> g_ry, g_rg;
+    std::vector<ResProb> rp;
+    int kmax = 0;
+    for (size_t i = 0; i < secs.size(); ++i) {
+      const PSec& x = secs[i];
+      if (x.direct || kc[i] == 0) continue;
+      const int k = std::min(x.c, kc[i] + 4);
+      kmax = std::max(kmax, k);
+      const int64_t no = x.cs->off;
+      g_ry.push_back(gp(x.M, k, x.N, no, x.N, 1, x.v_off, 1, x.b, x.z_off, k, 1));   // N V[:, :k] -> Z
+      g_rg.push_back(gp(x.N, k, x.M, no, 1, x.N, x.z_off, 1, k, x.q_off, x.b, 1));   // N^T (N V) -> Y
+      rp.push_back({x.N, k, x.q_off, x.v_off, x.val_off, x.b});
+    }
+    double worst = 0;
+    if (!rp.empty()) {
+      gemm_any(ctx, "ss.ry", rr, g_ry, Nm, dV, Z, s);
+      gemm_any(ctx, "ss.rg", rr, g_rg, Nm, Z, Y, s);
+      ResProb* drp = upload_cached(ctx, "proj.rp", rp, s);
+      BST_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * valtot, s));
+      ritz_residual<<<dim3(unsigned(rp.size()), unsigned(kmax)), 256, 0, s>>>(drp, Y, dV, lam, res);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+      BST_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+      BST_CUDA(cudaStreamSynchronize(s));
+      for (auto& r : rp)
+        for (int j = 0; j < r.k; ++j) worst = std::max(worst, hres[r.val_off + j]);
+      worst = lmax > 0 ? worst / lmax : 0.0;
+    }
+    if (ctx->tune_log.size() < (1u << 20)) {
+      char line[160];
+      snprintf(line, sizeof(line), "projector subspace: %d iterations, max residual/lambda_max %.3e\n", total,
+               worst);
+      ctx->tune_log += line;
+    }
+    if (worst <= tol) break;
+    if (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol) break;
+    if (total >= max_total) return false;
+    prev_worst = worst;
+    // resume from the Ritz vectors
+    for (auto& x : secs)
+      if (!x.direct)
+        BST_CUDA(cudaMemcpyAsync(Q + x.q_off, dV + x.v_off, sizeof(double) * int64_t(x.N) * x.b,
+                                 cudaMemcpyDeviceToDevice, s));
+  }
   hSig.assign(valtot, 0.0);
   for (auto& x : secs) {
     x.s_off = x.val_off;
@@ -480,84 +563,101 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   launch_scale(ctx, Nm, pn->cmat, dss, s);
   double* dV = nullptr;
   std::vector<double> hSig;
-  bool done = false;
-  if (ctx->proj_method == 1) {
-    ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
-    done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
-  }
-  if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
-  double nss = 0;
-  BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
-  const double nscale = std::sqrt(nss);
-  BST_REQUIRE(std::isfinite(nscale) && nscale > 0, BST_E_NUMERIC, "projector: N is zero or not finite");
-  // per sector descending order of the candidates (refinement may swap
-  // values that agree to rounding); the vectors are permuted to match
-  {
-    std::vector<int> perm_all;
-    std::vector<int64_t> ptask;
-    bool any = false;
-    for (auto& x : secs) {
-      std::vector<int> ord(x.c);
-      std::iota(ord.begin(), ord.end(), 0);
-      std::stable_sort(ord.begin(), ord.end(),
-                       [&](int a, int b) { return hSig[x.s_off + a] > hSig[x.s_off + b]; });
-      for (int j = 0; j < x.c; ++j) any |= ord[j] != j;
-      std::vector<double> tmp(x.c);
-      for (int j = 0; j < x.c; ++j) tmp[j] = hSig[x.s_off + ord[j]];
-      for (int j = 0; j < x.c; ++j) hSig[x.s_off + j] = tmp[j];
-      perm_all.insert(perm_all.end(), ord.begin(), ord.end());
-    }
-    if (any) {
-      int64_t vtot = 0, po = 0;
-      for (auto& x : secs) vtot = std::max(vtot, x.v_off + int64_t(x.N) * x.c);
-      double* tmpv = (double*)ctx->buf("proj.Vperm", sizeof(double) * std::max<int64_t>(vtot, 1), s);
-      int* dperm = upload_cached(ctx, "proj.perm", perm_all, s);
-      for (auto& x : secs) {
-        permute_cols<<<x.N, 128, 0, s>>>(dV + x.v_off, tmpv + x.v_off, x.c, dperm + po);
-        po += x.c;
-      }
-      BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
-      count_launch(ctx, int(secs.size()));
-    }
-  }
-
-  // global truncation: sigma descending, |q| ascending, q ascending
+  double nscale = 0;
   struct Cand { double sv; int q; int sec; int j; };
-  std::vector<Cand> cand;
-  double smax = 0, ssum = 0;
-  for (size_t i = 0; i < secs.size(); ++i)
-    for (int j = 0; j < secs[i].c; ++j) {
-      const double v = hSig[secs[i].s_off + j];
-      BST_REQUIRE(std::isfinite(v), BST_E_NUMERIC, "projector: non-finite singular value");
-      cand.push_back({v, int(new_flow * secs[i].cs->key), int(i), j});
-      smax = std::max(smax, v);
-      ssum += v;
-    }
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
-    if (a.sv != b.sv) return a.sv > b.sv;
-    if (std::abs(a.q) != std::abs(b.q)) return std::abs(a.q) < std::abs(b.q);
-    if (a.q != b.q) return a.q < b.q;
-    return a.j < b.j;
-  });
-  std::vector<int> kcount(secs.size(), 0);
+  std::vector<int> kcount;
   int64_t kept = 0;
-  double kept_sum = 0, kmin = smax;
-  for (auto& c : cand) {
-    if (kept >= chi) break;
-    if (!(c.sv > rel_cutoff * smax) || c.sv <= 0) break;
-    kcount[c.sec]++;
-    kept++;
-    kept_sum += c.sv;
-    kmin = std::min(kmin, c.sv);
-  }
-  BST_REQUIRE(kept > 0, BST_E_NUMERIC, "projector: nothing above the cutoff");
-  for (size_t i = 0; i < secs.size(); ++i)
-    for (int j = 1; j < kcount[i]; ++j)
-      BST_REQUIRE(hSig[secs[i].s_off + j] <= hSig[secs[i].s_off + j - 1], BST_E_NUMERIC, "projector: unsorted");
-  if (ctx->proj_method == 1)
+  double kept_sum = 0, kmin = 0, smax = 0, ssum = 0;
+  // The subspace method computes the leading candidates of every sector; if
+  // the global truncation keeps states up to the edge of some sector's
+  // iterated block (fewer than 16 guard vectors left), that sector may need
+  // more candidates than were computed: the projector is redone with the
+  // full FP64 SVD.
+  bool use_subspace = ctx->proj_method == 1;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    bool done = false;
+    if (use_subspace) {
+      ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
+      done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
+    }
+    if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
+    if (attempt == 0) {
+      double nss = 0;
+      BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
+      nscale = std::sqrt(nss);
+      BST_REQUIRE(std::isfinite(nscale) && nscale > 0, BST_E_NUMERIC, "projector: N is zero or not finite");
+    }
+    // per sector descending order of the candidates (refinement may swap
+    // values that agree to rounding); the vectors are permuted to match
+    {
+      std::vector<int> perm_all;
+      std::vector<int64_t> ptask;
+      bool any = false;
+      for (auto& x : secs) {
+        std::vector<int> ord(x.c);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return hSig[x.s_off + a] > hSig[x.s_off + b]; });
+        for (int j = 0; j < x.c; ++j) any |= ord[j] != j;
+        std::vector<double> tmp(x.c);
+        for (int j = 0; j < x.c; ++j) tmp[j] = hSig[x.s_off + ord[j]];
+        for (int j = 0; j < x.c; ++j) hSig[x.s_off + j] = tmp[j];
+        perm_all.insert(perm_all.end(), ord.begin(), ord.end());
+      }
+      if (any) {
+        int64_t vtot = 0, po = 0;
+        for (auto& x : secs) vtot = std::max(vtot, x.v_off + int64_t(x.N) * x.c);
+        double* tmpv = (double*)ctx->buf("proj.Vperm", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+        int* dperm = upload_cached(ctx, "proj.perm", perm_all, s);
+        for (auto& x : secs) {
+          permute_cols<<<x.N, 128, 0, s>>>(dV + x.v_off, tmpv + x.v_off, x.c, dperm + po);
+          po += x.c;
+        }
+        BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
+        count_launch(ctx, int(secs.size()));
+      }
+    }
+
+    // global truncation: sigma descending, |q| ascending, q ascending
+    std::vector<Cand> cand;
+    smax = 0;
+    ssum = 0;
     for (size_t i = 0; i < secs.size(); ++i)
-      BST_REQUIRE(secs[i].direct || kcount[i] + 16 <= secs[i].c, BST_E_NUMERIC,
-                  "projector: kept states reach the edge of the iterated subspace");
+      for (int j = 0; j < secs[i].c; ++j) {
+        const double v = hSig[secs[i].s_off + j];
+        BST_REQUIRE(std::isfinite(v), BST_E_NUMERIC, "projector: non-finite singular value");
+        cand.push_back({v, int(new_flow * secs[i].cs->key), int(i), j});
+        smax = std::max(smax, v);
+        ssum += v;
+      }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+      if (a.sv != b.sv) return a.sv > b.sv;
+      if (std::abs(a.q) != std::abs(b.q)) return std::abs(a.q) < std::abs(b.q);
+      if (a.q != b.q) return a.q < b.q;
+      return a.j < b.j;
+    });
+    kcount.assign(secs.size(), 0);
+    kept = 0;
+    kept_sum = 0;
+    kmin = smax;
+    for (auto& c : cand) {
+      if (kept >= chi) break;
+      if (!(c.sv > rel_cutoff * smax) || c.sv <= 0) break;
+      kcount[c.sec]++;
+      kept++;
+      kept_sum += c.sv;
+      kmin = std::min(kmin, c.sv);
+    }
+    BST_REQUIRE(kept > 0, BST_E_NUMERIC, "projector: nothing above the cutoff");
+    for (size_t i = 0; i < secs.size(); ++i)
+      for (int j = 1; j < kcount[i]; ++j)
+        BST_REQUIRE(hSig[secs[i].s_off + j] <= hSig[secs[i].s_off + j - 1], BST_E_NUMERIC, "projector: unsorted");
+    bool edge = false;
+    if (done)
+      for (size_t i = 0; i < secs.size(); ++i) edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c);
+    if (!edge) break;
+    use_subspace = false;
+  }
 
   std::vector<std::pair<int, int>> order;  // (charge, sec)
   for (size_t i = 0; i < secs.size(); ++i)

@@ -31,17 +31,22 @@ class Network:
     site_specs: leg dicts of A and R; x: (charges, degeneracies) of the env
     bond; draw(name, n) -> float64 numpy array of n values for tensor `name`.
     Env buffers get capacity for renewed tensors with chi-sized env legs.
+
+    single_layer: the double layer is never formed; the move takes the
+    single-layer site A'[P, l, u, r', d] = sum_r A[p,l,u,r,d] R[r,r',s] with
+    (p, s) fused into P, and contracts ket and bra separately.
     """
 
-    def __init__(self, ctx, site_specs, x, chi, draw, device="cuda:0"):
+    def __init__(self, ctx, site_specs, x, chi, draw, device="cuda:0", single_layer=False):
         self.ctx, self.chi, self.device = ctx, chi, device
+        self.single_layer = single_layer
         self.A = ctx.layout(site_specs["A"])
         self.R = ctx.layout(site_specs["R"])
         self.A_host = torch.from_numpy(draw("A", self.A.nnz)).pin_memory()
         self.R_host = torch.from_numpy(draw("R", self.R.nnz)).pin_memory()
         self.A_dev = self.A_host.to(device)
         self.R_dev = self.R_host.to(device)
-        self.aL, self.a = ctx.double_layer(self.A, self.A_dev, self.R, self.R_dev)
+        self.build_site()
         legs = env_legs(x[0], x[1], self.aL.legs)
         self.L0, self.host0 = {}, {}
         caps = {}
@@ -56,6 +61,19 @@ class Network:
             caps[r] = max(cap, L.nnz)
         self.env = bst.Env(ctx, self.L0, {r: self.host0[r].to(device) for r in ROLES}, caps)
         self.pristine = {r: self.env.buf[r].clone() for r in ROLES}
+
+    def build_site(self):
+        """The site tensor the move takes: the double layer a (with the
+        remover absorbed), or the single-layer A' (single_layer=True)."""
+        ctx = self.ctx
+        if not self.single_layer:
+            self.aL, self.a = ctx.double_layer(self.A, self.A_dev, self.R, self.R_dev)
+            self.siteL, self.site = self.aL, self.a
+            return
+        L1, t1 = ctx.contract(self.A, self.A_dev, self.R, self.R_dev, (3,), (0,))   # [p,l,u,d,r',s]
+        L2, t2 = ctx.permute(L1, t1, (0, 5, 1, 2, 4, 3))                            # [p,s,l,u,r',d]
+        self.siteL, self.site = ctx.fuse(L2, t2, (2, 1, 1, 1, 1))                   # [P,l,u,r',d]
+        self.aL = ctx.double_layer_layout(self.siteL)
 
     def reset(self):
         """Restore the input environment (device to device)."""
@@ -77,9 +95,11 @@ class Network:
         self.env.L = dict(self.L0)
         return nb
 
-    def step(self, prec, rel_cutoff=1e-14, with_double_layer=True):
-        """One pass of the hot path: double layer (with remover) and the full
-        move LEFT, RIGHT, UP, DOWN."""
+    def step(self, prec, rel_cutoff=1e-14, with_double_layer=True, direction=None):
+        """One pass of the hot path: the site tensor (double layer with
+        remover, or the single-layer site) and the full move LEFT, RIGHT, UP,
+        DOWN (or one `direction`)."""
         if with_double_layer:
-            self.aL, self.a = self.ctx.double_layer(self.A, self.A_dev, self.R, self.R_dev)
-        return self.ctx.ctm_move(self.env, self.aL, self.a, bst.ALL, self.chi, rel_cutoff, prec)
+            self.build_site()
+        d = bst.ALL if direction is None else direction
+        return self.ctx.ctm_move(self.env, self.siteL, self.site, d, self.chi, rel_cutoff, prec)
