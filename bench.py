@@ -102,6 +102,22 @@ def dist_env():
     return rank, world, local
 
 
+def job_ms(ms_local, world):
+    """Whole-job time per step: the slowest rank's (MAX over ranks, gloo)."""
+    if world <= 1:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms, world):
+    """Replicas: every rank completes one move per step, so the job rate is
+    world moves per (slowest) step time."""
+    return world * 1e3 / ms
+
+
 def cpu_oracle_time(steps=1, warmup=0):
     """Dense FP64 oracle: double layer + full move of the same workload on the
     host cores; returns (seconds per move list, cores)."""
@@ -419,14 +435,13 @@ def run_ours(args):
             one_step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         wall = time.perf_counter() - t0
     launches = (ctx.launches - l0) // args.steps
     ms = [a.elapsed_time(b_) for a, b_ in ev]
     ms_step = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = job_ms(ms_step, world)
 
     # per-kernel-class profile of one extra step (events around every launch)
     ctx.profile(True)
@@ -509,7 +524,7 @@ def run_ours(args):
         times, cores = cpu_oracle_time(1, 0)
         cpu = {"value": 1.0 / times[0], "unit": "moves/s", "cores": cores, "kind": "oracle",
                "sample": "one full move (double layer + L,R,U,D) of the same workload, dense numpy FP64"}
-    v = world * 1e3 / ms_step
+    v = job_value(ms_step, world)
     line = {
         "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

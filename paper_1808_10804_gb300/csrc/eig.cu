@@ -45,20 +45,30 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   int* order = (int*)(red + 1024);
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* H = in + pr.in_off;
-  // scale by the largest diagonal entry (in FP64) so FP32 cannot overflow
+  // scale by the largest diagonal entry (in FP64) so FP32 cannot overflow;
+  // every loop over the matrix is flat over all threads so the global loads
+  // are issued together
+  __shared__ double dmax[32];
+  {
+    double m = 0;
+    for (int i = tid; i < b; i += nt) m = fmax(m, fabs(H[(long long)i * b + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) dmax[tid >> 5] = m;
+  }
+  __syncthreads();
   __shared__ double hscale;
   if (tid == 0) {
     double m = 0;
-    for (int i = 0; i < b; ++i) m = fmax(m, fabs(H[(long long)i * b + i]));
+    for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, dmax[w]);
     hscale = m > 0 ? m : 1.0;
   }
   __syncthreads();
   const double inv = 1.0 / hscale;
-  for (int i = 0; i < bp; ++i)
-    for (int j = tid; j < bp; j += nt) {
-      A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
-      V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
-    }
+  for (int q = tid; q < bp * bp; q += nt) {
+    const int i = q / bp, j = q - i * bp;
+    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
+    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
   __syncthreads();
   const int npair = bp / 2;
   constexpr float kTau = 1e-5f;
@@ -167,8 +177,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   }
   __syncthreads();
   double* X = out + pr.out_off;
-  for (int i = 0; i < b; ++i)
-    for (int jn = tid; jn < b; jn += nt) X[(long long)i * b + jn] = double(V[i * ld + order[jn]]);
+  for (int q = tid; q < b * b; q += nt) {
+    const int i = q / b, jn = q - i * b;
+    X[q] = double(V[i * ld + order[jn]]);
+  }
   for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]) * hscale;
 }
 
@@ -192,17 +204,21 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
   double* e = E + pr.in_off;
   double* l = lam + pr.val_off;
   __shared__ double smax;
-  if (threadIdx.x == 0) smax = 0;
-  __syncthreads();
+  __shared__ double wmax[32];
+  double m = 0;
   for (int i = threadIdx.x; i < b; i += blockDim.x) {
     const double rii = 1.0 - xx[(long long)i * b + i];
-    l[i] = s[(long long)i * b + i] / (1.0 - rii);
+    const double li = s[(long long)i * b + i] / (1.0 - rii);
+    l[i] = li;
+    m = fmax(m, fabs(li));
   }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0;
-    for (int i = 0; i < b; ++i) m = fmax(m, fabs(l[i]));
-    smax = m;
+    double mm = 0;
+    for (int w = 0; w < int(blockDim.x + 31) / 32; ++w) mm = fmax(mm, wmax[w]);
+    smax = mm;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
@@ -243,9 +259,9 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
     dscd[i] = d > 0 ? 1.0 / sqrt(d) : 1.0;
   }
   __syncthreads();
-  for (int i = 0; i < b; ++i) {
-    const double si = dscd[i];
-    for (int j = tid; j < b; j += nt) L[i * ld + j] = float(M[(long long)i * b + j] * si * dscd[j]);
+  for (int q = tid; q < b * b; q += nt) {
+    const int i = q / b, j = q - i * b;
+    L[i * ld + j] = float(M[q] * dscd[i] * dscd[j]);
   }
   __syncthreads();
   // Blocked right-looking factorisation with 32-wide panels: warp 0
@@ -369,10 +385,9 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
   // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
   // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
   double* R = out + pr.out_off;
-  for (int i = 0; i < b; ++i) {
-    const double si = dscd[i];
-    for (int j = tid; j < b; j += nt)
-      R[(long long)i * b + j] = (drop[i] || drop[j] || j < i) ? 0.0 : si * double(Li[j * ld + i]);
+  for (int q = tid; q < b * b; q += nt) {
+    const int i = q / b, j = q - i * b;
+    R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : dscd[i] * double(Li[j * ld + i]);
   }
 }
 

@@ -2,9 +2,12 @@
 // truncated as in corboz14).
 //
 // N = Rtop^T Rbot over the left cut is block diagonal in the charge through
-// the right cut.  Each sector is decomposed with an FP64 SVD on the GPU
-// (cuSOLVER gesvd), the chi largest singular values over all sectors are
-// kept (a host decision: one stream synchronisation), and
+// the right cut.  The leading singular pairs of every sector come from a
+// residual-controlled subspace iteration on N^T N with an FP64 Rayleigh-Ritz
+// step (factors_subspace; sectors of dimension <= 160 are decomposed
+// directly), or from cuSOLVER's FP64 gesvd (factors_gesvd, on request or as
+// the fallback); the chi largest singular values over all sectors are kept
+// (a host decision: one stream synchronisation), and
 //     P  = Rbot V S^-1/2,      Pt = S^-1/2 U^T Rtop^T
 // are formed per sector with the grouped GEMM, then scattered into their
 // canonical block layouts.  The sign of every kept left singular vector is

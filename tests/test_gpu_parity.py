@@ -302,3 +302,27 @@ def test_full_move_fp64_d6chi72(bst, ctx):
     ctx.ctm_move(env, aL, ad, 4, cfg["chi"], prec="fp64")
     ctx.sync()
     compare_env(env, ref, ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4"), TOL64)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("ozaki", TOL_MOVE_OZ)])
+def test_repeated_move_same_result(bst, prec, tol):
+    """A second move on the same layouts (cached plans, buffers and projector
+    views) agrees with the oracle like the first."""
+    c = bst.Context(0)
+    try:
+        cfg, aL, ad, env = gpu_env(bst, c, "d6chi72", 72)
+        ref = octm.move(oracle_net("d6chi72"), "L", cfg["chi"])
+        pristine = {r: env.data(r).clone() for r in env.L}
+        L0 = dict(env.L)
+        c.ctm_move(env, aL, ad, 0, cfg["chi"], prec=prec)
+        compare_env(env, ref, ("C1", "T4", "C4"), tol)
+        for r in L0:
+            env.buf[r][:pristine[r].numel()].copy_(pristine[r])
+        env.L = dict(L0)
+        n0 = len(c.tuning_log().splitlines())
+        c.ctm_move(env, aL, ad, 0, cfg["chi"], prec=prec)
+        c.sync()
+        compare_env(env, ref, ("C1", "T4", "C4"), tol)
+        assert len(c.tuning_log().splitlines()) > n0
+    finally:
+        c.close()
