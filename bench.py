@@ -370,6 +370,50 @@ def single_layer_bench(bst, dev, local, prec, steps, warmup, flush, pk):
         torch.cuda.empty_cache()
 
 
+def run_profile_target(args):
+    """--quick with --only: warm-up and steps of one workload, nothing else
+    (a small, fixed command for profilers)."""
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    from paper_1808_10804_gb300 import build as b
+    b.build()
+    from paper_1808_10804_gb300 import bst
+    from workloads import su2_config, u1_config, values
+    ctx = bst.Context(local)
+    try:
+        if args.only == "batch":
+            inst = batch_instances(bst, ctx, dev)
+            la, lb = BATCH_LEGS
+            As, as_, Bs, bs = ([i[k] for i in inst] for k in range(4))
+            Cls, cs = ctx.contract_batched(As, as_, Bs, bs, la, lb, prec=args.prec)
+            for _ in range(args.warmup + args.steps):
+                ctx.contract_batched(As, as_, Bs, bs, la, lb, prec=args.prec, Cls=Cls, cs=cs)
+        elif args.only == "su2":
+            cfg = su2_config("D10chi150")
+            K, X = bst.Leg(1, *cfg["k"]), bst.Leg(1, *cfg["x"])
+            legs = {"C1": [X.dual(), X.dual()], "T1": [X, K.dual(), X.dual()], "T4": [X, K.dual(), X.dual()],
+                    "A": [K, K, K.dual(), K.dual()]}
+            L = {n: ctx.layout(l, group="su2") for n, l in legs.items()}
+            d = {n: torch.tensor(values(0, n, L[n].nnz), dtype=torch.float64, device=dev) for n in L}
+            for _ in range(args.warmup + args.steps):
+                LX1, x1 = ctx.contract(L["C1"], d["C1"], L["T1"], d["T1"], (0,), (0,), prec=args.prec)
+                LX2, x2 = ctx.contract(LX1, x1, L["T4"], d["T4"], (0,), (0,), prec=args.prec)
+                ctx.contract(LX2, x2, L["A"], d["A"], (0, 2), (1, 0), prec=args.prec)
+        elif args.only == "large":
+            from paper_1808_10804_gb300.ctmrg import Network
+            cfg = u1_config("d8chi256")
+            net = Network(ctx, {"A": cfg["A"], "R": cfg["R"]}, cfg["x"], cfg["chi"], lambda n, k: values(0, n, k),
+                          device=dev, single_layer=True)
+            for _ in range(args.warmup + args.steps):
+                net.reset()
+                net.step(args.prec, direction=bst.LEFT)
+        torch.cuda.synchronize()
+    finally:
+        ctx.close()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -562,8 +606,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-contraction report")
     ap.add_argument("--quick", action="store_true", help="warm-up and steps only, no report (for profilers)")
+    ap.add_argument("--only", default="ctm", choices=["ctm", "batch", "su2", "large"],
+                    help="with --quick: the workload to run (CTMRG move, batched contractions, SU(2) corner, "
+                         "large single-layer move)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.quick and args.only != "ctm":
+        run_profile_target(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -8,9 +8,10 @@
 // A product of two digits is an integer below 2^16 in magnitude, exact in
 // FP32.  The GEMM sums the 15 digit products with i + j <= 4 by diagonal
 // d = i + j (weight 2^-16-9d) in tensor memory:
-//   * d = 0, 1, 2 are read out every 32 K (one pipeline stage), where their
-//     FP32 sums are exact integers of magnitude <= 3 * 2^21, and added into
-//     32-bit integer registers (K <= 10000 keeps those from overflowing);
+//   * d = 0, 1, 2 are read out every 64 K (two pipeline stages), where their
+//     FP32 sums are exact integers of magnitude <= 3 * 2^22 < 2^24, and
+//     added into one 64-bit integer per output (K <= 10000 keeps it from
+//     overflowing);
 //   * d = 3, 4 carry weights <= 2^-27 of the leading term and accumulate in
 //     FP32 over the whole K.
 // The epilogue forms the result with 64-bit integer arithmetic and one
@@ -18,7 +19,7 @@
 //
 // Kernel: one 128 x 64 output tile per CTA; warp 0 drives TMA (64-byte
 // swizzled K-major tiles, 3-stage ring), warp 1 issues tcgen05.mma from one
-// thread, warps 2..5 drain tensor memory.  All waits are bounded: on expiry
+// thread, warps 2..9 drain tensor memory.  All waits are bounded: on expiry
 // the kernel records BST_E_TIMEOUT in the context's error word, lets its
 // copies drain (bounded), frees tensor memory and returns.
 #include <cuda.h>
@@ -168,11 +169,6 @@ __device__ __forceinline__ double pow2i(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// exact FP32 integer (|v| <= 2^22) -> int32
-__device__ __forceinline__ int f2i_exact(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
-
 struct Smem {
   alignas(1024) uint8_t stage[kStages][kStageBytes];
   uint64_t full[kStages], empty[kStages];
@@ -249,11 +245,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
+    // d0..d2 are drained every pair of K chunks (64 K): their FP32 sums stay
+    // exact integers below 2^24 (at most 3 * 64 products of magnitude
+    // <= 2^16 per diagonal entry)
     if (lane == 0 && nk > 0) {
       for (int c = 0; c < nk; ++c) {
-        const int s = c % kStages, buf = c & 1;
+        const int s = c % kStages, pc = c >> 1, buf = pc & 1;
+        const bool first = (c & 1) == 0;
         if (!mbar_wait(&sm.full[s], (c / kStages) & 1, abort_flag, err)) break;
-        if (c >= 2 && !mbar_wait(&sm.acc_empty[buf], ((c >> 1) - 1) & 1, abort_flag, err)) break;
+        if (first && pc >= 2 && !mbar_wait(&sm.acc_empty[buf], ((pc >> 1) - 1) & 1, abort_flag, err)) break;
         tc_fence_after();
         const uint32_t a0 = smem_u32(sm.stage[s]);
         const uint32_t b0 = a0 + kSlices * kABytes;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t acc;
               if (d <= 2) {
                 col = kColD0 + d * 2 * kTN + buf * kTN;
-                acc = (ks > 0 || i > 0) ? 1u : 0u;
+                acc = (!first || ks > 0 || i > 0) ? 1u : 0u;
               } else {
                 col = kColD3 + (d - 3) * kTN;
                 acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         mma_commit(&sm.empty[s]);
-        mma_commit(&sm.acc_full[buf]);
+        if (!first || c == nk - 1) mma_commit(&sm.acc_full[buf]);
       }
     }
   } else {
@@ -294,24 +294,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int j = 0; j < kHalf; ++j) T[j] = 0;
     bool ok = true;
-    for (int c = 0; c < nk && ok; ++c) {
-      const int buf = c & 1;
-      ok = mbar_wait(&sm.acc_full[buf], (c >> 1) & 1, abort_flag, err);
+    const int npair = (nk + 1) >> 1;
+    for (int p = 0; p < npair && ok; ++p) {
+      const int buf = p & 1;
+      ok = mbar_wait(&sm.acc_full[buf], (p >> 1) & 1, abort_flag, err);
       if (!ok) break;
       tc_fence_after();
       uint32_t v[32];
+      // exact FP32 integers below 2^24: one round-to-nearest conversion each
       tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
       tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += (long long)f2i_exact(v[j]) << 18;
+      for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
       tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
       tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += (long long)f2i_exact(v[j]) << 9;
+      for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
       tmem_ld32(lane_base + kColD2 + buf * kTN + c0, v);
       tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));  // exact, |v| < 2^23
+      for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));
       tc_fence_before();
       mbar_arrive(&sm.acc_empty[buf]);
     }
