@@ -356,11 +356,11 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   const int max_total = std::max(iters, 480);
   std::vector<double> hl(valtot), hres(valtot);
   double* res = (double*)ctx->buf("proj.res", sizeof(double) * std::max<int64_t>(valtot, 1), s);
-  int total = 0;
+  int total = 0, steps = iters;
   for (int round = 0;; ++round) {
     if (!sp_it.empty()) {
-      iterate(iters);
-      total += iters;
+      iterate(steps);
+      total += steps;
       orthonormalise();
       // Rayleigh-Ritz: H = (N Q)^T (N Q)
       gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
@@ -426,6 +426,17 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     if (worst <= tol) break;
     if (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol) break;
     if (total >= max_total) return false;
+    // length of the next round: from the second round on, extrapolate the
+    // residual's geometric decay per step to half the tolerance (at least
+    // `iters`, at most 6 * iters steps), so slowly converging sectors are
+    // checked with few Rayleigh-Ritz rounds
+    int next = iters;
+    if (round > 0 && worst > 0 && prev_worst > worst) {
+      const double rho = std::pow(worst / prev_worst, 1.0 / steps);
+      const double need = std::log(0.5 * tol / worst) / std::log(rho);
+      if (std::isfinite(need)) next = int(std::min<double>(6.0 * iters, std::max<double>(iters, std::ceil(need))));
+    }
+    steps = std::min(next, std::max(1, max_total - total));
     prev_worst = worst;
     // resume from the Ritz vectors
     for (auto& x : secs)
