@@ -50,6 +50,7 @@ Ctx::~Ctx() {
   for (auto& kv : gplans) kv.second->free_all();
   gplans.clear();
   for (auto& kv : bufs) kv.second.free_all();
+  for (auto& kv : su2_weights) kv.second.free_all();
   for (auto& kv : interned) delete kv.second;
   for (auto e : evpool) cudaEventDestroy(e);
   if (d_err) cudaFree(d_err);
@@ -523,7 +524,6 @@ bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const dou
                         double rel_cutoff, bst_prec prec, bst_ctm_stats* stats, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && a_layout && a && env, BST_E_ARG, "null argument");
-    require_u1(L_(a_layout));
     BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
     Ctx* c = C_(ctx);
     set_dev(c);

@@ -207,6 +207,7 @@ struct Ctx {
   std::map<std::string, std::shared_ptr<OzakiPlan>> ozplans;  // deleter bound in gemm_ozaki.cu
   std::map<std::string, std::shared_ptr<Su2Plan>> su2plans;   // deleter bound in su2.cu
   std::map<std::string, std::shared_ptr<ProjView>> projviews; // deleter bound in projector.cu
+  std::map<uint64_t, DevBuf> su2_weights;  // SU(2) layout id -> per-element 2J+1 (norms)
   int* d_err = nullptr;                     // device error word
   std::atomic<int64_t> launches{0};
   void* cusolver = nullptr;
@@ -272,6 +273,13 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
                          int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
                          cudaStream_t s);
 
+// SU(2): projectors from the reduced SVD per coupled spin J, truncated by
+// whole multiplets to total dimension chi_total; P and Pt land in context
+// buffers (*p, *pt); the new leg is incoming on P
+ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
+                         int64_t chi_total, double rel_cutoff, bst_prec prec, double** p, double** pt,
+                         cudaStream_t s);
+
 void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, double* lam, bst_prec prec,
                      cudaStream_t s);
 
@@ -305,6 +313,7 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
 void launch_scale(Ctx* ctx, double* x, int64_t n, const double* dev_scalar_inv, cudaStream_t s);
 void launch_sumsq(Ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStream_t s);
 void launch_fill(Ctx* ctx, double* x, int64_t n, double v, cudaStream_t s);
+void launch_sumsq_w(Ctx* ctx, const double* x, const double* w, int64_t n, double* dev_out, cudaStream_t s);
 
 inline void count_launch(Ctx* ctx, int n = 1) { ctx->launches += n; }
 

@@ -84,15 +84,42 @@ struct T {
 // c = a.legs(la) * b.legs(lb); result in a named context buffer
 T contract(Ctx* ctx, const char* name, T a, T b, std::vector<int> la, std::vector<int> lb, bst_prec prec,
            cudaStream_t s) {
+  if (a.L->group == BST_SU2) {
+    Layout* C = su2_contract_layout(ctx, a.L, b.L, la, lb);
+    double* out = (double*)ctx->buf(name, sizeof(double) * std::max<int64_t>(C->nnz, 1), s);
+    su2_contract(ctx, a.L, a.d, b.L, b.d, la, lb, prec, 1.0, 0.0, C, out, s);
+    return {C, out};
+  }
   ContractPlan* p = get_contract_plan(ctx, a.L, b.L, la, lb);
   double* out = (double*)ctx->buf(name, sizeof(double) * std::max<int64_t>(p->C->nnz, 1), s);
   run_contract(ctx, p, a.d, b.d, prec, 1.0, 0.0, out, s);
   return {p->C, out};
 }
 
-void normalise(Ctx* ctx, double* x, int64_t n, cudaStream_t s) {
+// Divide by the Frobenius norm of the full tensor; for SU(2) that is
+// sum over blocks of (2J+1) times the squared reduced block (||c||^2 = 2J+1,
+// blocks orthogonal).
+void normalise(Ctx* ctx, Layout* L, double* x, cudaStream_t s) {
+  const int64_t n = L->nnz;
   double* ss = (double*)ctx->buf("ctm.sumsq", sizeof(double), s);
-  launch_sumsq(ctx, x, n, ss, s);
+  if (L->group == BST_SU2) {
+    DevBuf& wb = ctx->su2_weights[L->id];
+    if (!wb.p) {
+      int nin = 0;
+      for (auto& l : L->legs) nin += l.flow == 1;
+      const int jpos = std::max(nin - 2, 0);
+      std::vector<double> w(std::max<int64_t>(n, 1), 1.0);
+      for (int64_t b = 0; b < L->nblocks; ++b) {
+        const int64_t e = b + 1 < L->nblocks ? L->offset[b + 1] : n;
+        for (int64_t i = L->offset[b]; i < e; ++i) w[i] = double(L->tree[b * L->ntree + jpos] + 1);
+      }
+      wb.get(sizeof(double) * w.size(), s);
+      BST_CUDA(cudaMemcpy(wb.p, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
+    }
+    launch_sumsq_w(ctx, x, (const double*)wb.p, n, ss, s);
+  } else {
+    launch_sumsq(ctx, x, n, ss, s);
+  }
   launch_scale(ctx, x, n, ss, s);
 }
 
@@ -188,12 +215,18 @@ static void left_move(Ctx* ctx, T* r, Layout* site_dual, int64_t chi, double cut
   T W2 = contract(ctx, "ctm.W2", W1, r[T3], {2}, {2}, prec, s);           // [T2.U, T2.L, T3.L, T3.U]
   T Q3 = absorb(ctx, "ctm.Q3", W2, {1, 3}, {2, 3}, a, site_dual, prec, s);         // [T2.U, T3.L, a.L, a.U]
   T Rb = contract(ctx, "ctm.Rb", Q4, Q3, {1, 3}, {1, 2}, prec, s);        // [T4.U, a.U | T2.U, a.U]
-  const int new_flow = r[C1].L->legs[1].flow;
-  int64_t pcap = Rb.L->legs[0].dim * Rb.L->legs[1].dim * chi;
-  int64_t ptcap = Rt.L->legs[0].dim * Rt.L->legs[1].dim * chi;
-  double* P = (double*)ctx->buf("ctm.P", sizeof(double) * pcap, s);
-  double* Pt = (double*)ctx->buf("ctm.Pt", sizeof(double) * ptcap, s);
-  *pres = svd_projector(ctx, Rt.L, Rt.d, Rb.L, Rb.d, 2, chi, cutoff, new_flow, prec, P, Pt, s);
+  double *P = nullptr, *Pt = nullptr;
+  if (a.L->group == BST_SU2) {
+    // chi is the total dimension; the new leg is incoming on P
+    *pres = su2_projector(ctx, Rt.L, Rt.d, Rb.L, Rb.d, 2, chi, cutoff, prec, &P, &Pt, s);
+  } else {
+    const int new_flow = r[C1].L->legs[1].flow;
+    int64_t pcap = Rb.L->legs[0].dim * Rb.L->legs[1].dim * chi;
+    int64_t ptcap = Rt.L->legs[0].dim * Rt.L->legs[1].dim * chi;
+    P = (double*)ctx->buf("ctm.P", sizeof(double) * pcap, s);
+    Pt = (double*)ctx->buf("ctm.Pt", sizeof(double) * ptcap, s);
+    *pres = svd_projector(ctx, Rt.L, Rt.d, Rb.L, Rb.d, 2, chi, cutoff, new_flow, prec, P, Pt, s);
+  }
   T tP{pres->P, P}, tPt{pres->Pt, Pt};
   // renormalise: C1' = X1 P, T4' = ((Pt T4) a) P, C4' = Pt (C4 T3)
   out[0] = contract(ctx, "ctm.C1n", X1, tP, {0, 1}, {0, 1}, prec, s);    // [T1.R, new]
@@ -202,7 +235,7 @@ static void left_move(Ctx* ctx, T* r, Layout* site_dual, int64_t chi, double cut
   out[1] = contract(ctx, "ctm.T4n", Z, tP, {1, 3}, {0, 1}, prec, s);     // [new^, a.R, new]
   T Y = contract(ctx, "ctm.Y", r[C4], r[T3], {1}, {0}, prec, s);           // [C4.U, T3.U, T3.R]
   out[2] = contract(ctx, "ctm.C4n", tPt, Y, {1, 2}, {0, 1}, prec, s);    // [new^, T3.R]
-  for (int i = 0; i < 3; ++i) normalise(ctx, const_cast<double*>(out[i].d), out[i].L->nnz, s);
+  for (int i = 0; i < 3; ++i) normalise(ctx, out[i].L, const_cast<double*>(out[i].d), s);
 }
 
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double cutoff,
@@ -215,6 +248,15 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
     BST_REQUIRE(L_(env->C[i])->rank == 2 && L_(env->T[i])->rank == 3, BST_E_ARG,
                 "env ranks must be 2 (C) and 3 (T)");
   }
+  if (a->group == BST_SU2) {
+    // quarter turns permute legs, which for SU(2) blocks means recoupling
+    // their trees: not implemented, so only the LEFT move runs
+    BST_REQUIRE(dir == 0, BST_E_UNSUPPORTED, "SU(2): only the LEFT move (dir 0) is implemented");
+    BST_REQUIRE(a->rank == 4, BST_E_UNSUPPORTED, "SU(2): the site must be the double layer a[L,U,R,D]");
+  }
+  for (int i = 0; i < 4; ++i)
+    BST_REQUIRE(L_(env->C[i])->group == a->group && L_(env->T[i])->group == a->group, BST_E_ARG,
+                "environment and site belong to different symmetry groups");
   if (stats) memset(stats, 0, sizeof(*stats));
   std::vector<int> seq;
   if (dir == 4) seq = {0, 2, 1, 3};  // LEFT, RIGHT, UP, DOWN

@@ -760,6 +760,355 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   return res;
 }
 
+// ---------------------------------------------------------------------------
+// SU(2) projector
+//
+// N = Rt^T Rb over the left cut, computed by the SU(2) contraction, has its
+// right-cut legs of Rt (beta) outgoing and those of Rb (beta') incoming, so
+// its canonical blocks are already in matrix form: the CGC of a block is
+// sum_M <beta'-tree|J M><beta-tree|J M>, and N is the direct sum over the
+// coupled spin J of reduced matrices N_J (rows: beta sector tuples with their
+// tree intermediates and reduced indices; columns: the same for beta') times
+// a projector of rank 2J+1.  The singular values of N are those of the N_J,
+// each 2J+1 times; the singular vectors are the reduced ones times the
+// coupled states (Sec. 2: SU(2) blocks store reduced tensors only).
+//   * per J: the same leading-pair solvers as U(1) (subspace iteration or
+//     gesvd);
+//   * truncation by whole multiplets: by descending sigma (ties: smaller J,
+//     then index), a multiplet is kept while the kept total dimension
+//     sum (2J+1) stays <= chi_total; one that would overflow is skipped, so no
+//     multiplet is cut;
+//   * V[beta'^dual..., new] and Ut[new^dual, beta^dual...] are SU(2) tensors
+//     whose reduced blocks are the gauge-fixed V_J S^-1/2 and (U_J S^-1/2)^T
+//     (their CGC tensors are exactly the coupled states above), and
+//     P = Rb . V, Pt = Ut . Rt by the SU(2) contraction.
+ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
+                         int64_t chi_total, double rel_cutoff, bst_prec prec, double** p_out, double** pt_out,
+                         cudaStream_t s) {
+  BST_REQUIRE(Rt->group == BST_SU2 && Rb->group == BST_SU2, BST_E_ARG, "SU(2) projector needs SU(2) tensors");
+  BST_REQUIRE(ncut >= 1 && ncut < Rt->rank && ncut < Rb->rank, BST_E_ARG, "bad ncut");
+  BST_REQUIRE(chi_total >= 1, BST_E_ARG, "chi must be positive");
+  std::vector<int> cut(ncut);
+  std::iota(cut.begin(), cut.end(), 0);
+  Layout* LN = su2_contract_layout(ctx, Rt, Rb, cut, cut);
+  const int nb = Rt->rank - ncut, nbp = Rb->rank - ncut;
+  for (int i = 0; i < nb; ++i)
+    BST_REQUIRE(LN->legs[i].flow == -1, BST_E_UNSUPPORTED, "SU(2) projector: Rt's right-cut legs must be outgoing");
+  for (int i = 0; i < nbp; ++i)
+    BST_REQUIRE(LN->legs[nb + i].flow == 1, BST_E_UNSUPPORTED,
+                "SU(2) projector: Rb's right-cut legs must be incoming");
+  double* Nd = (double*)ctx->buf("su2p.N", sizeof(double) * std::max<int64_t>(LN->nnz, 1), s);
+  su2_contract(ctx, Rt, rt, Rb, rb, cut, cut, prec, 1.0, 0.0, LN, Nd, s);
+
+  // matrix view of N per J; labels = [beta' intermediates, J, beta intermediates]
+  const int nin_inter = std::max(nbp - 2, 0);
+  std::map<int, std::map<std::vector<int32_t>, int64_t>> rows, cols;  // J -> config -> extent
+  auto cfg_of = [&](int64_t b, bool row) {
+    std::vector<int32_t> k;
+    const int32_t* sc = &LN->sect[b * LN->rank];
+    const int32_t* lb = &LN->tree[b * LN->ntree];
+    if (row) {
+      for (int i = 0; i < nb; ++i) k.push_back(sc[i]);
+      for (int i = nin_inter + 1; i < LN->ntree; ++i) k.push_back(lb[i]);
+    } else {
+      for (int i = 0; i < nbp; ++i) k.push_back(sc[nb + i]);
+      for (int i = 0; i < nin_inter; ++i) k.push_back(lb[i]);
+    }
+    return k;
+  };
+  auto extent = [&](int64_t b, int first, int n) {
+    int64_t e = 1;
+    for (int i = first; i < first + n; ++i) e *= LN->shape[b * LN->rank + i];
+    return e;
+  };
+  for (int64_t b = 0; b < LN->nblocks; ++b) {
+    const int J = LN->tree[b * LN->ntree + nin_inter];
+    rows[J][cfg_of(b, true)] = extent(b, 0, nb);
+    cols[J][cfg_of(b, false)] = extent(b, nb, nbp);
+  }
+  std::vector<MatSector> msec;
+  std::map<int, std::map<std::vector<int32_t>, int64_t>> roff, coff;
+  int64_t ntot = 0;
+  for (auto& kv : rows) {
+    MatSector m;
+    m.key = kv.first;
+    for (auto& r : kv.second) roff[kv.first][r.first] = m.rows, m.rows += r.second;
+    for (auto& c : cols[kv.first]) coff[kv.first][c.first] = m.cols, m.cols += c.second;
+    m.off = ntot;
+    ntot += m.rows * m.cols;
+    msec.push_back(std::move(m));
+  }
+  std::map<int, int> sec_of_J;
+  for (size_t i = 0; i < msec.size(); ++i) sec_of_J[int(msec[i].key)] = int(i);
+  const std::string rkey = "su2p/view/" + std::to_string(LN->id);
+  DevRelayout* rel = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->rplans.find(rkey);
+    if (it != ctx->rplans.end()) rel = it->second.get();
+  }
+  if (!rel) {
+    std::vector<RelTask> tasks;
+    for (int64_t b = 0; b < LN->nblocks; ++b) {
+      const int J = LN->tree[b * LN->ntree + nin_inter];
+      const MatSector& m = msec[sec_of_J[J]];
+      RelTask t{};
+      t.blk_off = LN->offset[b];
+      t.mat_base = m.off + roff[J][cfg_of(b, true)] * m.cols + coff[J][cfg_of(b, false)];
+      t.rank = LN->rank;
+      int64_t n = 1;
+      for (int i = 0; i < LN->rank; ++i) {
+        t.shape[i] = int32_t(LN->shape[b * LN->rank + i]);
+        n *= t.shape[i];
+      }
+      t.n = int32_t(n);
+      int64_t st = m.cols;
+      for (int i = nb - 1; i >= 0; --i) t.mstride[i] = st, st *= t.shape[i];
+      st = 1;
+      for (int i = nb + nbp - 1; i >= nb; --i) t.mstride[i] = st, st *= t.shape[i];
+      if (n > 0) tasks.push_back(t);
+    }
+    auto r = std::make_unique<DevRelayout>();
+    r->upload(tasks);
+    rel = r.get();
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->rplans[rkey] = std::move(r);
+  }
+  double* Nm = (double*)ctx->buf("su2p.Nm", sizeof(double) * std::max<int64_t>(ntot, 1), s);
+  launch_relayout(ctx, *rel, Nd, Nm, 0, 1.0, 0.0, s);
+  double* dss = (double*)ctx->buf("proj.nss", sizeof(double), s);
+  launch_sumsq(ctx, Nm, ntot, dss, s);
+  launch_scale(ctx, Nm, ntot, dss, s);
+
+  std::vector<PSec> secs;
+  for (auto& m : msec) {
+    if (m.rows == 0 || m.cols == 0) continue;
+    PSec x{};
+    x.cs = &m;
+    x.M = int(m.rows);
+    x.N = int(m.cols);
+    secs.push_back(x);
+  }
+  BST_REQUIRE(!secs.empty(), BST_E_NUMERIC, "projector: no non-empty sector");
+  double* dV = nullptr;
+  std::vector<double> hSig;
+  double nscale = 0, smax = 0, kmin = 0;
+  std::vector<int> kcount;
+  int64_t kept_dim = 0, kept = 0;
+  bool use_subspace = ctx->proj_method == 1;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    bool done = false;
+    if (use_subspace) {
+      ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
+      done = factors_subspace(ctx, Nm, secs, chi_total, prec, ctx->proj_iters, dV, hSig, s);
+    }
+    if (!done) factors_gesvd(ctx, Nm, ntot, secs, dV, hSig, s);
+    if (attempt == 0) {
+      double nss = 0;
+      BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
+      nscale = std::sqrt(nss);
+      BST_REQUIRE(std::isfinite(nscale) && nscale > 0, BST_E_NUMERIC, "projector: N is zero or not finite");
+    }
+    // candidates in descending order per sector (host sort; vectors follow)
+    std::vector<int> perm_all;
+    bool any = false;
+    for (auto& x : secs) {
+      std::vector<int> ord(x.c);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hSig[x.s_off + a] > hSig[x.s_off + b]; });
+      std::vector<double> tmp(x.c);
+      for (int j = 0; j < x.c; ++j) tmp[j] = hSig[x.s_off + ord[j]], any |= ord[j] != j;
+      for (int j = 0; j < x.c; ++j) hSig[x.s_off + j] = tmp[j];
+      perm_all.insert(perm_all.end(), ord.begin(), ord.end());
+    }
+    if (any) {
+      int64_t vtot = 0, po = 0;
+      for (auto& x : secs) vtot = std::max(vtot, x.v_off + int64_t(x.N) * x.c);
+      double* tmpv = (double*)ctx->buf("proj.Vperm", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+      int* dperm = upload_cached(ctx, "proj.perm", perm_all, s);
+      for (auto& x : secs) {
+        permute_cols<<<x.N, 128, 0, s>>>(dV + x.v_off, tmpv + x.v_off, x.c, dperm + po);
+        po += x.c;
+      }
+      BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
+      count_launch(ctx, int(secs.size()));
+    }
+    struct Cand { double sv; int tJ; int sec; int j; };
+    std::vector<Cand> cand;
+    smax = 0;
+    for (size_t i = 0; i < secs.size(); ++i)
+      for (int j = 0; j < secs[i].c; ++j) {
+        const double v = hSig[secs[i].s_off + j];
+        BST_REQUIRE(std::isfinite(v), BST_E_NUMERIC, "projector: non-finite singular value");
+        cand.push_back({v, int(secs[i].cs->key), int(i), j});
+        smax = std::max(smax, v);
+      }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+      if (a.sv != b.sv) return a.sv > b.sv;
+      if (a.tJ != b.tJ) return a.tJ < b.tJ;
+      return a.j < b.j;
+    });
+    kcount.assign(secs.size(), 0);
+    kept_dim = kept = 0;
+    kmin = smax;
+    for (auto& c : cand) {
+      if (!(c.sv > rel_cutoff * smax) || c.sv <= 0) break;
+      if (c.j != kcount[c.sec]) continue;  // an earlier multiplet of this sector was skipped
+      if (kept_dim + c.tJ + 1 > chi_total) continue;
+      kcount[c.sec]++;
+      kept++;
+      kept_dim += c.tJ + 1;
+      kmin = std::min(kmin, c.sv);
+    }
+    BST_REQUIRE(kept > 0, BST_E_NUMERIC, "projector: nothing kept");
+    bool edge = false;
+    if (done)
+      for (size_t i = 0; i < secs.size(); ++i) edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c);
+    if (!edge) break;
+    use_subspace = false;
+  }
+
+  // new leg (incoming on P): sectors J with kept multiplets
+  Leg nl;
+  nl.flow = 1;
+  ProjResult res;
+  std::map<int, int> kJ;  // J -> sector index in secs
+  for (size_t i = 0; i < secs.size(); ++i)
+    if (kcount[i] > 0) kJ[int(secs[i].cs->key)] = int(i);
+  for (auto& kv : kJ) {
+    nl.q.push_back(kv.first);
+    nl.d.push_back(kcount[kv.second]);
+    for (int j = 0; j < kcount[kv.second]; ++j) res.svals.push_back(hSig[secs[kv.second].s_off + j] * nscale);
+  }
+  nl.finish();
+  res.newleg = nl;
+  res.kept = kept_dim;
+  res.smin_over_smax = kmin / smax;
+
+  // gauge-fixed, scaled vectors per sector: Us [M x k], Vs [N x k]
+  int64_t us_tot = 0, vs_tot = 0, sk_tot = 0;
+  std::vector<int64_t> sk_off(secs.size()), ur_off(secs.size()), vs_off(secs.size());
+  for (size_t i = 0; i < secs.size(); ++i) {
+    sk_off[i] = sk_tot;
+    sk_tot += kcount[i];
+    ur_off[i] = us_tot;
+    us_tot += int64_t(secs[i].M) * kcount[i];
+    vs_off[i] = vs_tot;
+    vs_tot += int64_t(secs[i].N) * kcount[i];
+  }
+  std::vector<double> hsk(std::max<int64_t>(sk_tot, 1));
+  for (size_t i = 0; i < secs.size(); ++i)
+    for (int j = 0; j < kcount[i]; ++j) hsk[sk_off[i] + j] = hSig[secs[i].s_off + j];
+  double* dSk = upload_cached(ctx, "proj.sk", hsk, s);
+  double* Ur = (double*)ctx->buf("proj.Ur", sizeof(double) * std::max<int64_t>(us_tot, 1), s);
+  double* Us = (double*)ctx->buf("proj.Us", sizeof(double) * std::max<int64_t>(us_tot, 1), s);
+  double* Vs = (double*)ctx->buf("proj.Vs", sizeof(double) * std::max<int64_t>(vs_tot, 1), s);
+  std::vector<GemmProb> gu;
+  for (size_t i = 0; i < secs.size(); ++i) {
+    const int k = kcount[i];
+    if (k == 0) continue;
+    const PSec& x = secs[i];
+    gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
+  }
+  gemm_any(ctx, "proj.u", BST_FP64, gu, Nm, dV, Ur, s);
+  for (size_t i = 0; i < secs.size(); ++i) {
+    const PSec& x = secs[i];
+    const int k = kcount[i];
+    if (k == 0) continue;
+    gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i], k,
+                                         Us + ur_off[i], Vs + vs_off[i], 1, nscale);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
+
+  // V[beta'^dual..., new] and Ut[new^dual, beta^dual...]
+  std::vector<Leg> vl, ul{nl.dual()};
+  for (int i = 0; i < nbp; ++i) vl.push_back(LN->legs[nb + i].dual());
+  vl.push_back(nl);
+  for (int i = 0; i < nb; ++i) ul.push_back(LN->legs[i].dual());
+  Layout* LV = make_layout(ctx, BST_SU2, vl);
+  Layout* LU = make_layout(ctx, BST_SU2, ul);
+  std::vector<RelTask> tv, tu;
+  // V: labels [J, beta' out-tree intermediates]; block [beta' extents..., k]
+  for (int64_t b = 0; b < LV->nblocks; ++b) {
+    const int32_t* sc = &LV->sect[b * LV->rank];
+    const int32_t* lb = &LV->tree[b * LV->ntree];
+    const int J = nl.q[sc[nbp]];
+    const int si = kJ.at(J);
+    std::vector<int32_t> key(sc, sc + nbp);
+    key.insert(key.end(), lb + 1, lb + LV->ntree);
+    auto it = coff[J].find(key);
+    BST_REQUIRE(it != coff[J].end(), BST_E_SHAPE, "SU(2) projector: V block without a column of N");
+    const int k = kcount[si];
+    RelTask t{};
+    t.blk_off = LV->offset[b];
+    t.mat_base = vs_off[si] + it->second * k;
+    t.rank = LV->rank;
+    int64_t n = 1;
+    for (int i = 0; i < LV->rank; ++i) t.shape[i] = int32_t(LV->shape[b * LV->rank + i]), n *= t.shape[i];
+    t.n = int32_t(n);
+    t.mstride[nbp] = 1;
+    int64_t st = k;
+    for (int i = nbp - 1; i >= 0; --i) t.mstride[i] = st, st *= t.shape[i];
+    tv.push_back(t);
+  }
+  // Ut: labels [beta in-tree intermediates, J]; block [k, beta extents...]
+  for (int64_t b = 0; b < LU->nblocks; ++b) {
+    const int32_t* sc = &LU->sect[b * LU->rank];
+    const int32_t* lb = &LU->tree[b * LU->ntree];
+    const int J = nl.q[sc[0]];
+    const int si = kJ.at(J);
+    std::vector<int32_t> key(sc + 1, sc + 1 + nb);
+    key.insert(key.end(), lb, lb + LU->ntree - 1);
+    auto it = roff[J].find(key);
+    BST_REQUIRE(it != roff[J].end(), BST_E_SHAPE, "SU(2) projector: Ut block without a row of N");
+    const int k = kcount[si];
+    RelTask t{};
+    t.blk_off = LU->offset[b];
+    t.mat_base = ur_off[si] + it->second * k;
+    t.rank = LU->rank;
+    int64_t n = 1;
+    for (int i = 0; i < LU->rank; ++i) t.shape[i] = int32_t(LU->shape[b * LU->rank + i]), n *= t.shape[i];
+    t.n = int32_t(n);
+    t.mstride[0] = 1;
+    int64_t st = k;
+    for (int i = nb; i >= 1; --i) t.mstride[i] = st, st *= t.shape[i];
+    tu.push_back(t);
+  }
+  double* vd = (double*)ctx->buf("su2p.V", sizeof(double) * std::max<int64_t>(LV->nnz, 1), s);
+  double* ud = (double*)ctx->buf("su2p.Ut", sizeof(double) * std::max<int64_t>(LU->nnz, 1), s);
+  {
+    auto& slotv = ctx->rplans["su2p/V/" + std::to_string(LV->id) + "/" + std::to_string(LN->id)];
+    if (!slotv) {
+      slotv = std::make_unique<DevRelayout>();
+      slotv->upload(tv);
+    }
+    auto& slotu = ctx->rplans["su2p/U/" + std::to_string(LU->id) + "/" + std::to_string(LN->id)];
+    if (!slotu) {
+      slotu = std::make_unique<DevRelayout>();
+      slotu->upload(tu);
+    }
+    launch_relayout(ctx, *slotv, vd, Vs, 1, 1.0, 0.0, s);
+    launch_relayout(ctx, *slotu, ud, Us, 1, 1.0, 0.0, s);
+  }
+  std::vector<int> lbp(nbp), lvb(nbp), lub(nb), lrt(nb);
+  for (int i = 0; i < nbp; ++i) lbp[i] = ncut + i, lvb[i] = i;
+  for (int i = 0; i < nb; ++i) lub[i] = 1 + i, lrt[i] = ncut + i;
+  res.P = su2_contract_layout(ctx, Rb, LV, lbp, lvb);
+  res.Pt = su2_contract_layout(ctx, LU, Rt, lub, lrt);
+  retain(res.P);
+  retain(res.Pt);
+  double* pd = (double*)ctx->buf("su2p.P", sizeof(double) * std::max<int64_t>(res.P->nnz, 1), s);
+  double* ptd = (double*)ctx->buf("su2p.Pt", sizeof(double) * std::max<int64_t>(res.Pt->nnz, 1), s);
+  su2_contract(ctx, Rb, rb, LV, vd, lbp, lvb, prec, 1.0, 0.0, res.P, pd, s);
+  su2_contract(ctx, LU, ud, Rt, rt, lub, lrt, prec, 1.0, 0.0, res.Pt, ptd, s);
+  release(LV);
+  release(LU);
+  *p_out = pd;
+  *pt_out = ptd;
+  return res;
+}
+
 __global__ void transpose_kernel(const double* A, double* Y, int M, int N) {
   // Y[i + j*M] = A[i*N + j]
   __shared__ double t[32][33];

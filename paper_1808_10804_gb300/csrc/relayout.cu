@@ -184,6 +184,32 @@ __global__ void sumsq_final(const double* part, int np, double* out) {
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Weighted sum of squares sum_i w_i x_i^2 (per-CTA partials, then one CTA in
+// a fixed order): the Frobenius norm of an SU(2) tensor from its reduced
+// blocks, w = 2J+1 of the element's block.
+__global__ void sumsq_w_partial(const double* x, const double* w, long long n, double* part) {
+  __shared__ double sh[256];
+  double acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += w[i] * x[i] * x[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+void launch_sumsq_w(Ctx* ctx, const double* x, const double* w, int64_t n, double* dev_out, cudaStream_t s) {
+  int grid = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 304)));
+  double* part = (double*)ctx->buf("sumsq.part", sizeof(double) * 304, s);
+  sumsq_w_partial<<<grid, 256, 0, s>>>(x, w, n, part);
+  sumsq_final<<<1, 256, 0, s>>>(part, grid, dev_out);
+  BST_CUDA(cudaGetLastError());
+  count_launch(ctx, 2);
+}
+
 void launch_sumsq(Ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStream_t s) {
   int grid = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 304)));
   double* part = (double*)ctx->buf("sumsq.part", sizeof(double) * 304, s);

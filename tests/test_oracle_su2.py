@@ -223,3 +223,56 @@ def test_cfg3_leg_dimensions():
     assert (k.spins, k.degs) == tuple(cfg["k"])
     x = su2.Leg(1, *cfg["x"])
     assert (x.dim, x.rdim) == (150, 50)
+
+
+# ---------------------------------------------------------------------------
+# the SU(2) LEFT move of the oracle
+
+@pytest.fixture(scope="module")
+def su2_move():
+    from oracle import ctm_su2
+    from workloads import su2_config
+    net = ctm_su2.su2_network(su2_config("medium"), seed=1)
+    out, info = ctm_su2.left_move(net, 24, return_info=True)
+    return net, out, info
+
+
+def test_su2_move_spectrum_is_the_dense_spectrum(su2_move):
+    """The reduced sector matrices carry the dense N's singular values, each
+    2J+1 times (a wrong sector assembly or basis would change them)."""
+    net, out, info = su2_move
+    N = info["N"]
+    dims = N.shape
+    dense = np.linalg.svd(N.reshape(dims[0] * dims[1], dims[2] * dims[3]), compute_uv=False)
+    red = []
+    for J, (U, S, Vt) in info["sectors"].items():
+        red.extend(list(S) * (J + 1))
+    red = np.sort(np.array(red))[::-1]
+    dense = np.sort(dense)[::-1][:len(red)]
+    assert np.abs(dense - red).max() < 1e-10 * dense[0]
+    # the rest of the dense spectrum is zero (N is fully covered by its sectors)
+    assert len(red) <= dims[0] * dims[1]
+
+
+def test_su2_move_projectors_and_truncation(su2_move):
+    net, out, info = su2_move
+    new = info["new"]
+    assert info["dim"] == new.dim <= 24
+    # P~ P = 1 on the new leg (full dimension)
+    PtP = np.einsum("nab,abm->nm", info["Pt"], info["P"])
+    assert np.abs(PtP - np.eye(new.dim)).max() < 1e-10
+    # whole multiplets only: no discarded value above a kept one of the same J
+    for J, (U, S, Vt) in info["sectors"].items():
+        k = info["kept"][J]
+        assert all(S[j] >= S[k] for j in range(k)) if k < len(S) else True
+
+
+def test_su2_move_outputs_are_invariant(su2_move):
+    net, out, info = su2_move
+    rng = np.random.default_rng(3)
+    for r in ("C1", "T4", "C4"):
+        legs, dense = out[r]
+        assert abs(np.linalg.norm(dense) - 1.0) < 1e-12
+        assert np.abs(su2.to_dense(legs, su2.from_dense(legs, dense)) - dense).max() < 1e-12
+        R = su2.rotate(legs, dense, rng.standard_normal(3))
+        assert np.abs(R - dense).max() < 1e-11

@@ -162,6 +162,12 @@ def su2_config(name):
                 "phys": ((1,), (1,)),
                 "k": ((0, 1, 2, 3, 4), (11, 12, 12, 6, 1)),
                 "x": ((0, 1, 2, 3, 4, 5, 6), (11, 12, 10, 7, 5, 3, 2))}
+    if name == "medium":
+        return {"name": name,
+                "virtual": ((0, 1, 2), (1, 1, 1)),
+                "phys": ((1,), (1,)),
+                "k": ((0, 1, 2, 3, 4), (3, 4, 4, 2, 1)),
+                "x": ((0, 1, 2, 3), (4, 4, 3, 2))}
     if name == "small":
         return {"name": name,
                 "virtual": ((0, 1), (1, 1)),
