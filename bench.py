@@ -241,6 +241,74 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     return out
 
 
+def su2_move_bench(bst, dev, local, prec, steps, warmup, flush, pk):
+    """SU(2) LEFT move of the D=10 (d=5), X=150 (chi=50) workload on seeded
+    reduced blocks (env and site a[k,k,k^dual,k^dual]).  One step = the
+    environment restored and one LEFT move."""
+    import numpy as np
+    import torch
+    from workloads import su2_config, values
+    cfg = su2_config("D10chi150")
+    ctx = bst.Context(local)
+    try:
+        K, X = bst.Leg(1, *cfg["k"]), bst.Leg(1, *cfg["x"])
+        Xf = lambda f: bst.Leg(f, X.charges, X.degs)
+        legs = {"C1": [Xf(-1), Xf(-1)], "C2": [Xf(1), Xf(-1)], "C3": [Xf(1), Xf(1)], "C4": [Xf(1), Xf(-1)],
+                "T1": [Xf(1), K.dual(), Xf(-1)], "T2": [Xf(1), K, Xf(-1)], "T3": [Xf(1), K, Xf(-1)],
+                "T4": [Xf(1), K.dual(), Xf(-1)], "a": [K, K, K.dual(), K.dual()]}
+        L = {r: ctx.layout(lg, group="su2") for r, lg in legs.items()}
+        d = {r: torch.tensor(values(0, "A" if r == "a" else r, L[r].nnz), dtype=torch.float64, device=dev)
+             for r in L}
+        roles = bst.ROLES
+        caps = {r: max(L[r].nnz, 50 * 150 * (42 if r.startswith("T") else 1) * 2) for r in roles}
+        env = bst.Env(ctx, {r: L[r] for r in roles}, {r: d[r] for r in roles}, caps)
+        pristine = {r: env.data(r).clone() for r in roles}
+        L0 = dict(env.L)
+        stream = torch.cuda.current_stream()
+
+        def run(p):
+            for r in roles:
+                env.buf[r][:pristine[r].numel()].copy_(pristine[r])
+            env.L = dict(L0)
+            return ctx.ctm_move(env, L["a"], d["a"], bst.LEFT, 150, prec=p)
+
+        run("fp64")
+        ref = {r: env.data(r).cpu().numpy() for r in ("C1", "T4", "C4")}
+        st = run(prec)
+        torch.cuda.synchronize()
+        err = max(float(np.linalg.norm(env.data(r).cpu().numpy() - ref[r]) / np.linalg.norm(ref[r])) for r in ref)
+
+        def timed(p, n):
+            for _ in range(warmup):
+                run(p)
+            ev = []
+            for i in range(n):
+                flush.fill_(float(i))
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                run(p)
+                b_.record(stream)
+                ev.append((a_, b_))
+            torch.cuda.synchronize()
+            return statistics.median(x.elapsed_time(y) for x, y in ev)
+
+        ms = timed(prec, steps)
+        ms64 = timed("fp64", max(3, steps // 2))
+        ctx.profile(True)
+        run(prec)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        flops = sum(v[2] for k, v in prof.items() if k.startswith("gemm"))
+        return {"workload": "su2_D10_X150_left_move", "value": 1e3 / ms, "unit": "moves/s", "ms_per_step": ms,
+                "fp64_path_ms_per_step": ms64, "rel_err_vs_fp64_path": err, "kept_total_dim": st["kept"][0],
+                "algorithmic_gflop": flops / 1e9, "block_sparse_tflops": flops / (ms / 1e3) / 1e12,
+                "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()}}
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
+
+
 def su2_corner_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     """SU(2) enlarged corner of the D=10 (d=5), X=150 (chi=50) workload:
     X1 = C1.T1, X2 = X1.T4, Q1 = X2.a on seeded reduced blocks.  One step =
@@ -524,10 +592,11 @@ def run_ours(args):
         fp64_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev2)
 
     pk = peaks()
-    batched = su2 = large = None
+    batched = su2 = su2m = large = None
     if not args.no_batch:
         batched = batch_bench(bst, ctx, dev, prec, args.steps, args.warmup, flush, pk)
         su2 = su2_corner_bench(bst, ctx, dev, prec, args.steps, args.warmup, flush, pk)
+        su2m = su2_move_bench(bst, dev, local, prec, args.steps, args.warmup, flush, pk)
         large = single_layer_bench(bst, dev, local, prec, args.steps, args.warmup, flush, pk)
 
     if rank != 0:
@@ -590,6 +659,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "batched": batched,
         "su2_corner": su2,
+        "su2_left_move": su2m,
         "single_layer_large": large,
     }
     print(json.dumps(line), flush=True)
