@@ -153,6 +153,9 @@ struct DevGemm {
   int32_t* tile_idx = nullptr;    // tile -> linear tile index inside its problem
   int ntiles = 0, nprobs = 0;
   double flops = 0;  // algorithmic 2*M*N*K summed over the problems
+  int64_t* w_off = nullptr;  // per problem: offset of its M x N slice in a split-K workspace
+  int64_t wtot = 0;          // sum of M*N
+  int maxK = 0;
   // order 0: problem order; 1: tiles of the longest-K problems first
   void upload(const std::vector<GemmProb>& p, int tm, int tn, int order = 0);
   void free_all();
@@ -247,6 +250,10 @@ void launch_relayout(Ctx* ctx, const DevRelayout& r, const double* blk, double* 
 DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmProb>& probs);
 void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* B, double* C,
                      cudaStream_t s);
+// the same product with K split into ksplit slices reduced in a fixed order
+// (more CTAs for small, deep products)
+void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double* A, const double* B, double* C,
+                            cudaStream_t s);
 extern const int kF64TileM, kF64TileN;
 
 // gemm_ozaki.cu

@@ -28,6 +28,14 @@ void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn, int order) 
     }
   }
   ntiles = int(tp.size());
+  std::vector<int64_t> wo(std::max(nprobs, 1), 0);
+  wtot = 0;
+  maxK = 0;
+  for (int i = 0; i < nprobs; ++i) {
+    wo[i] = wtot;
+    wtot += int64_t(p[i].M) * p[i].N;
+    maxK = std::max(maxK, p[i].K);
+  }
   if (order == 1) {
     std::vector<int> idx(ntiles);
     for (int i = 0; i < ntiles; ++i) idx[i] = i;
@@ -44,6 +52,10 @@ void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn, int order) 
     BST_CUDA(cudaMalloc(&probs, sizeof(GemmProb) * nprobs));
     BST_CUDA(cudaMemcpy(probs, p.data(), sizeof(GemmProb) * nprobs, cudaMemcpyHostToDevice));
   }
+  if (nprobs) {
+    BST_CUDA(cudaMalloc(&w_off, sizeof(int64_t) * nprobs));
+    BST_CUDA(cudaMemcpy(w_off, wo.data(), sizeof(int64_t) * nprobs, cudaMemcpyHostToDevice));
+  }
   if (ntiles) {
     BST_CUDA(cudaMalloc(&tile_prob, sizeof(int32_t) * ntiles));
     BST_CUDA(cudaMalloc(&tile_idx, sizeof(int32_t) * ntiles));
@@ -56,6 +68,8 @@ void DevGemm::free_all() {
   if (probs) cudaFree(probs);
   if (tile_prob) cudaFree(tile_prob);
   if (tile_idx) cudaFree(tile_idx);
+  if (w_off) cudaFree(w_off);
+  w_off = nullptr;
   probs = nullptr;
   tile_prob = tile_idx = nullptr;
   ntiles = nprobs = 0;
@@ -67,19 +81,13 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                : "d"(a), "d"(b));
 }
 
-// 128 threads = 4 warps in a 2x2 arrangement, each warp a 32x32 sub-tile
-// made of 4x4 DMMA tiles of 8x8.
-__global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restrict__ probs,
-                                                       const int32_t* __restrict__ tile_prob,
-                                                       const int32_t* __restrict__ tile_idx,
-                                                       const double* __restrict__ A,
-                                                       const double* __restrict__ B, double* __restrict__ C) {
-  __shared__ double sA[kBK][kF64TileM + kPad];
-  __shared__ double sB[kBK][kF64TileN + kPad];
-  const GemmProb p = probs[tile_prob[blockIdx.x]];
-  const int nt = (p.N + kF64TileN - 1) / kF64TileN;
-  const int m0 = (tile_idx[blockIdx.x] / nt) * kF64TileM;
-  const int n0 = (tile_idx[blockIdx.x] % nt) * kF64TileN;
+// One 64x64 output tile of problem p over the K range [kb, ke), written to
+// out[m * om + n * on].  128 threads = 4 warps in a 2x2 arrangement, each warp
+// a 32x32 sub-tile made of 4x4 DMMA tiles of 8x8.
+__device__ __forceinline__ void f64_tile(const GemmProb& p, int m0, int n0, int kb, int ke,
+                                         const double* __restrict__ A, const double* __restrict__ B,
+                                         double* __restrict__ out, long long om, long long on,
+                                         double (*sA)[kF64TileM + kPad], double (*sB)[kF64TileN + kPad]) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int g = lane >> 2, tg = lane & 3;
@@ -90,14 +98,14 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restric
     for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
   const double* Ap = A + p.a_off;
   const double* Bp = B + p.b_off;
-  for (int k0 = 0; k0 < p.K; k0 += kBK) {
+  for (int k0 = kb; k0 < ke; k0 += kBK) {
 #pragma unroll
     for (int e = tid; e < kF64TileM * kBK; e += 128) {
       const int m = e / kBK, k = e % kBK;
       const int gm = m0 + m, gk = k0 + k;
-      sA[k][m] = (gm < p.M && gk < p.K) ? Ap[(long long)gm * p.a_m + (long long)gk * p.a_k] : 0.0;
+      sA[k][m] = (gm < p.M && gk < ke) ? Ap[(long long)gm * p.a_m + (long long)gk * p.a_k] : 0.0;
       const int gn = n0 + m;
-      sB[k][m] = (gn < p.N && gk < p.K) ? Bp[(long long)gn * p.b_n + (long long)gk * p.b_k] : 0.0;
+      sB[k][m] = (gn < p.N && gk < ke) ? Bp[(long long)gn * p.b_n + (long long)gk * p.b_k] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -114,7 +122,6 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restric
     }
     __syncthreads();
   }
-  double* Cp = C + p.c_off;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -123,8 +130,58 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restric
       for (int h = 0; h < 2; ++h) {
         const int gm = m0 + wm + i * 8 + g;
         const int gn = n0 + wn + j * 8 + tg * 2 + h;
-        if (gm < p.M && gn < p.N) Cp[(long long)gm * p.c_m + (long long)gn * p.c_n] = acc[i][j][h];
+        if (gm < p.M && gn < p.N) out[(long long)gm * om + (long long)gn * on] = acc[i][j][h];
       }
+}
+
+__global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restrict__ probs,
+                                                       const int32_t* __restrict__ tile_prob,
+                                                       const int32_t* __restrict__ tile_idx,
+                                                       const double* __restrict__ A,
+                                                       const double* __restrict__ B, double* __restrict__ C) {
+  __shared__ double sA[kBK][kF64TileM + kPad];
+  __shared__ double sB[kBK][kF64TileN + kPad];
+  const GemmProb p = probs[tile_prob[blockIdx.x]];
+  const int nt = (p.N + kF64TileN - 1) / kF64TileN;
+  const int m0 = (tile_idx[blockIdx.x] / nt) * kF64TileM;
+  const int n0 = (tile_idx[blockIdx.x] % nt) * kF64TileN;
+  f64_tile(p, m0, n0, 0, p.K, A, B, C + p.c_off, p.c_m, p.c_n, sA, sB);
+}
+
+// Split-K: CTA (tile, s) computes the partial product over the s-th K slice
+// (slices of a multiple of 16) into W[s][problem][m][n]; the reduction adds
+// the slices in a fixed order (deterministic result).
+__global__ void __launch_bounds__(128) gemm_f64_splitk_kernel(const GemmProb* __restrict__ probs,
+                                                              const int32_t* __restrict__ tile_prob,
+                                                              const int32_t* __restrict__ tile_idx,
+                                                              const double* __restrict__ A,
+                                                              const double* __restrict__ B, double* __restrict__ W,
+                                                              const int64_t* __restrict__ w_off, long long wtot,
+                                                              int ksplit) {
+  __shared__ double sA[kBK][kF64TileM + kPad];
+  __shared__ double sB[kBK][kF64TileN + kPad];
+  const int pi = tile_prob[blockIdx.x];
+  const GemmProb p = probs[pi];
+  const int nt = (p.N + kF64TileN - 1) / kF64TileN;
+  const int m0 = (tile_idx[blockIdx.x] / nt) * kF64TileM;
+  const int n0 = (tile_idx[blockIdx.x] % nt) * kF64TileN;
+  const int kc = ((p.K + ksplit - 1) / ksplit + kBK - 1) / kBK * kBK;
+  const int kb = min(p.K, int(blockIdx.y) * kc), ke = min(p.K, kb + kc);
+  f64_tile(p, m0, n0, kb, ke, A, B, W + blockIdx.y * wtot + w_off[pi], p.N, 1, sA, sB);
+}
+
+__global__ void gemm_f64_reduce_kernel(const GemmProb* __restrict__ probs, const double* __restrict__ W,
+                                       const int64_t* __restrict__ w_off, long long wtot, int ksplit,
+                                       double* __restrict__ C) {
+  const GemmProb p = probs[blockIdx.y];
+  const long long n = (long long)p.M * p.N;
+  const double* w = W + w_off[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < ksplit; ++s) v += w[s * wtot + e];
+    const long long m = e / p.N, c = e - m * p.N;
+    C[p.c_off + m * p.c_m + c * p.c_n] = v;
+  }
 }
 
 DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmProb>& probs) {
@@ -136,6 +193,22 @@ DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmPr
   DevGemm* raw = g.get();
   ctx->gplans[key] = std::move(g);
   return raw;
+}
+
+void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double* A, const double* B, double* C,
+                            cudaStream_t s) {
+  if (g.ntiles == 0) return;
+  if (ksplit <= 1) {
+    launch_gemm_f64(ctx, g, A, B, C, s);
+    return;
+  }
+  double* W = (double*)ctx->buf("gemm_f64.splitk", sizeof(double) * std::max<int64_t>(1, g.wtot * ksplit), s);
+  ProfScope ps(ctx, s, "gemm_f64", g.flops, 0.0);
+  gemm_f64_splitk_kernel<<<dim3(unsigned(g.ntiles), unsigned(ksplit)), 128, 0, s>>>(
+      g.probs, g.tile_prob, g.tile_idx, A, B, W, g.w_off, g.wtot, ksplit);
+  gemm_f64_reduce_kernel<<<dim3(64, unsigned(g.nprobs)), 256, 0, s>>>(g.probs, W, g.w_off, g.wtot, ksplit, C);
+  BST_CUDA(cudaGetLastError());
+  count_launch(ctx, 2);
 }
 
 void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* B, double* C, cudaStream_t s) {

@@ -144,8 +144,15 @@ static std::string probs_key(const std::vector<GemmProb>& probs) {
 static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std::vector<GemmProb>& probs,
                      const double* A, const double* B, double* C, cudaStream_t s) {
   if (probs.empty()) return;
-  if (prec == BST_FP64)
-    launch_gemm_f64(ctx, *get_dev_gemm(ctx, tag + "/" + probs_key(probs), probs), A, B, C, s);
+  if (prec == BST_FP64) {
+    // the projector's FP64 products are small and deep (b x b x K): split K
+    // until about two CTAs per SM are busy
+    const DevGemm& g = *get_dev_gemm(ctx, tag + "/" + probs_key(probs), probs);
+    int ksplit = 1;
+    if (g.ntiles > 0 && g.ntiles < 304)
+      ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 64, 16}));
+    launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s);
+  }
   else
     run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s);
 }
