@@ -46,7 +46,7 @@ def build(verbose=False, force=False):
     """Compile every source and link libbst.so; returns its path."""
     os.makedirs(OBJ, exist_ok=True)
     srcs = sources()
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "bst.h"))
     if not force and os.path.exists(OUT):
         newest = max(os.path.getmtime(p) for p in srcs + hdrs)

@@ -16,6 +16,7 @@
 #include <cstring>
 
 #include "bst_internal.h"
+#include "relayout_dev.cuh"
 
 namespace bst {
 
@@ -78,37 +79,7 @@ __global__ void __launch_bounds__(kBatchThreads) relayout_batch_kernel(const Bat
                                                                        double beta, int chunk) {
   const int2 c = chunks[blockIdx.x];
   const BatchTask& bt = tasks[c.x];
-  const RelTask& t = bt.t;
-  double* blk = bases[bt.src];
-  const int r = t.rank;
-  int shape[kMaxRank];
-  long long ms[kMaxRank];
-#pragma unroll
-  for (int i = 0; i < kMaxRank; ++i) {
-    shape[i] = i < r ? t.shape[i] : 1;
-    ms[i] = i < r ? t.mstride[i] : 0;
-  }
-  const int end = min(t.n, c.y + chunk);
-  for (int e = c.y + threadIdx.x; e < end; e += kBatchThreads) {
-    int rem = e;
-    long long mo = t.mat_base;
-#pragma unroll
-    for (int i = kMaxRank - 1; i >= 0; --i) {
-      if (i < r) {
-        const int ii = rem % shape[i];
-        rem /= shape[i];
-        mo += ii * ms[i];
-      }
-    }
-    const long long bo = t.blk_off + e;
-    if (dir == 0) {
-      mat[mo] = blk[bo];
-    } else {
-      double v = alpha * mat[mo];
-      if (beta != 0.0) v += beta * blk[bo];
-      blk[bo] = v;
-    }
-  }
+  relayout_range<kBatchThreads>(bt.t, c.y, min(bt.t.n, c.y + chunk), bases[bt.src], mat, dir, alpha, beta);
 }
 
 // (Re)build the chunk table of a relayout for `chunk` elements per CTA.

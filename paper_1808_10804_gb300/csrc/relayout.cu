@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "bst_internal.h"
+#include "relayout_dev.cuh"
 
 namespace bst {
 
@@ -99,35 +100,7 @@ __global__ void __launch_bounds__(kRelThreads) relayout_kernel(const RelTask* __
                                                                double alpha, double beta) {
   const int2 c = chunks[blockIdx.x];
   const RelTask& t = tasks[c.x];
-  const int r = t.rank;
-  int shape[kMaxRank];
-  long long ms[kMaxRank];
-#pragma unroll
-  for (int i = 0; i < kMaxRank; ++i) {
-    shape[i] = i < r ? t.shape[i] : 1;
-    ms[i] = i < r ? t.mstride[i] : 0;
-  }
-  const int end = min(t.n, c.y + kChunk);
-  for (int e = c.y + threadIdx.x; e < end; e += kRelThreads) {
-    int rem = e;
-    long long mo = t.mat_base;
-#pragma unroll
-    for (int i = kMaxRank - 1; i >= 0; --i) {
-      if (i < r) {
-        int ii = rem % shape[i];
-        rem /= shape[i];
-        mo += ii * ms[i];
-      }
-    }
-    const long long bo = t.blk_off + e;
-    if (dir == 0) {
-      mat[mo] = blk[bo];
-    } else {
-      double v = alpha * mat[mo];
-      if (beta != 0.0) v += beta * blk[bo];
-      blk[bo] = v;
-    }
-  }
+  relayout_range<kRelThreads>(t, c.y, min(t.n, c.y + kChunk), blk, mat, dir, alpha, beta);
 }
 
 void launch_relayout(Ctx* ctx, const DevRelayout& r, const double* blk, double* mat, int dir, double alpha,
