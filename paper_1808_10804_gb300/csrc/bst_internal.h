@@ -264,8 +264,11 @@ void ozaki_free(OzakiPlan* oz);
 // generic Ozaki GEMM over a problem list (used by the projector)
 // `order` selects the tile schedule (0 problem order, 1 longest K first,
 // 2 column tiles outer); each schedule is its own cached plan
+// split_a = false reuses the A digits of this plan's previous call (the
+// caller guarantees that A has not changed since)
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs,
-                          const double* A, const double* B, double* C, cudaStream_t s, int order = 0);
+                          const double* A, const double* B, double* C, cudaStream_t s, int order = 0,
+                          bool split_a = true);
 
 // projector.cu
 struct ProjResult {

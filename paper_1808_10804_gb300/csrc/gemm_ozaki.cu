@@ -564,17 +564,18 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   return P;
 }
 
-static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s) {
+static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s,
+                     bool split_a = true) {
   if (P->ntiles == 0) return;
   {
     ProfScope ps(ctx, s, "split_bf16", 0.0, P->split_bytes);
-    const int wa = P->rowsA, wb = P->rowsB;
+    const int wa = split_a ? P->rowsA : 0, wb = P->rowsB;
     if (wa) oz::ozaki_split_kernel<<<(wa + 7) / 8, 256, 0, s>>>(P->d_sa, P->nsa, A, P->SA, P->eA, P->rowsA,
                                                                P->kpitch);
     if (wb) oz::ozaki_split_kernel<<<(wb + 7) / 8, 256, 0, s>>>(P->d_sb, P->nsb, B, P->SB, P->eB, P->rowsB,
                                                                P->kpitch);
     BST_CUDA(cudaGetLastError());
-    count_launch(ctx, 2);
+    count_launch(ctx, (wa ? 1 : 0) + (wb ? 1 : 0));
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
   oz::ozaki_gemm_kernel<<<P->ntiles, oz::kThreads, smem_bytes(), s>>>(P->mapA, P->mapB, P->d_probs, P->d_tiles,
@@ -594,7 +595,7 @@ void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double*
 void ozaki_free(OzakiPlan* oz) { delete oz; }
 
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
-                          const double* B, double* C, cudaStream_t s, int order) {
+                          const double* B, double* C, cudaStream_t s, int order, bool split_a) {
   // plans live in the context (freed with it), keyed by caller tag, problem
   // list and tile schedule
   const std::string key = tag + "/" + std::to_string(probs_hash(probs)) + "/" + std::to_string(order);
@@ -610,7 +611,7 @@ void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<Ge
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->ozplans[key] = std::move(np);
   }
-  run_plan(ctx, P, A, B, C, s);
+  run_plan(ctx, P, A, B, C, s, split_a);
 }
 
 }  // namespace bst

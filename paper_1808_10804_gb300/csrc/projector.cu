@@ -142,7 +142,7 @@ static std::string probs_key(const std::vector<GemmProb>& probs) {
 
 // FP64-accurate grouped GEMM in the requested arithmetic.
 static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std::vector<GemmProb>& probs,
-                     const double* A, const double* B, double* C, cudaStream_t s) {
+                     const double* A, const double* B, double* C, cudaStream_t s, bool same_a = false) {
   if (probs.empty()) return;
   if (prec == BST_FP64) {
     // the projector's FP64 products are small and deep (b x b x K): split K
@@ -154,7 +154,7 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
     launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s);
   }
   else
-    run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s);
+    run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s, 0, !same_a);
 }
 
 template <class T>
@@ -313,13 +313,17 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   };
   // CholQR with an FP32 factor after each half step: the blocks N Q and
   // N^T Z carry the condition number sigma_1/sigma_b once, not squared
+  // N is split into tensor-core digits once per projector call: its two
+  // plans ("ss.z": N, "ss.y": N^T) keep their A digits between steps
+  bool n_split = false;
   auto iterate = [&](int n) {
     for (int t = 0; t < n; ++t) {
-      gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s);
+      gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s, n_split);
       gemm_any(ctx, "ss.gz", prec, g_gz, Z, Z, Msm, s);
       cholinv();
       gemm_any(ctx, "ss.qz", prec, g_qz, Z, Rinv, Z2, s);
-      gemm_any(ctx, "ss.y", prec, g_y, Nm, Z2, Y, s);
+      gemm_any(ctx, "ss.y", prec, g_y, Nm, Z2, Y, s, n_split);
+      n_split = true;
       gemm_any(ctx, "ss.gy", prec, g_gy, Y, Y, Msm, s);
       cholinv();
       gemm_any(ctx, "ss.qy", prec, g_qy, Y, Rinv, Q, s);
