@@ -17,9 +17,9 @@
 // The epilogue forms the result with 64-bit integer arithmetic and one
 // conversion to FP64.  Relative error ~2^-40 against the row/column scales.
 //
-// Kernel: one 128 x 64 output tile per CTA; warp 0 drives TMA (64-byte
-// swizzled K-major tiles, 3-stage ring), warp 1 issues tcgen05.mma from one
-// thread, warps 2..9 drain tensor memory.  All waits are bounded: on expiry
+// Kernel: persistent, one CTA per SM walking the plan's 128 x 64 output
+// tiles; warp 0 drives TMA (64-byte swizzled K-major tiles, 3-stage ring),
+// warp 1 issues tcgen05.mma from one thread, warps 2..9 drain tensor memory.  All waits are bounded: on expiry
 // the kernel records BST_E_TIMEOUT in the context's error word, lets its
 // copies drain (bounded), frees tensor memory and returns.
 #include <cuda.h>
@@ -173,22 +173,27 @@ struct Smem {
   alignas(1024) uint8_t stage[kStages][kStageBytes];
   uint64_t full[kStages], empty[kStages];
   uint64_t acc_full[2], acc_empty[2];
+  uint64_t acc34_empty;  // the epilogue has read d3, d4 of the previous tile
   uint32_t tmem_base;
   int abort_flag;
-  int eb[kTN];
 };
 
+// Persistent: CTA b processes tiles b, b + gridDim.x, ... in the plan's tile
+// order.  Every tile has at least one K chunk (the plan writes K == 0
+// problems separately): the epilogue of a tile always waits for that tile's
+// products, so no role runs two mbarrier phases ahead of another.  The three roles walk the same sequence of K chunks, counted across
+// tiles (stage ring and mbarrier phases continue from tile to tile), and the
+// epilogue of one tile overlaps the copies and products of the next: d0..d2
+// are double-buffered per pair of chunks, d3 and d4 are released as soon as
+// the epilogue has folded them into its integer accumulators.
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                      const Prob* __restrict__ probs, const Tile* __restrict__ tiles,
+                      const Prob* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
                       const int* __restrict__ expA, const int* __restrict__ expB, int rowsA, int rowsB,
                       double* __restrict__ C, int* err) {
   extern __shared__ uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Tile t = tiles[blockIdx.x];
-  const Prob p = probs[t.prob];
-  const int nk = (p.K + kTK - 1) / kTK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.acc_full[b], 1);
       mbar_init(&sm.acc_empty[b], 256);
     }
+    mbar_init(&sm.acc34_empty, 256);
     sm.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -208,10 +214,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (threadIdx.x >= 64 && threadIdx.x < 64 + kTN) {
-    const int j = threadIdx.x - 64;
-    sm.eb[j] = (t.n0 + j < p.N) ? expB[p.brow + t.n0 + j] : 0;
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -220,25 +222,33 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
-    if (lane == 0 && nk > 0) {
-      int issued = 0;
-      for (int c = 0; c < nk; ++c) {
-        const int s = c % kStages;
-        if (c >= kStages && !mbar_wait(&sm.empty[s], ((c / kStages) - 1) & 1, abort_flag, err)) break;
-        mbar_expect_tx(&sm.full[s], kStageBytes);
-        uint8_t* base = sm.stage[s];
-        const int k0 = c * kTK;
-        for (int i = 0; i < kSlices; ++i)
-          tma_load_2d(base + i * kABytes, &mapA, k0, i * rowsA + p.arow + t.m0, &sm.full[s]);
-        for (int j = 0; j < kSlices; ++j)
-          tma_load_2d(base + kSlices * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
-        issued = c + 1;
+    if (lane == 0) {
+      long long g = 0;  // chunks issued so far (all tiles)
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+        const Tile t = tiles[ti];
+        const Prob p = probs[t.prob];
+        const int nk = (p.K + kTK - 1) / kTK;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = int(g % kStages);
+          if (g >= kStages && !mbar_wait(&sm.empty[s], int((g / kStages) - 1) & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sm.full[s], kStageBytes);
+          uint8_t* base = sm.stage[s];
+          const int k0 = c * kTK;
+          for (int i = 0; i < kSlices; ++i)
+            tma_load_2d(base + i * kABytes, &mapA, k0, i * rowsA + p.arow + t.m0, &sm.full[s]);
+          for (int j = 0; j < kSlices; ++j)
+            tma_load_2d(base + kSlices * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
+        }
       }
       if (*abort_flag) {
         // let the copies in flight land before the CTA exits (bounded)
-        for (int c = std::max(0, issued - kStages); c < issued; ++c) {
-          const int s = c % kStages;
-          for (long long i = 0; i < kSpinLimit && !mbar_try(&sm.full[s], (c / kStages) & 1); ++i) {
+        for (long long c = (g > kStages ? g - kStages : 0); c < g; ++c) {
+          const int s = int(c % kStages);
+          for (long long i = 0; i < kSpinLimit && !mbar_try(&sm.full[s], int(c / kStages) & 1); ++i) {
           }
         }
       }
@@ -248,36 +258,56 @@ __global__ void __launch_bounds__(kThreads, 1)
     // d0..d2 are drained every pair of K chunks (64 K): their FP32 sums stay
     // exact integers below 2^24 (at most 3 * 64 products of magnitude
     // <= 2^16 per diagonal entry)
-    if (lane == 0 && nk > 0) {
-      for (int c = 0; c < nk; ++c) {
-        const int s = c % kStages, pc = c >> 1, buf = pc & 1;
-        const bool first = (c & 1) == 0;
-        if (!mbar_wait(&sm.full[s], (c / kStages) & 1, abort_flag, err)) break;
-        if (first && pc >= 2 && !mbar_wait(&sm.acc_empty[buf], ((pc >> 1) - 1) & 1, abort_flag, err)) break;
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(sm.stage[s]);
-        const uint32_t b0 = a0 + kSlices * kABytes;
-        for (int ks = 0; ks < kTK / 16; ++ks) {
-          for (int d = 0; d <= 4; ++d) {
-            for (int i = 0; i <= d; ++i) {
-              const int j = d - i;
-              uint32_t col;
-              uint32_t acc;
-              if (d <= 2) {
-                col = kColD0 + d * 2 * kTN + buf * kTN;
-                acc = (!first || ks > 0 || i > 0) ? 1u : 0u;
-              } else {
-                col = kColD3 + (d - 3) * kTN;
-                acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
+    if (lane == 0) {
+      long long g = 0, pg = 0;  // chunks and chunk pairs consumed so far (all tiles)
+      int tn = 0;               // tiles of this CTA so far
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++tn) {
+        const Prob p = probs[tiles[ti].prob];
+        const int nk = (p.K + kTK - 1) / kTK;
+        for (int c = 0; c < nk; ++c, ++g) {
+          const int s = int(g % kStages);
+          const long long pc = pg + (c >> 1);
+          const int buf = int(pc & 1);
+          const bool first = (c & 1) == 0;
+          if (!mbar_wait(&sm.full[s], int(g / kStages) & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          if (first && pc >= 2 && !mbar_wait(&sm.acc_empty[buf], int((pc >> 1) - 1) & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          if (c == 0 && tn > 0 && !mbar_wait(&sm.acc34_empty, (tn - 1) & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sm.stage[s]);
+          const uint32_t b0 = a0 + kSlices * kABytes;
+          for (int ks = 0; ks < kTK / 16; ++ks) {
+            for (int d = 0; d <= 4; ++d) {
+              for (int i = 0; i <= d; ++i) {
+                const int j = d - i;
+                uint32_t col;
+                uint32_t acc;
+                if (d <= 2) {
+                  col = kColD0 + d * 2 * kTN + buf * kTN;
+                  acc = (!first || ks > 0 || i > 0) ? 1u : 0u;
+                } else {
+                  col = kColD3 + (d - 3) * kTN;
+                  acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
+                }
+                const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
+                const uint64_t bd = smem_desc(b0 + j * kBBytes + ks * 32);
+                mma_bf16(tmem + col, ad, bd, acc);
               }
-              const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
-              const uint64_t bd = smem_desc(b0 + j * kBBytes + ks * 32);
-              mma_bf16(tmem + col, ad, bd, acc);
             }
           }
+          mma_commit(&sm.empty[s]);
+          if (!first || c == nk - 1) mma_commit(&sm.acc_full[buf]);
         }
-        mma_commit(&sm.empty[s]);
-        if (!first || c == nk - 1) mma_commit(&sm.acc_full[buf]);
+        pg += (nk + 1) >> 1;
       }
     }
   } else {
@@ -289,39 +319,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = ((warp - 2) >> 2) * kHalf;
     const int row = q * 32 + lane;
     const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
-    // T = sum over chunks of (S0 2^18 + S1 2^9 + S2): exact in 64 bits
-    long long T[kHalf];
-#pragma unroll
-    for (int j = 0; j < kHalf; ++j) T[j] = 0;
+    long long pg = 0;
     bool ok = true;
-    const int npair = (nk + 1) >> 1;
-    for (int p = 0; p < npair && ok; ++p) {
-      const int buf = p & 1;
-      ok = mbar_wait(&sm.acc_full[buf], (p >> 1) & 1, abort_flag, err);
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      const Tile t = tiles[ti];
+      const Prob p = probs[t.prob];
+      const int nk = (p.K + kTK - 1) / kTK;
+      // T = sum over chunk pairs of (S0 2^18 + S1 2^9 + S2): exact in 64 bits
+      long long T[kHalf];
+#pragma unroll
+      for (int j = 0; j < kHalf; ++j) T[j] = 0;
+      const int npair = (nk + 1) >> 1;
+      for (int pp = 0; pp < npair; ++pp) {
+        const long long pc = pg + pp;
+        const int buf = int(pc & 1);
+        ok = mbar_wait(&sm.acc_full[buf], int(pc >> 1) & 1, abort_flag, err);
+        if (!ok) break;
+        tc_fence_after();
+        uint32_t v[32];
+        // exact FP32 integers below 2^24: one round-to-nearest conversion each
+        tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
+        tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
+        tmem_ld32(lane_base + kColD2 + buf * kTN + c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));
+        tc_fence_before();
+        mbar_arrive(&sm.acc_empty[buf]);
+      }
       if (!ok) break;
-      tc_fence_after();
-      uint32_t v[32];
-      // exact FP32 integers below 2^24: one round-to-nearest conversion each
-      tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
-      tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
-      tmem_ld32(lane_base + kColD2 + buf * kTN + c0, v);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));
-      tc_fence_before();
-      mbar_arrive(&sm.acc_empty[buf]);
-    }
-    if (ok) {
-      const int gm = t.m0 + row;
-      const bool row_ok = gm < p.M;
-      const int ea = row_ok ? expA[p.arow + gm] : 0;
-      double* crow = C + p.c_off + (long long)gm * p.c_m;
+      pg += npair;
+      // X = S0 2^27 + S1 2^18 + S2 2^9 + (S3 + S4 2^-9), folded into T; then
+      // d3 and d4 are released to the next tile's products
 #pragma unroll
       for (int h = 0; h < kHalf / 16; ++h) {
         uint32_t w3[16], w4[16];
@@ -335,14 +370,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int jj = h * 16 + j;
-          const int gn = t.n0 + c0 + jj;
-          // X = S0 2^27 + S1 2^18 + S2 2^9 + (S3 + S4 2^-9);  C = X 2^(ea+eb-43)
           const float small = __uint_as_float(w3[j]) + __uint_as_float(w4[j]) * (1.0f / 512.0f);
-          const long long X = (T[jj] << 9) + __float2ll_rn(small);
-          const int e = ea + sm.eb[c0 + jj] - 43;
-          const double v = (double)X * pow2i(e >> 1) * pow2i(e - (e >> 1));
-          if (row_ok && gn < p.N) crow[(long long)gn * p.c_n] = v;
+          T[h * 16 + j] = (T[h * 16 + j] << 9) + __float2ll_rn(small);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&sm.acc34_empty);
+      // C = X 2^(ea+eb-43)
+      const int gm = t.m0 + row;
+      const bool row_ok = gm < p.M;
+      const int ea = row_ok ? expA[p.arow + gm] : 0;
+      double* crow = C + p.c_off + (long long)gm * p.c_m;
+#pragma unroll
+      for (int jj = 0; jj < kHalf; ++jj) {
+        const int gn = t.n0 + c0 + jj;
+        if (row_ok && gn < p.N) {
+          const int e = ea + expB[p.brow + gn] - 43;
+          crow[(long long)gn * p.c_n] = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
         }
       }
     }
@@ -467,8 +511,12 @@ struct OzakiPlan {
   CUtensorMap mapA, mapB;
   double flops = 0;
   double split_bytes = 0;  // FP64 read + 5 BF16 digits written per element, exponent per row
-  bool zero_only = false;  // every problem has K == 0
-  std::vector<GemmProb> zprobs;  // K == 0 problems, written as zeros
+  // K == 0 problems (no matched block pair): written as zeros by a separate
+  // launch, so every tile of the persistent GEMM has at least one K chunk
+  // (its epilogue then always waits for products of that tile, which keeps
+  // the CTA's mbarrier phases in step)
+  GemmProb* d_zprobs = nullptr;
+  int nzprobs = 0;
   ~OzakiPlan() {
     cudaFree(d_probs);
     cudaFree(d_tiles);
@@ -478,10 +526,29 @@ struct OzakiPlan {
     cudaFree(SB);
     cudaFree(eA);
     cudaFree(eB);
+    cudaFree(d_zprobs);
   }
 };
 
+// C = 0 on the problems with K == 0 (one CTA row per problem)
+__global__ void zero_probs_kernel(const GemmProb* __restrict__ zp, double* __restrict__ C) {
+  const GemmProb p = zp[blockIdx.y];
+  const long long n = (long long)p.M * p.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long m = e / p.N, c = e - m * p.N;
+    C[p.c_off + m * p.c_m + c * p.c_n] = 0.0;
+  }
+}
+
 static size_t smem_bytes() { return sizeof(oz::Smem) + 1024; }
+
+// streaming multiprocessors of the current device (one persistent CTA each)
+static int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  return n > 0 ? n : 152;
+}
 
 // Tile schedule of a plan (the order in which CTAs pick up output tiles):
 // 0 problem order, row tiles outer; 1 longest K first (the tiles that take
@@ -492,6 +559,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   std::vector<oz::Prob> hp;
   std::vector<oz::Tile> ht;
   std::vector<oz::SplitTask> sa, sb;
+  std::vector<GemmProb> zp;
   int maxk = 1;
   for (auto& g : probs) {
     BST_REQUIRE(g.K <= 10000, BST_E_UNSUPPORTED, "Ozaki GEMM: K above 10000");
@@ -514,7 +582,9 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
     P->rowsB += g.N;
     const int pi = int(hp.size());
     hp.push_back(q);
-    if (order == 2) {
+    if (g.K == 0) {
+      zp.push_back(g);
+    } else if (order == 2) {
       for (int n0 = 0; n0 < g.N; n0 += oz::kTN)
         for (int m0 = 0; m0 < g.M; m0 += oz::kTM) ht.push_back({pi, m0, n0, 0});
     } else {
@@ -541,6 +611,8 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   };
   up(&P->d_probs, hp);
   up(&P->d_tiles, ht);
+  up(&P->d_zprobs, zp);
+  P->nzprobs = int(zp.size());
   up(&P->d_sa, sa);
   up(&P->d_sb, sb);
   // split buffers: 5 slices x rows x kpitch BF16, with room for a full tile
@@ -566,6 +638,11 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
 
 static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s,
                      bool split_a = true) {
+  if (P->nzprobs) {
+    zero_probs_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_zprobs, C);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
   if (P->ntiles == 0) return;
   {
     ProfScope ps(ctx, s, "split_bf16", 0.0, P->split_bytes);
@@ -578,9 +655,9 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
     count_launch(ctx, (wa ? 1 : 0) + (wb ? 1 : 0));
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
-  oz::ozaki_gemm_kernel<<<P->ntiles, oz::kThreads, smem_bytes(), s>>>(P->mapA, P->mapB, P->d_probs, P->d_tiles,
-                                                                       P->eA, P->eB, P->rowsA, P->rowsB, C,
-                                                                       ctx->d_err);
+  const int grid = std::min(P->ntiles, num_sms());
+  oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(P->mapA, P->mapB, P->d_probs, P->d_tiles, P->ntiles,
+                                                                  P->eA, P->eB, P->rowsA, P->rowsB, C, ctx->d_err);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
 }

@@ -326,3 +326,24 @@ def test_repeated_move_same_result(bst, prec, tol):
         assert len(c.tuning_log().splitlines()) > n0
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("ozaki", 1e-11)])
+def test_contract_many_tiles_with_empty_sectors(bst, ctx, prec, tol):
+    """Output sectors with no matched block pair (K = 0) between sectors that
+    have one, with several output tiles per SM: the persistent tensor-core
+    GEMM walks many tiles per CTA and the K = 0 sectors come out exactly 0."""
+    r = u1.Leg(1, (-2, 0, 2), (1200, 1200, 1200))
+    k = u1.Leg(-1, (0,), (64,))
+    c = u1.Leg(-1, (-2, 0, 2), (1200, 1200, 1200))
+    rng = np.random.default_rng(11)
+    A = u1.to_dense([r, k], rng.standard_normal(u1.nnz([r, k])))
+    B = u1.to_dense([k.dual(), c], rng.standard_normal(u1.nnz([k.dual(), c])))
+    LA, a = upload(bst, ctx, [r, k], A)
+    LB, b = upload(bst, ctx, [k.dual(), c], B)
+    LC, cd = ctx.contract(LA, a, LB, b, (1,), (0,), prec=prec)
+    torch.cuda.synchronize()
+    ref = u1.from_dense([r, c], A @ B)
+    got = cd.cpu().numpy()
+    assert rel_err(got, ref) <= tol
+    assert np.all(got[ref == 0] == 0)
