@@ -345,7 +345,20 @@ typedef struct {
  * on the updated environment.  Every directional move computes the four
  * enlarged corners, the half systems, the projectors (as
  * bst_svd_projector with rel_cutoff) and renormalises and normalises the
- * renewed tensors (Frobenius norm 1).  stats may be NULL. */
+ * renewed tensors (Frobenius norm 1).  stats may be NULL.
+ *
+ * Site: either the double layer a[L,U,R,D] (rank 4), or a single-layer
+ * site A[P,L,U,R,D] (rank 5, U(1) only) whose double layer
+ * sum_P A (x) A* has the legs fuse(A.x, A.x^dual); then a is never formed:
+ * every contraction with it runs as a contraction with A and one with A*
+ * (the edges' site legs are split into ket and bra parts and fused back).
+ *
+ * SU(2) (site and environment BST_SU2): dir 0 only (the other directions
+ * permute legs, which for SU(2) blocks needs tree recoupling:
+ * BST_E_UNSUPPORTED); chi is the total dimension of the new bond, filled by
+ * whole multiplets in descending singular value (one that would overflow
+ * chi is skipped), stats->kept is that total dimension; the new bond is
+ * incoming on C1' and T4' (outgoing on T4''s first leg and on C4'). */
 BST_API bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a,
                         bst_env* env, int64_t chi, double rel_cutoff, bst_prec prec,
                         bst_ctm_stats* stats, bst_stream stream);
