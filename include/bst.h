@@ -11,7 +11,7 @@
  * the rule is enforced by hand (Sec. 2, text after Eq. "tensor-cgc").
  *
  * Conventions used by every call:
- *   - charges are integers: 2*Sz for U(1);
+ *   - charges are integers: 2*Sz for U(1), doubled spins 2j for SU(2);
  *   - a leg's sectors are given with strictly ascending charges and
  *     positive reduced degeneracies (Sec. 2, "Reduced and Total
  *     Dimensions": the reduced dimension is the sum of the degeneracies);
@@ -114,7 +114,8 @@ BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
 /* Eigensolver behind bst_svd_projector and bst_ctm_move.
  *   BST_PROJ_SUBSPACE (default): per sector of N, subspace iteration on
  *     N^T N with a block of 160 vectors (CholQR orthonormalisation), in
- *     rounds of `iters` steps, each closed by a Rayleigh-Ritz step in FP64
+ *     rounds (the first two of `iters` steps, later ones sized by the
+ *     residual's observed decay), each closed by a Rayleigh-Ritz step in FP64
  *     (FP32 Jacobi eigensolver refined by Ogita-Aishima steps); sectors of
  *     dimension <= 160 are decomposed directly.  A round is accepted when
  *     every Ritz pair the truncation keeps has a residual
