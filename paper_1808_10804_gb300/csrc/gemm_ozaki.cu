@@ -401,18 +401,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Split FP64 rows into the five BF16 digit slices (integer arithmetic on the
 // bit pattern).  One warp per row; digits for k in [K, roundup(K, 32)) are 0.
-__global__ void ozaki_split_kernel(const SplitTask* __restrict__ tasks, int ntasks, const double* __restrict__ X,
-                                   __nv_bfloat16* __restrict__ S, int* __restrict__ ex, int rows_total,
-                                   int kpitch) {
-  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One launch splits both operands: CTAs [0, ga) take the rows of A, the
+// others those of B.  The task of a row is found by binary search over the
+// tasks' first rows (ascending).
+struct SplitJob {
+  const SplitTask* tasks;
+  int ntasks, rows_total;
+  const double* X;
+  __nv_bfloat16* S;
+  int* ex;
+};
+
+__global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch) {
+  const bool is_a = int(blockIdx.x) < ga;
+  const SplitJob& J = is_a ? ja : jb;
+  const SplitTask* __restrict__ tasks = J.tasks;
+  const int ntasks = J.ntasks, rows_total = J.rows_total;
+  const double* __restrict__ X = J.X;
+  __nv_bfloat16* __restrict__ S = J.S;
+  int* __restrict__ ex = J.ex;
+  const int warp_g = ((int(blockIdx.x) - (is_a ? 0 : ga)) * int(blockDim.x) + int(threadIdx.x)) >> 5;
   const int lane = threadIdx.x & 31;
-  // locate (task, row)
-  int t = 0, r = warp_g;
-  while (t < ntasks && r >= tasks[t].rows) {
-    r -= tasks[t].rows;
-    ++t;
+  if (warp_g >= rows_total || ntasks == 0) return;
+  // locate (task, row): last task whose first row is <= warp_g
+  int tlo = 0, thi = ntasks - 1;
+  while (tlo < thi) {
+    const int mid = (tlo + thi + 1) >> 1;
+    if (tasks[mid].row0 <= warp_g) tlo = mid;
+    else thi = mid - 1;
   }
-  if (t >= ntasks) return;
+  const int t = tlo;
+  const int r = warp_g - tasks[t].row0;
+  if (r < 0 || r >= tasks[t].rows) return;
   const SplitTask tk = tasks[t];
   const double* xr = X + tk.base + (long long)r * tk.s_r;
   unsigned long long mx = 0;
@@ -647,12 +667,14 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
   {
     ProfScope ps(ctx, s, "split_bf16", 0.0, P->split_bytes);
     const int wa = split_a ? P->rowsA : 0, wb = P->rowsB;
-    if (wa) oz::ozaki_split_kernel<<<(wa + 7) / 8, 256, 0, s>>>(P->d_sa, P->nsa, A, P->SA, P->eA, P->rowsA,
-                                                               P->kpitch);
-    if (wb) oz::ozaki_split_kernel<<<(wb + 7) / 8, 256, 0, s>>>(P->d_sb, P->nsb, B, P->SB, P->eB, P->rowsB,
-                                                               P->kpitch);
+    const int ga = (wa + 7) / 8, gb = (wb + 7) / 8;  // 8 rows (warps) per CTA
+    if (ga + gb > 0) {
+      const oz::SplitJob ja{P->d_sa, P->nsa, P->rowsA, A, P->SA, P->eA};
+      const oz::SplitJob jb{P->d_sb, P->nsb, P->rowsB, B, P->SB, P->eB};
+      oz::ozaki_split_kernel<<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
+    }
     BST_CUDA(cudaGetLastError());
-    count_launch(ctx, (wa ? 1 : 0) + (wb ? 1 : 0));
+    count_launch(ctx, (wa + wb) > 0 ? 1 : 0);
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
   const int grid = std::min(P->ntiles, num_sms());
