@@ -41,6 +41,12 @@ static bst_status guarded(F&& f) {
 
 namespace bst {
 Ctx::~Ctx() {
+  if (side) {
+    cudaStreamSynchronize(side);
+    cudaStreamDestroy(side);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   projviews.clear();
   su2plans.clear();
   bplans.clear();

@@ -219,6 +219,10 @@ struct Ctx {
   double* d_scratch_small = nullptr;
   bool autotune = true;      // time schedule candidates on the first batched call of a plan
   std::string tune_log;      // one line per tuning decision
+  // second stream for work that overlaps the caller's stream inside one
+  // call (the projector's direct sectors), with its fork and join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ~Ctx();
   void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
 };
@@ -252,8 +256,9 @@ void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* 
                      cudaStream_t s);
 // the same product with K split into ksplit slices reduced in a fixed order
 // (more CTAs for small, deep products)
+// ws names the context buffer that holds the K-slice partial products
 void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double* A, const double* B, double* C,
-                            cudaStream_t s);
+                            cudaStream_t s, const char* ws = "gemm_f64.splitk");
 extern const int kF64TileM, kF64TileN;
 
 // gemm_ozaki.cu

@@ -29,7 +29,7 @@ struct SmallProb {
 // One CTA per problem.  A and V live in shared memory as FP32.
 __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
                                                       double* __restrict__ out, double* __restrict__ vals,
-                                                      int max_sweeps) {
+                                                      int max_sweeps, float tfloor, float junk) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
   const int b = pr.b;
@@ -74,15 +74,20 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   constexpr float kTau = 1e-5f;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test relative to the diagonal (keeps small eigenvalues
-    // accurate) with a floor kTau below which values are not resolved:
-    // max_{i<j} a_ij^2 / (max(|a_ii|, kTau) max(|a_jj|, kTau)); one thread
-    // per row
+    // accurate) with a floor tfloor below which values are not resolved:
+    // max_{i<j} a_ij^2 / (max(|a_ii|, tfloor) max(|a_jj|, tfloor)); with a
+    // floor of 1 (the scale) the test is absolute.  Pairs whose diagonal
+    // entries are both below `junk` are left out (a cluster at the FP32
+    // rounding level of the input, where rotations only move noise); one
+    // thread per row
     float worst = 0.f;
     for (int i = tid; i < b; i += nt) {
-      const float di = fmaxf(fabsf(A[i * ld + i]), kTau);
+      const float ai = fabsf(A[i * ld + i]);
+      const float di = fmaxf(ai, tfloor);
       for (int j = i + 1; j < b; ++j) {
         const float a = A[i * ld + j];
-        worst = fmaxf(worst, a * a / (di * fmaxf(fabsf(A[j * ld + j]), kTau)));
+        const float aj = fabsf(A[j * ld + j]);
+        if (fmaxf(ai, aj) >= junk) worst = fmaxf(worst, a * a / (di * fmaxf(aj, tfloor)));
       }
     }
     red[tid] = worst;
@@ -275,27 +280,42 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
   for (int kb = 0; kb < b; kb += 32) {
     const int w = min(32, b - kb);
     if (warp == 0) {
-      for (int c = 0; c < w; ++c) {
-        const int k = kb + c;
-        if (lane == 0) {
-          const float d = L[k * ld + k];
-          drop[k] = !(d > 1e-6f);
-          L[k * ld + k] = drop[k] ? 1.0f : sqrtf(d);
-        }
-        __syncwarp();
-        const int dk = drop[k];
-        const float lkk = L[k * ld + k];
-        // column k inside the block, and row k left of the diagonal if dropped
-        for (int i = k + 1 + lane; i < kb + w; i += 32) L[i * ld + k] = dk ? 0.f : L[i * ld + k] / lkk;
-        if (dk)
-          for (int j = kb + lane; j < k; j += 32) L[k * ld + j] = 0.f;
-        __syncwarp();
-        if (!dk)
-          for (int i = k + 1 + lane; i < kb + w; i += 32) {
-            const float lik = L[i * ld + k];
-            for (int j = k + 1; j <= i; ++j) L[i * ld + j] -= lik * L[j * ld + k];
+      // the 32x32 diagonal block in registers, lane i holding row kb+i;
+      // pivots and column entries travel by warp shuffles
+      float row[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) row[c] = (lane < w && c < w) ? L[(kb + lane) * ld + kb + c] : 0.f;
+      int mydrop = 0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < w) {
+          const float dkk = __shfl_sync(0xffffffffu, row[k], k);
+          const bool dk = !(dkk > 1e-6f);
+          const float lkk = dk ? 1.0f : sqrtf(dkk);
+          if (lane == k) {
+            row[k] = lkk;
+            mydrop = dk;
+            if (dk) {
+#pragma unroll
+              for (int c = 0; c < k; ++c) row[c] = 0.f;
+            }
+          } else if (lane > k) {
+            row[k] = dk ? 0.f : row[k] / lkk;
           }
-        __syncwarp();
+          if (!dk) {
+#pragma unroll
+            for (int j = k + 1; j < 32; ++j) {
+              const float ljk = __shfl_sync(0xffffffffu, row[k], j);
+              if (lane >= j) row[j] -= row[k] * ljk;
+            }
+          }
+        }
+      }
+      if (lane < w) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < w) L[(kb + lane) * ld + kb + c] = row[c];
+        drop[kb + lane] = mydrop;
       }
     }
     __syncthreads();
@@ -303,18 +323,29 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
     for (int c = 0; c < w; ++c)
       if (drop[kb + c])
         for (int j = tid; j < kb; j += nt) L[(kb + c) * ld + j] = 0.f;
-    // panel solve: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T
+    // panel solve: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T, the
+    // row in registers, the diagonal block read as broadcasts
     for (int i = kb + w + tid; i < b; i += nt) {
-      for (int c = 0; c < w; ++c) {
-        const int k = kb + c;
-        if (drop[k]) {
-          L[i * ld + k] = 0.f;
-          continue;
+      float x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = c < w ? L[i * ld + kb + c] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < w) {
+          const int k = kb + c;
+          if (drop[k]) {
+            x[c] = 0.f;
+          } else {
+            float v = x[c];
+#pragma unroll
+            for (int cc = 0; cc < c; ++cc) v -= x[cc] * L[k * ld + kb + cc];
+            x[c] = v / L[k * ld + k];
+          }
         }
-        float v = L[i * ld + k];
-        for (int cc = 0; cc < c; ++cc) v -= L[i * ld + kb + cc] * L[k * ld + kb + cc];
-        L[i * ld + k] = v / L[k * ld + k];
       }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < w) L[i * ld + kb + c] = x[c];
     }
     __syncthreads();
     // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i

@@ -196,13 +196,13 @@ DevGemm* get_dev_gemm(Ctx* ctx, const std::string& key, const std::vector<GemmPr
 }
 
 void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double* A, const double* B, double* C,
-                            cudaStream_t s) {
+                            cudaStream_t s, const char* ws) {
   if (g.ntiles == 0) return;
   if (ksplit <= 1) {
     launch_gemm_f64(ctx, g, A, B, C, s);
     return;
   }
-  double* W = (double*)ctx->buf("gemm_f64.splitk", sizeof(double) * std::max<int64_t>(1, g.wtot * ksplit), s);
+  double* W = (double*)ctx->buf(ws, sizeof(double) * std::max<int64_t>(1, g.wtot * ksplit), s);
   ProfScope ps(ctx, s, "gemm_f64", g.flops, 0.0);
   gemm_f64_splitk_kernel<<<dim3(unsigned(g.ntiles), unsigned(ksplit)), 128, 0, s>>>(
       g.probs, g.tile_prob, g.tile_idx, A, B, W, g.w_off, g.wtot, ksplit);

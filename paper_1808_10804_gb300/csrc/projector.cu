@@ -115,7 +115,7 @@ struct ResProb {
   int32_t m, k;
   int64_t y_off, v_off, val_off, ld;
 };
-__global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int);
+__global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
 __global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double);
 __global__ void add_inplace(double*, const double*, long long);
 __global__ void cholinv_f32(const SmallProb*, const double*, double*, int*);
@@ -142,7 +142,8 @@ static std::string probs_key(const std::vector<GemmProb>& probs) {
 
 // FP64-accurate grouped GEMM in the requested arithmetic.
 static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std::vector<GemmProb>& probs,
-                     const double* A, const double* B, double* C, cudaStream_t s, bool same_a = false) {
+                     const double* A, const double* B, double* C, cudaStream_t s, bool same_a = false,
+                     const char* ws = "gemm_f64.splitk") {
   if (probs.empty()) return;
   if (prec == BST_FP64) {
     // the projector's FP64 products are small and deep (b x b x K): split K
@@ -151,7 +152,7 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
     int ksplit = 1;
     if (g.ntiles > 0 && g.ntiles < 304)
       ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 64, 16}));
-    launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s);
+    launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s, ws);
   }
   else
     run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s, 0, !same_a);
@@ -188,20 +189,24 @@ static void setup_attrs() {
 // (H1 = X1^T H X1, nearly diagonal) and a second FP32 Jacobi pass resolves
 // it to high relative accuracy; two Ogita-Aishima steps then bring the
 // vectors and values to FP64 accuracy.  Values below 1e-6 of the largest
-// are treated as one unresolved cluster.
+// are treated as one unresolved cluster.  `pre` prefixes every workspace,
+// plan and table name, so calls with different prefixes may run on
+// different streams at the same time.
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
-                      int64_t smtot, int64_t valtot, cudaStream_t s) {
+                      int64_t smtot, int64_t valtot, cudaStream_t s, const std::string& pre = "") {
   if (sp.empty()) return;
   setup_attrs();
-  SmallProb* dsp = upload_cached(ctx, "eig.sp", sp, s);
+  SmallProb* dsp = upload_cached(ctx, pre + "eig.sp", sp, s);
   int bmax = 0;
   for (auto& p : sp) bmax = std::max(bmax, p.b);
-  double* X1 = (double*)ctx->buf("eig.x1", sizeof(double) * smtot, s);
-  double* H1 = (double*)ctx->buf("eig.h1", sizeof(double) * smtot, s);
-  double* XtX = (double*)ctx->buf("eig.xtx", sizeof(double) * smtot, s);
-  double* T = (double*)ctx->buf("eig.t", sizeof(double) * smtot, s);
-  double* S = (double*)ctx->buf("eig.s", sizeof(double) * smtot, s);
-  double* E = (double*)ctx->buf("eig.e", sizeof(double) * smtot, s);
+  double* X1 = (double*)ctx->buf(pre + "eig.x1", sizeof(double) * smtot, s);
+  double* H1 = (double*)ctx->buf(pre + "eig.h1", sizeof(double) * smtot, s);
+  double* XtX = (double*)ctx->buf(pre + "eig.xtx", sizeof(double) * smtot, s);
+  double* T = (double*)ctx->buf(pre + "eig.t", sizeof(double) * smtot, s);
+  double* S = (double*)ctx->buf(pre + "eig.s", sizeof(double) * smtot, s);
+  double* E = (double*)ctx->buf(pre + "eig.e", sizeof(double) * smtot, s);
+  const std::string wsname = pre + "gemm_f64.splitk";
+  const char* ws = wsname.c_str();
   std::vector<GemmProb> g_xtx, g_hx, g_s, g_xe;
   for (auto& p : sp) {
     const int b = p.b;
@@ -217,25 +222,25 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   for (auto& p : sp) jac_flops += 7.0 * double(p.b) * p.b * 18.0 * p.b / 2.0;
   {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f /*P1*/);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
-  gemm_any(ctx, "oa.hx", prec, g_hx, H, X1, T, s);
-  gemm_any(ctx, "oa.s", prec, g_s, X1, T, H1, s);
+  gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X1, T, s, false, ws);
+  gemm_any(ctx, pre + "oa.s", prec, g_s, X1, T, H1, s, false, ws);
   {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f /*P2*/);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
-  gemm_any(ctx, "oa.xe", prec, g_xe, X1, T, X, s);  // X = X1 X2
+  gemm_any(ctx, pre + "oa.xe", prec, g_xe, X1, T, X, s, false, ws);  // X = X1 X2
   for (int it = 0; it < 2; ++it) {
-    gemm_any(ctx, "oa.xtx", prec, g_xtx, X, X, XtX, s);
-    gemm_any(ctx, "oa.hx", prec, g_hx, H, X, T, s);
-    gemm_any(ctx, "oa.s", prec, g_s, X, T, S, s);
+    gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
+    gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
+    gemm_any(ctx, pre + "oa.s", prec, g_s, X, T, S, s, false, ws);
     oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9, 1e-6);
-    gemm_any(ctx, "oa.xe", prec, g_xe, X, E, T, s);
+    gemm_any(ctx, pre + "oa.xe", prec, g_xe, X, E, T, s, false, ws);
     add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx, 2);
@@ -279,10 +284,9 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   double* lam = (double*)ctx->buf("proj.lam", sizeof(double) * std::max<int64_t>(valtot, 1), s);
   // row-major blocks: Q, Y [N x b] at q_off; Z, Z2 [M x b] at z_off
   std::vector<GemmProb> g_z, g_gz, g_qz, g_y, g_gy, g_qy, g_h, g_v, g_direct, g_polish;
-  std::vector<SmallProb> sp_it, sp_all;
+  std::vector<SmallProb> sp_it;
   for (auto& x : secs) {
     SmallProb sp{x.b, 0, x.sm_off, x.sm_off, x.val_off};
-    sp_all.push_back(sp);
     const int64_t no = x.cs->off;
     if (x.direct) {
       g_direct.push_back(gp(x.N, x.N, x.M, no, 1, x.N, no, 1, x.N, x.sm_off, x.N, 1));  // N^T N
@@ -367,6 +371,33 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   const int max_total = std::max(iters, 480);
   std::vector<double> hl(valtot), hres(valtot);
   double* res = (double*)ctx->buf("proj.res", sizeof(double) * std::max<int64_t>(valtot, 1), s);
+  // The direct sectors (N^T N decomposed whole) do not depend on the
+  // iterations: their Gram products and eigensolver run once, on the
+  // context's second stream, while the subspace iterations of the large
+  // sectors run on `s`; they write disjoint parts of Msm, Xv and lam and
+  // use their own workspaces.  A dense start needs several more Jacobi
+  // sweeps than the nearly diagonal Rayleigh-Ritz matrices, so they are
+  // kept out of the per-round eigensolver launches.
+  bool forked = false;
+  if (!g_direct.empty()) {
+    std::vector<SmallProb> sp_dir;
+    for (auto& x : secs)
+      if (x.direct) sp_dir.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
+    if (!ctx->side) {
+      BST_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      BST_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      BST_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
+    // (an earlier call that left by an error may still have side work in
+    // flight on these buffers: the fork orders after it)
+    BST_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    BST_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    BST_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    gemm_any(ctx, "side.ss.direct", rr, g_direct, Nm, Nm, Msm, ctx->side, false, "side.gemm_f64.splitk");
+    small_eig(ctx, rr, sp_dir, Msm, Xv, lam, smtot, valtot, ctx->side, "side.");
+    BST_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
+    forked = true;
+  }
   int total = 0, steps = iters;
   for (int round = 0;; ++round) {
     if (!sp_it.empty()) {
@@ -377,14 +408,17 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
       gemm_any(ctx, "ss.h", rr, g_h, Z, Z, Msm, s);
     }
-    gemm_any(ctx, "ss.direct", rr, g_direct, Nm, Nm, Msm, s);
-    small_eig(ctx, rr, sp_all, Msm, Xv, lam, smtot, valtot, s);
-    // V = Q W (iterative) or W (direct)
+    small_eig(ctx, rr, sp_it, Msm, Xv, lam, smtot, valtot, s);
+    // V = Q W (iterative) or W (direct, once the second stream is joined)
     if (!g_v.empty()) gemm_any(ctx, "ss.v", rr, g_v, Q, Xv, dV, s);
-    for (auto& x : secs)
-      if (x.direct)
-        BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
-                                 cudaMemcpyDeviceToDevice, s));
+    if (forked) {
+      BST_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+      forked = false;
+      for (auto& x : secs)
+        if (x.direct)
+          BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
+                                   cudaMemcpyDeviceToDevice, s));
+    }
     BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
     BST_CUDA(cudaStreamSynchronize(s));
     if (sp_it.empty()) break;
