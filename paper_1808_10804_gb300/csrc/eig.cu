@@ -244,72 +244,149 @@ __global__ void add_inplace(double* __restrict__ X, const double* __restrict__ X
     X[i] += XE[i];
 }
 
+// Conversions between FP64 and FP32 with a power-of-two scale, built from
+// the IEEE-754 fields with integer operations: the FP64 pipe of this part
+// is narrow (a few operations per clock per SM), so per-element FP64
+// multiplies and conversions would dominate the small kernels' loads and
+// stores.
+// float(x * 2^e), rounded to nearest even; results below the FP32 normal
+// range flush to zero and above it saturate to infinity.
+__device__ __forceinline__ float f64_to_f32_scaled(double x, int e) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned sign = unsigned(u >> 32) & 0x80000000u;
+  const int ex = int((u >> 52) & 0x7ff);
+  const unsigned long long mant = u & 0xfffffffffffffull;
+  if (ex == 0) return __uint_as_float(sign);  // zero and FP64 subnormals
+  if (ex == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
+  int fe = ex - 1023 + e + 127;
+  unsigned m = unsigned(mant >> 29);
+  const unsigned rest = unsigned(mant & 0x1fffffffull);  // the 29 dropped bits
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ++m;
+  if (m == 0x800000u) {
+    m = 0;
+    ++fe;
+  }
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | (unsigned(fe) << 23) | m);
+}
+
+// double(f) * 2^e, exact; FP32 subnormals flush to zero.
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int e) {
+  const unsigned v = __float_as_uint(f);
+  const unsigned long long sign = static_cast<unsigned long long>(v & 0x80000000u) << 32;
+  const int ex = int((v >> 23) & 0xff);
+  const unsigned long long mant = static_cast<unsigned long long>(v & 0x7fffffu) << 29;
+  if (ex == 0) return __longlong_as_double(static_cast<long long>(sign));
+  if (ex == 0xff) return __longlong_as_double(static_cast<long long>(sign | 0x7ff0000000000000ull | mant));
+  const int de = ex - 127 + 1023 + e;
+  if (de <= 0) return __longlong_as_double(static_cast<long long>(sign));
+  if (de >= 0x7ff) return __longlong_as_double(static_cast<long long>(sign | 0x7ff0000000000000ull));
+  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(de) << 52) | mant));
+}
+
+// x = r * 2^k with r in [1, 2) (x > 0 finite and normal)
+__device__ __forceinline__ void split_pow2(double x, int* k, float* r) {
+  const int ex = int((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ff);
+  *k = ex - 1023;
+  *r = f64_to_f32_scaled(x, -*k);
+}
+
 // FP32 Cholesky of M (b x b, FP64 in) and Rinv = (L^T)^-1 (upper, FP64 out).
-__global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
-                                                   double* __restrict__ out, int* err) {
+// 512 threads; b <= 160.
+__global__ void __launch_bounds__(512) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
+                                                  double* __restrict__ out, int* err) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
-  const int b = pr.b, ld = b + 1;
+  const int b = pr.b, ld = b + 1, bb = b * b;
   float* L = sh;            // b x ld
   float* Li = L + b * ld;   // b x ld, inverse of L
+  int* drop = reinterpret_cast<int*>(Li + b * ld + b);
+  float* rsc = Li + b * ld;                                  // b row scales: mantissas
+  int* ksc = reinterpret_cast<int*>(Li + b * ld + 2 * b);    // b row scales: exponents
   const double* M = in + pr.in_off;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // scale by the diagonal so the factorisation sees unit diagonal; the
-  // scales are formed once per row in FP64 (one square root and division
-  // each), the matrix entries then need two FP64 products
-  float* dsc = Li + b * ld;
-  double* dscd = reinterpret_cast<double*>(dsc + b + b);  // float offset 2b(b+1)+2b: 8-byte aligned
+  const int warp = tid >> 5, lane = tid & 31;
+  // scale by the diagonal so the factorisation sees unit diagonal: row i is
+  // scaled by 1/sqrt(M_ii) = rsc[i] 2^ksc[i] (one FP64 square root and
+  // division per row); the entries take the power of two exactly in the
+  // conversion to FP32 and the mantissas as two FP32 products
   for (int i = tid; i < b; i += nt) {
     const double d = M[(long long)i * b + i];
-    dscd[i] = d > 0 ? 1.0 / sqrt(d) : 1.0;
+    int k = 0;
+    float r = 1.f;
+    if (d > 0) split_pow2(1.0 / sqrt(d), &k, &r);
+    ksc[i] = k;
+    rsc[i] = r;
   }
   __syncthreads();
-  for (int q = tid; q < b * b; q += nt) {
-    const int i = q / b, j = q - i * b;
-    L[i * ld + j] = float(M[q] * dscd[i] * dscd[j]);
+  // eight global loads in flight per thread
+  for (int q0 = tid; q0 < bb; q0 += 8 * nt) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u * nt;
+      v[u] = q < bb ? M[q] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u * nt;
+      if (q < bb) {
+        const int i = q / b, j = q - i * b;
+        L[i * ld + j] = f64_to_f32_scaled(v[u], ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+        Li[i * ld + j] = 0.f;
+      }
+    }
   }
   __syncthreads();
-  // Blocked right-looking factorisation with 32-wide panels: warp 0
-  // factors the diagonal block (warp-synchronous), all threads then solve
-  // the panel below it and update the trailing lower triangle.
-  // Columns whose pivot falls below 1e-6 (numerically dependent on earlier
-  // ones at FP32 level) are dropped: their row and column of the factor
-  // become the identity and their column of Rinv is zero.
-  int* drop = reinterpret_cast<int*>(dsc + b);
-  const int warp = tid >> 5, lane = tid & 31;
+  // Blocked right-looking factorisation with 32-wide panels.  Warp 0
+  // factors the diagonal block D in registers (lane i holds row i, pivots
+  // and column entries travel by warp shuffles) and forms D^-1 column by
+  // lane (stored as the diagonal block of Li).  The panel below is then panel * D^-T, and
+  // all threads update the trailing lower triangle.  Columns whose pivot
+  // falls below 1e-6 (numerically dependent on earlier ones at FP32 level)
+  // are dropped: their row and column of the factor become the identity
+  // and their column of Rinv is zero.
   for (int kb = 0; kb < b; kb += 32) {
     const int w = min(32, b - kb);
     if (warp == 0) {
-      // the 32x32 diagonal block in registers, lane i holding row kb+i;
-      // pivots and column entries travel by warp shuffles
       float row[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) row[c] = (lane < w && c < w) ? L[(kb + lane) * ld + kb + c] : 0.f;
       int mydrop = 0;
+      float myinv = 1.f;  // 1 / D[lane][lane]
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
         if (k < w) {
           const float dkk = __shfl_sync(0xffffffffu, row[k], k);
-          const bool dk = !(dkk > 1e-6f);
-          const float lkk = dk ? 1.0f : sqrtf(dkk);
-          if (lane == k) {
-            row[k] = lkk;
-            mydrop = dk;
-            if (dk) {
+          const bool dk = !(dkk > 1e-6f);  // the same on every lane
+          const float inv = dk ? 1.f : rsqrtf(dkk);
+          const bool me = lane == k;
+          row[k] = me ? (dk ? 1.f : dkk * inv) : (lane > k ? (dk ? 0.f : row[k] * inv) : row[k]);
+          mydrop = me ? int(dk) : mydrop;
+          myinv = me ? inv : myinv;
+          if (dk) {
+            // row k of the factor becomes that of the identity
 #pragma unroll
-              for (int c = 0; c < k; ++c) row[c] = 0.f;
-            }
-          } else if (lane > k) {
-            row[k] = dk ? 0.f : row[k] / lkk;
-          }
-          if (!dk) {
+            for (int c = 0; c < k; ++c) row[c] = me ? 0.f : row[c];
+          } else {
 #pragma unroll
             for (int j = k + 1; j < 32; ++j) {
               const float ljk = __shfl_sync(0xffffffffu, row[k], j);
-              if (lane >= j) row[j] -= row[k] * ljk;
+              row[j] = lane >= j ? fmaf(-row[k], ljk, row[j]) : row[j];
             }
           }
         }
+      }
+      // column `lane` of D^-1 by forward substitution, D[i][k] and
+      // 1 / D[i][i] broadcast from lane i
+      float col[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        float acc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc = fmaf(-__shfl_sync(0xffffffffu, row[k], i), col[k], acc);
+        col[i] = acc * __shfl_sync(0xffffffffu, myinv, i);
       }
       if (lane < w) {
 #pragma unroll
@@ -317,39 +394,45 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
           if (c < w) L[(kb + lane) * ld + kb + c] = row[c];
         drop[kb + lane] = mydrop;
       }
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < w && lane < w) Li[(kb + i) * ld + kb + lane] = col[i];
     }
     __syncthreads();
     // dropped columns of this block: zero their rows left of the block too
     for (int c = 0; c < w; ++c)
       if (drop[kb + c])
         for (int j = tid; j < kb; j += nt) L[(kb + c) * ld + j] = 0.f;
-    // panel solve: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T, the
-    // row in registers, the diagonal block read as broadcasts
-    for (int i = kb + w + tid; i < b; i += nt) {
-      float x[32];
+    // panel: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T; four threads
+    // per row, eight columns each; the row is read whole before any thread
+    // of it writes
+    const int m = b - kb - w;
+    for (int base = 0; base < 4 * m; base += nt) {
+      const int item = base + tid;
+      const bool act = item < 4 * m;
+      const int i = kb + w + (act ? item >> 2 : 0), g = item & 3;
+      float y[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) x[c] = c < w ? L[i * ld + kb + c] : 0.f;
+      for (int c = 0; c < 32; ++c) y[c] = (act && c < w) ? L[i * ld + kb + c] : 0.f;
+      __syncthreads();
+      if (act) {
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c < w) {
-          const int k = kb + c;
-          if (drop[k]) {
-            x[c] = 0.f;
-          } else {
-            float v = x[c];
+        for (int u = 0; u < 8; ++u) {
+          const int c = 8 * g + u;
+          if (c < w) {
+            // D^-1 is lower triangular (zeros above its diagonal); columns
+            // past the block (y = 0 there) read a valid entry instead
+            const float* dinv = Li + (kb + c) * ld + kb;
+            float acc = 0.f;
 #pragma unroll
-            for (int cc = 0; cc < c; ++cc) v -= x[cc] * L[k * ld + kb + cc];
-            x[c] = v / L[k * ld + k];
+            for (int cc = 0; cc < 32; ++cc) acc = fmaf(y[cc], dinv[cc < w ? cc : 0], acc);
+            L[i * ld + kb + c] = drop[kb + c] ? 0.f : acc;
           }
         }
       }
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < w) L[i * ld + kb + c] = x[c];
     }
     __syncthreads();
     // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i
-    const int m = b - kb - w;
     if (m > 0) {
       const int P = nt / m > 0 ? nt / m : 1;
       const int jj = tid % m, ph = tid / m;
@@ -368,63 +451,81 @@ __global__ void __launch_bounds__(1024) cholinv_f32(const SmallProb* __restrict_
     }
     __syncthreads();
   }
-  // inverse of the lower factor, blocked: diagonal 32x32 blocks by one warp
-  // each, then block rows in order, Li[I][J] = -Li[I][I] sum_K L[I][K] Li[K][J]
+  // inverse of the lower factor by block rows (the diagonal blocks D^-1 are
+  // in place): Li[I][J] = -D_I^-1 sum_{K=J}^{I-1} L[I][K] Li[K][J].  Thread
+  // (warp ty, lane tx) owns rows ib+ty, ib+ty+16 and columns tx+32s, s < I.
   const int nb = (b + 31) / 32;
-  for (int q = tid; q < b * b; q += nt) {
-    const int i = q / b, j = q - i * b;
-    Li[i * ld + j] = 0.f;
-  }
-  __syncthreads();
-  if (warp < nb) {
-    const int kb = warp * 32, w = min(32, b - kb);
-    // column lane of the diagonal block's inverse by forward substitution
-    if (lane < w) {
-      const int j = kb + lane;
-      for (int i = j; i < kb + w; ++i) {
-        float acc = (i == j) ? 1.f : 0.f;
-        for (int k = j; k < i; ++k) acc -= L[i * ld + k] * Li[k * ld + j];
-        Li[i * ld + j] = acc / L[i * ld + i];
+  for (int I = 1; I < nb; ++I) {
+    const int ib = I * 32;
+    const int r0 = min(ib + warp, b - 1), r1 = min(ib + warp + 16, b - 1);
+    // T[i][j] = sum_{k < ib} L[i][k] Li[k][j], stashed in the (unused)
+    // upper triangle of Li at [j][i]
+    float acc[2][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = 0.f;
+    for (int k = 0; k < ib; ++k) {
+      const float a0 = L[r0 * ld + k], a1 = L[r1 * ld + k];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        // Li[k][j] is zero for k < j; rows above block s are skipped (they
+        // hold earlier stashes)
+        if (s < I && k >= 32 * s) {
+          const float v = Li[k * ld + lane + 32 * s];
+          acc[0][s] = fmaf(a0, v, acc[0][s]);
+          acc[1][s] = fmaf(a1, v, acc[1][s]);
+        }
       }
     }
-  }
-  __syncthreads();
-  for (int I = 1; I < nb; ++I) {
-    const int ib = I * 32, wi = min(32, b - ib);
-    // T[I][J] = sum_{K=J}^{I-1} L[I][K] Li[K][J] for all J < I, stored in the
-    // (still zero) upper part of Li at [J][I] transposed... kept in registers:
-    // each thread owns one (row i, column j) entry of the block row
-    for (int q = tid; q < wi * ib; q += nt) {
-      const int r = q / ib, j = q - r * ib;
-      const int i = ib + r;
-      const int jb = (j / 32) * 32;
-      float acc = 0.f;
-      for (int k = jb; k < ib; ++k) acc += L[i * ld + k] * Li[k * ld + j];
-      // stash in the upper triangle (unused) of Li: position [j][i]
-      Li[j * ld + i] = acc;
-    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < I) {
+        const int j = lane + 32 * s;
+        if (ib + warp < b) Li[j * ld + ib + warp] = acc[0][s];
+        if (ib + warp + 16 < b) Li[j * ld + ib + warp + 16] = acc[1][s];
+      }
     __syncthreads();
-    for (int q = tid; q < wi * ib; q += nt) {
-      const int r = q / ib, j = q - r * ib;
-      const int i = ib + r;
-      float acc = 0.f;
-      for (int k = ib; k <= i; ++k) acc -= Li[i * ld + k] * Li[j * ld + k];
-      Li[i * ld + j] = acc;
+    // Li[i][j] = -sum_{k in block I} D_I^-1[i][k] T[k][j]
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = 0.f;
+    const int wi = min(32, b - ib);
+    for (int kk = 0; kk < wi; ++kk) {
+      const int k = ib + kk;
+      const float a0 = Li[r0 * ld + k], a1 = Li[r1 * ld + k];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (s < I) {
+          const float v = Li[(lane + 32 * s) * ld + k];
+          acc[0][s] = fmaf(a0, v, acc[0][s]);
+          acc[1][s] = fmaf(a1, v, acc[1][s]);
+        }
     }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < I) {
+        const int j = lane + 32 * s;
+        if (ib + warp < b) Li[(ib + warp) * ld + j] = -acc[0][s];
+        if (ib + warp + 16 < b) Li[(ib + warp + 16) * ld + j] = -acc[1][s];
+      }
     __syncthreads();
   }
   // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
-  // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i]
+  // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i] = (rsc[i] Li[j][i]) 2^ksc[i]
   double* R = out + pr.out_off;
-  for (int q = tid; q < b * b; q += nt) {
-    const int i = q / b, j = q - i * b;
-    R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : dscd[i] * double(Li[j * ld + i]);
+  for (int q0 = tid; q0 < bb; q0 += 4 * nt) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * nt;
+      if (q < bb) {
+        const int i = q / b, j = q - i * b;
+        R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : f32_to_f64_scaled(rsc[i] * Li[j * ld + i], ksc[i]);
+      }
+    }
   }
 }
 
 size_t cholinv_smem(int b) {
-  // L, Li (b x (b+1) floats), dsc (b floats), drop (b ints), pad, dscd (b doubles)
-  return sizeof(float) * (2 * b * (b + 1) + 2 * b) + sizeof(double) * b;
+  // L, Li (b x (b+1) floats), rsc (b floats), drop (b ints), ksc (b ints)
+  return sizeof(float) * (2 * b * (b + 1) + 3 * b);
 }
 
 // out = alpha * I + beta * in (square blocks)

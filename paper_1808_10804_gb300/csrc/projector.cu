@@ -311,7 +311,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   for (auto& x : sp_it) chol_flops += 2.0 * 2.0 * double(x.b) * x.b * x.b / 3.0;  // factor + inverse, FMA = 2
   auto cholinv = [&]() {
     ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
-    cholinv_f32<<<int(sp_it.size()), 1024, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+    cholinv_f32<<<int(sp_it.size()), 512, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   };

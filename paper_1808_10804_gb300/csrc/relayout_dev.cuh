@@ -65,6 +65,16 @@ __device__ __forceinline__ void relayout_range(const RelTask& t, int begin, int 
 #pragma unroll
       for (int u = 0; u < kU; ++u)
         if (ok[u]) mat[mo[u]] = v[u];
+    } else if (alpha == 1.0 && beta == 0.0) {
+      // plain gather: no FP64 arithmetic (the FP64 pipe is narrow enough
+      // that one multiply per element would cost about as much as its
+      // 16 bytes of traffic)
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ok[u]) v[u] = mat[mo[u]];
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ok[u]) blk[t.blk_off + e0 + u * kThreads] = v[u];
     } else {
 #pragma unroll
       for (int u = 0; u < kU; ++u)
