@@ -258,9 +258,18 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   // whose error is amplified by 1/gap, and always runs in FP64.
   const bst_prec rr = BST_FP64;
   int64_t vtot = 0, qtot = 0, ztot = 0, smtot = 0, valtot = 0;
+  // Block of an iterated sector.  In mixed precision: a sector keeps at
+  // most chi vectors; half as many again (plus 16) set the convergence rate
+  // (sigma_{b+1} / sigma_kept)^2 per iteration; multiples of 32, at most
+  // 160 (the Cholesky and eigensolver costs grow as b^2 and b^3, the
+  // products as b).  In FP64 the full 160: the wider guard band keeps the
+  // vectors at the truncation edge at FP64 accuracy.
+  const int b_it = prec == BST_FP64
+                       ? kEigMax
+                       : int(std::min<int64_t>(kEigMax, std::max<int64_t>(64, (chi + chi / 2 + 16 + 31) / 32 * 32)));
   for (auto& x : secs) {
     x.direct = x.N <= kEigMax;
-    x.b = x.direct ? x.N : kEigMax;
+    x.b = x.direct ? x.N : b_it;
     x.c = x.b;
     x.v_off = vtot;
     vtot += int64_t(x.N) * x.c;
