@@ -18,6 +18,7 @@
 namespace bst {
 
 constexpr int kEigMax = 160;
+constexpr int kOaMax = 160;  // largest b of oa_update
 
 struct SmallProb {
   int32_t b, pad;
@@ -199,6 +200,9 @@ size_t jacobi_smem(int b) {
 // E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when the pair is separated,
 // |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|) and not both below
 // junk * max|lam| (values the FP32 stage cannot resolve), else R_ij / 2.
+// Grid (problem, slice): every CTA forms the b values in shared memory
+// (slice 0 also stores them) and then its slice of the b x b entries, so
+// the FP64 divisions spread over the whole GPU.
 __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __restrict__ XtX,
                           const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam,
                           double rel_delta, double junk) {
@@ -207,7 +211,7 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
   const double* xx = XtX + pr.in_off;
   const double* s = S + pr.in_off;
   double* e = E + pr.in_off;
-  double* l = lam + pr.val_off;
+  __shared__ double l[kOaMax];
   __shared__ double smax;
   __shared__ double wmax[32];
   double m = 0;
@@ -215,6 +219,7 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
     const double rii = 1.0 - xx[(long long)i * b + i];
     const double li = s[(long long)i * b + i] / (1.0 - rii);
     l[i] = li;
+    if (blockIdx.y == 0) lam[pr.val_off + i] = li;
     m = fmax(m, fabs(li));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -226,8 +231,10 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
     smax = mm;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
-    const int i = q / b, j = q % b;
+  const int bb = b * b, per = (bb + int(gridDim.y) - 1) / int(gridDim.y);
+  const int q0 = int(blockIdx.y) * per, q1 = min(bb, q0 + per);
+  for (int q = q0 + int(threadIdx.x); q < q1; q += blockDim.x) {
+    const int i = q / b, j = q - i * b;
     const double rij = (i == j ? 1.0 : 0.0) - xx[q];
     const double delta = rel_delta * fmax(fabs(l[i]), fabs(l[j])) + 1e-300 * smax;
     const bool unresolved = fabs(l[i]) < junk * smax && fabs(l[j]) < junk * smax;

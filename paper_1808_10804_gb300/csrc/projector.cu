@@ -146,12 +146,13 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
                      const char* ws = "gemm_f64.splitk") {
   if (probs.empty()) return;
   if (prec == BST_FP64) {
-    // the projector's FP64 products are small and deep (b x b x K): split K
-    // until about two CTAs per SM are busy
+    // the projector's FP64 products are small and deep (b x b x K), and an
+    // SM does only ~8 GFLOP/s of FP64 tensor work: split K (slices down to
+    // 16 deep) until about two CTAs per SM are busy
     const DevGemm& g = *get_dev_gemm(ctx, tag + "/" + probs_key(probs), probs);
     int ksplit = 1;
     if (g.ntiles > 0 && g.ntiles < 304)
-      ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 64, 16}));
+      ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 16, 16}));
     launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s, ws);
   }
   else
@@ -239,7 +240,9 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
     gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
     gemm_any(ctx, pre + "oa.s", prec, g_s, X, T, S, s, false, ws);
-    oa_update<<<int(sp.size()), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9, 1e-6);
+    // about two CTAs per SM over all problems
+    const int slices = std::max(1, std::min(64, 304 / int(sp.size())));
+    oa_update<<<dim3(unsigned(sp.size()), unsigned(slices)), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9, 1e-6);
     gemm_any(ctx, pre + "oa.xe", prec, g_xe, X, E, T, s, false, ws);
     add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
     BST_CUDA(cudaGetLastError());
