@@ -337,7 +337,11 @@ typedef struct {
 typedef struct {
   int64_t kept[4];        /* kept states per directional move (L,R,U,D order of execution) */
   double smin_over_smax[4];
-  double trunc_weight[4]; /* sum of discarded sigma / sum of all sigma */
+  /* sum of discarded sigma / sum of all computed sigma: every sigma of a
+   * directly decomposed sector, the leading block of an iterated one; a
+   * small sector whose Frobenius norm is below the cut holds no kept state
+   * and is not decomposed (it adds nothing to either sum) */
+  double trunc_weight[4];
 } bst_ctm_stats;
 
 /* CTMRG move on a one-site cell (Sec. 3 and Sec. 3.2): dir 0 = LEFT (renews

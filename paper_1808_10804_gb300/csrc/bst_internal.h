@@ -223,6 +223,11 @@ struct Ctx {
   // call (the projector's direct sectors), with its fork and join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // projector: per sector structure, whether the last call found every
+  // directly decomposed sector unable to reach the truncation (scheduling
+  // hint only: such sectors are then deferred and, if still provably
+  // below the cut, skipped)
+  std::map<std::string, bool> direct_below_cut;
   ~Ctx();
   void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
 };

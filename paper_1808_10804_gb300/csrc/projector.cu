@@ -250,6 +250,21 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   }
 }
 
+// Sum of squares of each listed block of x (one CTA per block, fixed order).
+__global__ void block_sumsq(const double* __restrict__ x, const int64_t* __restrict__ off_n, double* __restrict__ out) {
+  const int64_t off = off_n[2 * blockIdx.x], n = off_n[2 * blockIdx.x + 1];
+  __shared__ double sh[256];
+  double acc = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += x[off + i] * x[off + i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
 // Leading right singular vectors of every sector of N: subspace iteration on
 // N^T N (block b) and a Rayleigh-Ritz step; small sectors directly.
 // Fills dV (row-major N x c per sector) and hSig; returns false when a
@@ -390,8 +405,39 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   // use their own workspaces.  A dense start needs several more Jacobi
   // sweeps than the nearly diagonal Rayleigh-Ritz matrices, so they are
   // kept out of the per-round eigensolver launches.
+  //
+  // A direct sector whose Frobenius norm is below the chi-th largest Ritz
+  // value of the iterated sectors cannot reach the truncation: Ritz values
+  // are lower bounds of the singular values (interlacing), so at least chi
+  // states lie above every singular value of that sector.  When the last
+  // call with this sector structure found all direct sectors below the
+  // cut, they are deferred to after the first Rayleigh-Ritz step and
+  // skipped if the bound holds again (their candidates are zero and never
+  // kept); otherwise they overlap on the second stream.
+  std::vector<int> dir_idx;
+  std::string dir_key = "chi" + std::to_string(chi);
+  for (size_t i = 0; i < secs.size(); ++i) {
+    dir_key += "," + std::to_string(secs[i].M) + "x" + std::to_string(secs[i].N);
+    if (secs[i].direct) dir_idx.push_back(int(i));
+  }
+  const bool can_defer = !dir_idx.empty() && !sp_it.empty();
+  const bool defer = can_defer && ctx->direct_below_cut.count(dir_key) && ctx->direct_below_cut[dir_key];
+  double* dfro = nullptr;
+  std::vector<double> hfro(dir_idx.size(), 0.0);
+  if (can_defer) {
+    std::vector<int64_t> offn;
+    for (int i : dir_idx) {
+      offn.push_back(secs[i].cs->off);
+      offn.push_back(int64_t(secs[i].M) * secs[i].N);
+    }
+    int64_t* doffn = upload_cached(ctx, "proj.fro.offn", offn, s);
+    dfro = (double*)ctx->buf("proj.fro", sizeof(double) * dir_idx.size(), s);
+    block_sumsq<<<int(dir_idx.size()), 256, 0, s>>>(Nm, doffn, dfro);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
   bool forked = false;
-  if (!g_direct.empty()) {
+  if (!g_direct.empty() && !defer) {
     std::vector<SmallProb> sp_dir;
     for (auto& x : secs)
       if (x.direct) sp_dir.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
@@ -432,7 +478,57 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                                    cudaMemcpyDeviceToDevice, s));
     }
     BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+    if (round == 0 && dfro)
+      BST_CUDA(cudaMemcpyAsync(hfro.data(), dfro, sizeof(double) * hfro.size(), cudaMemcpyDeviceToHost, s));
     BST_CUDA(cudaStreamSynchronize(s));
+    if (round == 0 && can_defer) {
+      // chi-th largest Ritz value of the iterated sectors
+      std::vector<double> rv;
+      for (auto& x : secs)
+        if (!x.direct)
+          for (int j = 0; j < x.c; ++j) rv.push_back(hl[x.val_off + j]);
+      double cut = 0;
+      if (int64_t(rv.size()) >= chi && chi > 0) {
+        std::nth_element(rv.begin(), rv.begin() + (chi - 1), rv.end(), std::greater<double>());
+        cut = rv[chi - 1];
+      }
+      // the margin covers the rounding of both sides
+      std::vector<char> below(dir_idx.size());
+      bool all_below = true;
+      for (size_t t = 0; t < dir_idx.size(); ++t) {
+        below[t] = cut > 0 && hfro[t] < 0.99 * cut;
+        all_below = all_below && below[t];
+      }
+      ctx->direct_below_cut[dir_key] = all_below;
+      if (defer) {
+        std::vector<GemmProb> g_rel;
+        std::vector<SmallProb> sp_rel;
+        for (size_t t = 0; t < dir_idx.size(); ++t) {
+          const PSec& x = secs[dir_idx[t]];
+          if (below[t]) {
+            BST_CUDA(cudaMemsetAsync(lam + x.val_off, 0, sizeof(double) * x.c, s));
+            BST_CUDA(cudaMemsetAsync(dV + x.v_off, 0, sizeof(double) * int64_t(x.N) * x.c, s));
+            for (int j = 0; j < x.c; ++j) hl[x.val_off + j] = 0.0;
+          } else {
+            const int64_t no = x.cs->off;
+            g_rel.push_back(gp(x.N, x.N, x.M, no, 1, x.N, no, 1, x.N, x.sm_off, x.N, 1));  // N^T N
+            sp_rel.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
+          }
+        }
+        if (!sp_rel.empty()) {
+          gemm_any(ctx, "ss.direct.late", rr, g_rel, Nm, Nm, Msm, s);
+          small_eig(ctx, rr, sp_rel, Msm, Xv, lam, smtot, valtot, s, "late.");
+          for (size_t t = 0; t < dir_idx.size(); ++t)
+            if (!below[t]) {
+              const PSec& x = secs[dir_idx[t]];
+              BST_CUDA(cudaMemcpyAsync(dV + x.v_off, Xv + x.sm_off, sizeof(double) * int64_t(x.N) * x.N,
+                                       cudaMemcpyDeviceToDevice, s));
+            }
+          BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+          BST_CUDA(cudaStreamSynchronize(s));
+        }
+      }
+    }
     if (sp_it.empty()) break;
     // the Ritz pairs the truncation would keep
     double lmax = 0;
