@@ -154,6 +154,7 @@ struct DevGemm {
   int ntiles = 0, nprobs = 0;
   double flops = 0;  // algorithmic 2*M*N*K summed over the problems
   int64_t* w_off = nullptr;  // per problem: offset of its M x N slice in a split-K workspace
+  std::vector<int64_t> hw_off;  // the same offsets on the host
   int64_t wtot = 0;          // sum of M*N
   int maxK = 0;
   // order 0: problem order; 1: tiles of the longest-K problems first
@@ -261,6 +262,9 @@ void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* 
                      cudaStream_t s);
 // the same product with K split into ksplit slices reduced in a fixed order
 // (more CTAs for small, deep products)
+// C[prob] = sum over the ksplit slices of W (slice stride g.wtot, problem
+// offsets g.w_off, each M x N row-major), in slice order, into C's strides
+void launch_ksplit_reduce(Ctx* ctx, const DevGemm& g, const double* W, int ksplit, double* C, cudaStream_t s);
 // ws names the context buffer that holds the K-slice partial products
 void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double* A, const double* B, double* C,
                             cudaStream_t s, const char* ws = "gemm_f64.splitk");

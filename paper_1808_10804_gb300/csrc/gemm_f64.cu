@@ -36,6 +36,7 @@ void DevGemm::upload(const std::vector<GemmProb>& p, int tm, int tn, int order) 
     wtot += int64_t(p[i].M) * p[i].N;
     maxK = std::max(maxK, p[i].K);
   }
+  hw_off.assign(wo.begin(), wo.begin() + nprobs);
   if (order == 1) {
     std::vector<int> idx(ntiles);
     for (int i = 0; i < ntiles; ++i) idx[i] = i;
@@ -209,6 +210,13 @@ void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double
   gemm_f64_reduce_kernel<<<dim3(64, unsigned(g.nprobs)), 256, 0, s>>>(g.probs, W, g.w_off, g.wtot, ksplit, C);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx, 2);
+}
+
+void launch_ksplit_reduce(Ctx* ctx, const DevGemm& g, const double* W, int ksplit, double* C, cudaStream_t s) {
+  if (g.nprobs == 0) return;
+  gemm_f64_reduce_kernel<<<dim3(64, unsigned(g.nprobs)), 256, 0, s>>>(g.probs, W, g.w_off, g.wtot, ksplit, C);
+  BST_CUDA(cudaGetLastError());
+  count_launch(ctx);
 }
 
 void launch_gemm_f64(Ctx* ctx, const DevGemm& g, const double* A, const double* B, double* C, cudaStream_t s) {

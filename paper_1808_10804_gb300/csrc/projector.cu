@@ -154,9 +154,45 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
     if (g.ntiles > 0 && g.ntiles < 304)
       ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 16, 16}));
     launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s, ws);
+    return;
   }
-  else
+  // Mixed: the tcgen05 kernel gives each 128 x 64 output tile to one CTA,
+  // so a small, deep product (the b x b Gram of an M x b block, N Q) keeps
+  // few SMs busy.  Split K (slices of a multiple of 32, at most 8) until
+  // about one tile per SM is in flight: the slices are problems of their
+  // own writing an M x N workspace slice, summed in slice order in FP64.
+  int64_t tiles = 0;
+  int maxK = 0;
+  for (auto& p : probs) {
+    tiles += int64_t((p.M + 127) / 128) * ((p.N + 63) / 64);
+    maxK = std::max(maxK, p.K);
+  }
+  int ks = 1;
+  if (tiles > 0 && tiles < 152) ks = int(std::min<int64_t>({(152 + tiles - 1) / tiles, maxK / 96, 8}));
+  if (ks <= 1) {
     run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s, 0, !same_a);
+    return;
+  }
+  const DevGemm& g = *get_dev_gemm(ctx, tag + "/ksred/" + probs_key(probs), probs);
+  std::vector<GemmProb> sp;
+  for (int sl = 0; sl < ks; ++sl)
+    for (size_t i = 0; i < probs.size(); ++i) {
+      const GemmProb& p = probs[i];
+      const int kc = ((p.K + ks - 1) / ks + 31) / 32 * 32;
+      const int kb = std::min(p.K, sl * kc), ke = std::min(p.K, kb + kc);
+      GemmProb q = p;
+      q.K = ke - kb;
+      q.a_off = p.a_off + int64_t(kb) * p.a_k;
+      q.b_off = p.b_off + int64_t(kb) * p.b_k;
+      q.c_off = int64_t(sl) * g.wtot + g.hw_off[i];
+      q.c_m = p.N;
+      q.c_n = 1;
+      sp.push_back(q);
+    }
+  const std::string wsname = std::string(ws) + ".oz";
+  double* W = (double*)ctx->buf(wsname, sizeof(double) * std::max<int64_t>(1, g.wtot * ks), s);
+  run_gemm_ozaki_probs(ctx, tag + "/ks", sp, A, B, W, s, 0, !same_a);
+  launch_ksplit_reduce(ctx, g, W, ks, C, s);
 }
 
 template <class T>
