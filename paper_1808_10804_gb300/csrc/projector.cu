@@ -587,14 +587,15 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       const int k = std::min(x.c, kc[i] + 4);
       kmax = std::max(kmax, k);
       const int64_t no = x.cs->off;
-      g_ry.push_back(gp(x.M, k, x.N, no, x.N, 1, x.v_off, 1, x.b, x.z_off, k, 1));   // N V[:, :k] -> Z
-      g_rg.push_back(gp(x.N, k, x.M, no, 1, x.N, x.z_off, 1, k, x.q_off, x.b, 1));   // N^T (N V) -> Y
+      // N V[:, :k] = (N Q) W[:, :k]: Z still holds the Rayleigh-Ritz product N Q
+      g_ry.push_back(gp(x.M, k, x.b, x.z_off, x.b, 1, x.sm_off, 1, x.b, x.z_off, k, 1));  // -> Z2
+      g_rg.push_back(gp(x.N, k, x.M, no, 1, x.N, x.z_off, 1, k, x.q_off, x.b, 1));         // N^T (N V) -> Y
       rp.push_back({x.N, k, x.q_off, x.v_off, x.val_off, x.b});
     }
     double worst = 0;
     if (!rp.empty()) {
-      gemm_any(ctx, "ss.ry", rr, g_ry, Nm, dV, Z, s);
-      gemm_any(ctx, "ss.rg", rr, g_rg, Nm, Z, Y, s);
+      gemm_any(ctx, "ss.ry", rr, g_ry, Z, Xv, Z2, s);
+      gemm_any(ctx, "ss.rg", rr, g_rg, Nm, Z2, Y, s);
       ResProb* drp = upload_cached(ctx, "proj.rp", rp, s);
       BST_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * valtot, s));
       ritz_residual<<<dim3(unsigned(rp.size()), unsigned(kmax)), 256, 0, s>>>(drp, Y, dV, lam, res);
