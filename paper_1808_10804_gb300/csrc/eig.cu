@@ -439,20 +439,27 @@ __global__ void __launch_bounds__(512) cholinv_f32(const SmallProb* __restrict__
       }
     }
     __syncthreads();
-    // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i
+    // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i;
+    // a thread takes columns jj and m-1-jj (m+1 rows together, so the
+    // threads are balanced) and every P-th row of them
     if (m > 0) {
-      const int P = nt / m > 0 ? nt / m : 1;
-      const int jj = tid % m, ph = tid / m;
+      const int half = (m + 1) / 2;
+      const int P = nt / half > 0 ? nt / half : 1;
+      const int pj = tid % half, ph = tid / half;
       if (ph < P) {
-        const int j = kb + w + jj;
-        float lj[32];
+        for (int side = 0; side < 2; ++side) {
+          const int jj = side == 0 ? pj : m - 1 - pj;
+          if (side == 1 && jj == pj) break;  // odd m: the middle column once
+          const int j = kb + w + jj;
+          float lj[32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) lj[c] = c < w ? L[j * ld + kb + c] : 0.f;
-        for (int i = j + ph; i < b; i += P) {
-          float acc = 0.f;
+          for (int c = 0; c < 32; ++c) lj[c] = c < w ? L[j * ld + kb + c] : 0.f;
+          for (int i = j + ph; i < b; i += P) {
+            float acc = 0.f;
 #pragma unroll
-          for (int c = 0; c < 32; ++c) acc += L[i * ld + kb + (c < w ? c : 0)] * lj[c];
-          L[i * ld + j] -= acc;
+            for (int c = 0; c < 32; ++c) acc += L[i * ld + kb + (c < w ? c : 0)] * lj[c];
+            L[i * ld + j] -= acc;
+          }
         }
       }
     }
@@ -470,16 +477,20 @@ __global__ void __launch_bounds__(512) cholinv_f32(const SmallProb* __restrict__
     float acc[2][4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = 0.f;
-    for (int k = 0; k < ib; ++k) {
-      const float a0 = L[r0 * ld + k], a1 = L[r1 * ld + k];
+    // k by 32-row segments: in segment g the column groups s <= g take part
+    // (Li[k][j] is zero for k < j, and the rows above block s hold earlier
+    // stashes)
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        // Li[k][j] is zero for k < j; rows above block s are skipped (they
-        // hold earlier stashes)
-        if (s < I && k >= 32 * s) {
-          const float v = Li[k * ld + lane + 32 * s];
-          acc[0][s] = fmaf(a0, v, acc[0][s]);
-          acc[1][s] = fmaf(a1, v, acc[1][s]);
+    for (int g = 0; g < 4; ++g) {
+      if (g < I) {
+        for (int k = 32 * g; k < 32 * g + 32; ++k) {
+          const float a0 = L[r0 * ld + k], a1 = L[r1 * ld + k];
+#pragma unroll
+          for (int s = 0; s <= g; ++s) {
+            const float v = Li[k * ld + lane + 32 * s];
+            acc[0][s] = fmaf(a0, v, acc[0][s]);
+            acc[1][s] = fmaf(a1, v, acc[1][s]);
+          }
         }
       }
     }
