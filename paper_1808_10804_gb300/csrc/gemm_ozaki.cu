@@ -529,6 +529,11 @@ struct OzakiPlan {
   __nv_bfloat16 *SA = nullptr, *SB = nullptr;
   int *eA = nullptr, *eB = nullptr;
   CUtensorMap mapA, mapB;
+  // every problem reads B as it reads A (a Gram matrix X^T X): with the same
+  // pointer for both, B's split is skipped and its tiles come from A's
+  // digits through mapBA
+  bool ab_same = false;
+  CUtensorMap mapBA;
   double flops = 0;
   double split_bytes = 0;  // FP64 read + 5 BF16 digits written per element, exponent per row
   // K == 0 problems (no matched block pair): written as zeros by a separate
@@ -581,9 +586,11 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   std::vector<oz::SplitTask> sa, sb;
   std::vector<GemmProb> zp;
   int maxk = 1;
+  P->ab_same = !probs.empty();
   for (auto& g : probs) {
     BST_REQUIRE(g.K <= 10000, BST_E_UNSUPPORTED, "Ozaki GEMM: K above 10000");
     maxk = std::max(maxk, g.K);
+    P->ab_same = P->ab_same && g.M == g.N && g.a_off == g.b_off && g.a_m == g.b_n && g.a_k == g.b_k;
   }
   P->kpitch = (maxk + oz::kTK - 1) / oz::kTK * oz::kTK;
   for (auto& g : probs) {
@@ -647,6 +654,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   BST_CUDA(cudaMalloc(&P->eB, sizeof(int) * std::max(P->rowsB, 1)));
   P->mapA = make_map(P->SA, P->kpitch, int(ra), oz::kTM);
   P->mapB = make_map(P->SB, P->kpitch, int(rb), oz::kTN);
+  if (P->ab_same) P->mapBA = make_map(P->SA, P->kpitch, int(ra), oz::kTN);
   static bool attr = false;
   if (!attr) {
     BST_CUDA(cudaFuncSetAttribute(oz::ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -664,9 +672,10 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
     count_launch(ctx);
   }
   if (P->ntiles == 0) return;
+  const bool b_from_a = P->ab_same && A == B && split_a;
   {
-    ProfScope ps(ctx, s, "split_bf16", 0.0, P->split_bytes);
-    const int wa = split_a ? P->rowsA : 0, wb = P->rowsB;
+    ProfScope ps(ctx, s, "split_bf16", 0.0, b_from_a ? 0.5 * P->split_bytes : P->split_bytes);
+    const int wa = split_a ? P->rowsA : 0, wb = b_from_a ? 0 : P->rowsB;
     const int ga = (wa + 7) / 8, gb = (wb + 7) / 8;  // 8 rows (warps) per CTA
     if (ga + gb > 0) {
       const oz::SplitJob ja{P->d_sa, P->nsa, P->rowsA, A, P->SA, P->eA};
@@ -678,8 +687,9 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
   const int grid = std::min(P->ntiles, num_sms());
-  oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(P->mapA, P->mapB, P->d_probs, P->d_tiles, P->ntiles,
-                                                                  P->eA, P->eB, P->rowsA, P->rowsB, C, ctx->d_err);
+  oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(
+      P->mapA, b_from_a ? P->mapBA : P->mapB, P->d_probs, P->d_tiles, P->ntiles, P->eA, b_from_a ? P->eA : P->eB,
+      P->rowsA, P->rowsB, C, ctx->d_err);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
 }
