@@ -211,6 +211,7 @@ struct PSec {
   bool direct;     // eigen-decomposition of N^T N without subspace iteration
   int b;           // small problem size
   int64_t q_off, z_off, sm_off, val_off;
+  int64_t kmax;    // most states the truncation can keep from this sector (0: chi)
 };
 
 static void setup_attrs() {
@@ -305,25 +306,30 @@ __global__ void block_sumsq(const double* __restrict__ x, const int64_t* __restr
 // N^T N (block b) and a Rayleigh-Ritz step; small sectors directly.
 // Fills dV (row-major N x c per sector) and hSig; returns false when a
 // sector needs more candidates than the small eigensolver holds.
+// `top_chi`: the truncation keeps exactly the chi largest values (U(1));
+// only then can a sector be skipped by the bound below.
 static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int64_t chi, bst_prec prec, int iters,
-                             double*& dV, std::vector<double>& hSig, cudaStream_t s) {
+                             double*& dV, std::vector<double>& hSig, cudaStream_t s, bool top_chi = true) {
   // The iterations only have to converge the subspace, so they run in the
   // call's arithmetic; the Rayleigh-Ritz stage fixes the individual vectors,
   // whose error is amplified by 1/gap, and always runs in FP64.
   const bst_prec rr = BST_FP64;
   int64_t vtot = 0, qtot = 0, ztot = 0, smtot = 0, valtot = 0;
-  // Block of an iterated sector.  In mixed precision: a sector keeps at
-  // most chi vectors; half as many again (plus 16) set the convergence rate
-  // (sigma_{b+1} / sigma_kept)^2 per iteration; multiples of 32, at most
-  // 160 (the Cholesky and eigensolver costs grow as b^2 and b^3, the
-  // products as b).  In FP64 the full 160: the wider guard band keeps the
-  // vectors at the truncation edge at FP64 accuracy.
-  const int b_it = prec == BST_FP64
-                       ? kEigMax
-                       : int(std::min<int64_t>(kEigMax, std::max<int64_t>(64, (chi + chi / 2 + 16 + 31) / 32 * 32)));
+  // Block of an iterated sector.  In mixed precision: the sector keeps at
+  // most kmax vectors (chi; for SU(2) chi over the multiplet dimension);
+  // half as many again (plus 16) set the convergence rate (sigma_{b+1} /
+  // sigma_kept)^2 per iteration; multiples of 32, 64 to 160 (the Cholesky
+  // and eigensolver costs grow as b^2 and b^3, the products as b).  In
+  // FP64 the full 160: the wider guard band keeps the vectors at the
+  // truncation edge at FP64 accuracy.
+  auto block_of = [&](const PSec& x) {
+    if (prec == BST_FP64) return kEigMax;
+    const int64_t k = x.kmax > 0 ? std::min<int64_t>(x.kmax, chi) : chi;
+    return int(std::min<int64_t>(kEigMax, std::max<int64_t>(64, (k + k / 2 + 16 + 31) / 32 * 32)));
+  };
   for (auto& x : secs) {
     x.direct = x.N <= kEigMax;
-    x.b = x.direct ? x.N : b_it;
+    x.b = x.direct ? x.N : block_of(x);
     x.c = x.b;
     x.v_off = vtot;
     vtot += int64_t(x.N) * x.c;
@@ -456,7 +462,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     dir_key += "," + std::to_string(secs[i].M) + "x" + std::to_string(secs[i].N);
     if (secs[i].direct) dir_idx.push_back(int(i));
   }
-  const bool can_defer = !dir_idx.empty() && !sp_it.empty();
+  const bool can_defer = top_chi && !dir_idx.empty() && !sp_it.empty();
   const bool defer = can_defer && ctx->direct_below_cut.count(dir_key) && ctx->direct_below_cut[dir_key];
   double* dfro = nullptr;
   std::vector<double> hfro(dir_idx.size(), 0.0);
@@ -1077,6 +1083,7 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     x.cs = &m;
     x.M = int(m.rows);
     x.N = int(m.cols);
+    x.kmax = std::max<int64_t>(1, chi_total / (int64_t(m.key) + 1));  // a multiplet of spin J counts 2J+1
     secs.push_back(x);
   }
   BST_REQUIRE(!secs.empty(), BST_E_NUMERIC, "projector: no non-empty sector");
@@ -1090,7 +1097,9 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     bool done = false;
     if (use_subspace) {
       ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
-      done = factors_subspace(ctx, Nm, secs, chi_total, prec, ctx->proj_iters, dV, hSig, s);
+      // whole multiplets are kept while they fit, so a value below the
+      // chi-th largest may still be kept: no sector is skipped
+      done = factors_subspace(ctx, Nm, secs, chi_total, prec, ctx->proj_iters, dV, hSig, s, false);
     }
     if (!done) factors_gesvd(ctx, Nm, ntot, secs, dV, hSig, s);
     if (attempt == 0) {
