@@ -229,6 +229,10 @@ struct Ctx {
   // hint only: such sectors are then deferred and, if still provably
   // below the cut, skipped)
   std::map<std::string, bool> direct_below_cut;
+  // projector: per sector structure, whether the last mixed-precision call
+  // needed more than one subspace round (its intermediate Rayleigh-Ritz
+  // steps then run in the mixed arithmetic)
+  std::map<std::string, bool> multi_round;
   ~Ctx();
   void* buf(const std::string& name, size_t bytes, cudaStream_t s) { return bufs[name].get(bytes, s); }
 };

@@ -498,19 +498,28 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     BST_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     forked = true;
   }
+  // Rounds that only decide whether to iterate on (and restart from Ritz
+  // vectors) do not need FP64 vectors: when the last mixed-precision call
+  // with this sector structure needed several rounds, Rayleigh-Ritz runs in
+  // the call's arithmetic until the residual test passes, and one more
+  // round without iterations (re-orthonormalised block, FP64 Rayleigh-Ritz)
+  // gives the vectors and must pass the test again.
+  const std::string rr_key = dir_key + "/rounds";
+  bool mixed_rr = prec != BST_FP64 && ctx->multi_round.count(rr_key) && ctx->multi_round[rr_key];
   int total = 0, steps = iters;
   for (int round = 0;; ++round) {
+    const bst_prec rrp = mixed_rr ? prec : rr;
     if (!sp_it.empty()) {
       iterate(steps);
       total += steps;
       orthonormalise();
       // Rayleigh-Ritz: H = (N Q)^T (N Q)
-      gemm_any(ctx, "ss.zrr", rr, g_z, Nm, Q, Z, s);
-      gemm_any(ctx, "ss.h", rr, g_h, Z, Z, Msm, s);
+      gemm_any(ctx, "ss.zrr", rrp, g_z, Nm, Q, Z, s);
+      gemm_any(ctx, "ss.h", rrp, g_h, Z, Z, Msm, s);
     }
-    small_eig(ctx, rr, sp_it, Msm, Xv, lam, smtot, valtot, s);
+    small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s);
     // V = Q W (iterative) or W (direct, once the second stream is joined)
-    if (!g_v.empty()) gemm_any(ctx, "ss.v", rr, g_v, Q, Xv, dV, s);
+    if (!g_v.empty()) gemm_any(ctx, "ss.v", rrp, g_v, Q, Xv, dV, s);
     if (forked) {
       BST_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
       forked = false;
@@ -600,8 +609,8 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     }
     double worst = 0;
     if (!rp.empty()) {
-      gemm_any(ctx, "ss.ry", rr, g_ry, Z, Xv, Z2, s);
-      gemm_any(ctx, "ss.rg", rr, g_rg, Nm, Z2, Y, s);
+      gemm_any(ctx, "ss.ry", rrp, g_ry, Z, Xv, Z2, s);
+      gemm_any(ctx, "ss.rg", rrp, g_rg, Nm, Z2, Y, s);
       ResProb* drp = upload_cached(ctx, "proj.rp", rp, s);
       BST_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * valtot, s));
       ritz_residual<<<dim3(unsigned(rp.size()), unsigned(kmax)), 256, 0, s>>>(drp, Y, dV, lam, res);
@@ -619,20 +628,26 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                worst);
       ctx->tune_log += line;
     }
-    if (worst <= tol) break;
-    if (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol) break;
-    if (total >= max_total) return false;
+    const bool ok = worst <= tol || (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol);
+    if (ok && !mixed_rr) break;
+    if (total >= max_total) {
+      ctx->multi_round[rr_key] = true;
+      return false;
+    }
     // length of the next round: from the second round on, extrapolate the
     // residual's geometric decay per step to half the tolerance (at least
     // `iters`, at most 6 * iters steps), so slowly converging sectors are
     // checked with few Rayleigh-Ritz rounds
     int next = iters;
-    if (round > 0 && worst > 0 && prev_worst > worst) {
+    if (ok) {
+      mixed_rr = false;  // converged under mixed Rayleigh-Ritz: the FP64 round
+      next = 0;
+    } else if (round > 0 && steps > 0 && worst > 0 && prev_worst > worst) {
       const double rho = std::pow(worst / prev_worst, 1.0 / steps);
       const double need = std::log(0.5 * tol / worst) / std::log(rho);
       if (std::isfinite(need)) next = int(std::min<double>(6.0 * iters, std::max<double>(iters, std::ceil(need))));
     }
-    steps = std::min(next, std::max(1, max_total - total));
+    steps = next == 0 ? 0 : std::min(next, std::max(1, max_total - total));
     prev_worst = worst;
     // resume from the Ritz vectors
     for (auto& x : secs)
@@ -640,6 +655,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
         BST_CUDA(cudaMemcpyAsync(Q + x.q_off, dV + x.v_off, sizeof(double) * int64_t(x.N) * x.b,
                                  cudaMemcpyDeviceToDevice, s));
   }
+  if (prec != BST_FP64) ctx->multi_round[rr_key] = total > iters;
   hSig.assign(valtot, 0.0);
   for (auto& x : secs) {
     x.s_off = x.val_off;
