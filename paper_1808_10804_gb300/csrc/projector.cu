@@ -506,6 +506,8 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   // gives the vectors and must pass the test again.
   const std::string rr_key = dir_key + "/rounds";
   bool mixed_rr = prec != BST_FP64 && ctx->multi_round.count(rr_key) && ctx->multi_round[rr_key];
+  if (mixed_rr && ctx->tune_log.size() < (1u << 20))
+    ctx->tune_log += "projector subspace: intermediate Rayleigh-Ritz rounds in mixed arithmetic\n";
   int total = 0, steps = iters;
   for (int round = 0;; ++round) {
     const bst_prec rrp = mixed_rr ? prec : rr;
