@@ -802,6 +802,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   // more candidates than were computed: the projector is redone with the
   // full FP64 SVD.
   bool use_subspace = ctx->proj_method == 1;
+  bool from_subspace = false;  // the candidates come from factors_subspace
   for (int attempt = 0; attempt < 2; ++attempt) {
     bool done = false;
     if (use_subspace) {
@@ -809,6 +810,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
       done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
     }
     if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
+    from_subspace = done;
     if (attempt == 0) {
       double nss = 0;
       BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
@@ -843,6 +845,26 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
         }
         BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
         count_launch(ctx, int(secs.size()));
+        if (done) {
+          // the Rayleigh-Ritz vectors W of the iterated sectors follow V
+          // (V = Q W), so that N V = (N Q) W column by column below
+          int64_t wtot = 0;
+          for (auto& x : secs) wtot = std::max(wtot, x.sm_off + int64_t(x.b) * x.b);
+          double* Xv = (double*)ctx->buf("proj.X2", sizeof(double), s);
+          double* tmpw = (double*)ctx->buf("proj.Wperm", sizeof(double) * std::max<int64_t>(wtot, 1), s);
+          po = 0;
+          int nw = 0;
+          for (auto& x : secs) {
+            if (!x.direct) {
+              permute_cols<<<x.b, 128, 0, s>>>(Xv + x.sm_off, tmpw + x.sm_off, x.c, dperm + po);
+              BST_CUDA(cudaMemcpyAsync(Xv + x.sm_off, tmpw + x.sm_off, sizeof(double) * int64_t(x.b) * x.b,
+                                       cudaMemcpyDeviceToDevice, s));
+              ++nw;
+            }
+            po += x.c;
+          }
+          count_launch(ctx, nw);
+        }
       }
     }
 
@@ -937,15 +959,23 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   double* Ptm = (double*)ctx->buf("proj.Ptm", sizeof(double) * std::max<int64_t>(vpt->mv.total, 1), s);
   BST_CUDA(cudaMemsetAsync(Pm, 0, sizeof(double) * std::max<int64_t>(vp->mv.total, 1), s));
   BST_CUDA(cudaMemsetAsync(Ptm, 0, sizeof(double) * std::max<int64_t>(vpt->mv.total, 1), s));
-  std::vector<GemmProb> gu, gpp, gpt;
+  std::vector<GemmProb> gu, guz, gpp, gpt;
   for (size_t i = 0; i < secs.size(); ++i) {
     const int k = kcount[i];
     if (k == 0) continue;
     const PSec& x = secs[i];
-    // Ur = N V_k  ([M x k]; V row-major N x c)
-    gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
+    // Ur = N V_k  ([M x k]; V row-major N x c), in FP64 (see
+    // factors_subspace); for an iterated sector N V = (N Q) W with N Q the
+    // final Rayleigh-Ritz product, still in its buffer: M x k x b in place
+    // of M x k x N
+    if (from_subspace && !x.direct)
+      guz.push_back(gp(x.M, k, x.b, x.z_off, x.b, 1, x.sm_off, 1, x.b, ur_off[i], k, 1));
+    else
+      gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
   }
-  gemm_any(ctx, "proj.u", BST_FP64, gu, Nm, dV, Ur, s);  // left vectors in FP64 (see factors_subspace)
+  gemm_any(ctx, "proj.u", BST_FP64, gu, Nm, dV, Ur, s);
+  gemm_any(ctx, "proj.uz", BST_FP64, guz, (const double*)ctx->buf("proj.Z", sizeof(double), s),
+           (const double*)ctx->buf("proj.X2", sizeof(double), s), Ur, s);
   int64_t uo = 0, vo = 0;
   for (size_t i = 0; i < secs.size(); ++i) {
     const PSec& x = secs[i];
