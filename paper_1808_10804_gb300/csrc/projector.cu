@@ -141,6 +141,26 @@ static std::string probs_key(const std::vector<GemmProb>& probs) {
 }
 
 // FP64-accurate grouped GEMM in the requested arithmetic.
+// Number of K slices for `tiles` output tiles: at least enough CTAs to put
+// `per_sm` on every SM, at most `kmax` slices; among those the count with
+// the shortest busiest SM, ceil(tiles * ks / SMs) CTAs of 1/ks of K each,
+// fewer slices on ties.
+static int k_slices(int64_t tiles, int kmax, int per_sm) {
+  const int64_t sms = 152;
+  if (tiles <= 0 || kmax <= 1) return 1;
+  const int kmin = int(std::max<int64_t>(1, std::min<int64_t>(kmax, (sms * per_sm + tiles - 1) / tiles)));
+  int best = kmin;
+  double best_t = 1e300;
+  for (int ks = kmin; ks <= kmax; ++ks) {
+    const double t = double((tiles * ks + sms - 1) / sms) / ks;
+    if (t < best_t - 1e-12) {
+      best_t = t;
+      best = ks;
+    }
+  }
+  return best;
+}
+
 static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std::vector<GemmProb>& probs,
                      const double* A, const double* B, double* C, cudaStream_t s, bool same_a = false,
                      const char* ws = "gemm_f64.splitk") {
@@ -151,8 +171,7 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
     // 16 deep) until about two CTAs per SM are busy
     const DevGemm& g = *get_dev_gemm(ctx, tag + "/" + probs_key(probs), probs);
     int ksplit = 1;
-    if (g.ntiles > 0 && g.ntiles < 304)
-      ksplit = std::max(1, std::min({(304 + g.ntiles - 1) / g.ntiles, g.maxK / 16, 16}));
+    if (g.ntiles > 0 && g.ntiles < 304) ksplit = k_slices(g.ntiles, std::min(g.maxK / 16, 16), 2);
     launch_gemm_f64_splitk(ctx, g, ksplit, A, B, C, s, ws);
     return;
   }
@@ -168,7 +187,7 @@ static void gemm_any(Ctx* ctx, const std::string& tag, bst_prec prec, const std:
     maxK = std::max(maxK, p.K);
   }
   int ks = 1;
-  if (tiles > 0 && tiles < 152) ks = int(std::min<int64_t>({(152 + tiles - 1) / tiles, maxK / 96, 8}));
+  if (tiles > 0 && tiles < 152) ks = k_slices(tiles, std::min(maxK / 96, 8), 1);
   if (ks <= 1) {
     run_gemm_ozaki_probs(ctx, tag, probs, A, B, C, s, 0, !same_a);
     return;
