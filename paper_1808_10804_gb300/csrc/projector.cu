@@ -242,10 +242,13 @@ static void setup_attrs() {
 }
 
 // Symmetric eigenproblems (b <= 160) in FP64 accuracy.  An FP32 Jacobi
-// pass diagonalises H to FP32 level; H is rotated into that basis in FP64
+// pass diagonalises H to FP32 level (off-diagonals tested absolutely, in
+// units of the largest diagonal entry; pairs of values both below 1e-5 of
+// it left to the next pass); H is rotated into that basis in FP64
 // (H1 = X1^T H X1, nearly diagonal) and a second FP32 Jacobi pass resolves
-// it to high relative accuracy; two Ogita-Aishima steps then bring the
-// vectors and values to FP64 accuracy.  Values below 1e-6 of the largest
+// it to high relative accuracy (tested relative to the diagonal, floor
+// 1e-5); two Ogita-Aishima steps then bring the vectors and values to FP64
+// accuracy.  Values below 1e-6 of the largest
 // are treated as one unresolved cluster.  `pre` prefixes every workspace,
 // plan and table name, so calls with different prefixes may run on
 // different streams at the same time.
@@ -279,7 +282,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   for (auto& p : sp) jac_flops += 7.0 * double(p.b) * p.b * 18.0 * p.b / 2.0;
   {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f /*P1*/);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
@@ -287,7 +290,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   gemm_any(ctx, pre + "oa.s", prec, g_s, X1, T, H1, s, false, ws);
   {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f /*P2*/);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
