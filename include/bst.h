@@ -113,17 +113,30 @@ BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
 BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
 /* Eigensolver behind bst_svd_projector and bst_ctm_move.
  *   BST_PROJ_SUBSPACE (default): per sector of N, subspace iteration on
- *     N^T N with a block of 160 vectors (CholQR orthonormalisation), in
- *     rounds (the first two of `iters` steps, later ones sized by the
- *     residual's observed decay), each closed by a Rayleigh-Ritz step in FP64
- *     (FP32 Jacobi eigensolver refined by Ogita-Aishima steps); sectors of
- *     dimension <= 160 are decomposed directly.  A round is accepted when
- *     every Ritz pair the truncation keeps has a residual
- *     ||N^T N v - lambda v|| <= tol * lambda_max (tol 3e-14 for BST_FP64,
- *     4e-12 for BST_OZAKI, whose iterations run on the tensor cores), or
- *     when the residual has stopped falling within 100 tol.  Falls back to
- *     BST_PROJ_GESVD after 480 steps, or when the truncation keeps states
- *     within 16 of a sector's block edge.
+ *     N^T N with a block of b vectors (CholQR orthonormalisation; b = 160
+ *     for BST_FP64, for BST_OZAKI k + k/2 + 16 rounded up to 32 in 64..160,
+ *     k the most states the sector can hold: chi, or chi / (2J+1) for an
+ *     SU(2) sector of spin J), in rounds (the first two of `iters` steps,
+ *     later ones sized by the residual's observed decay), each closed by a
+ *     Rayleigh-Ritz step in FP64 (FP32 Jacobi eigensolver refined by
+ *     Ogita-Aishima steps); sectors of dimension <= 160 are decomposed
+ *     directly.  A round is accepted when every Ritz pair the truncation
+ *     keeps has a residual ||N^T N v - lambda v|| <= tol * lambda_max (tol
+ *     3e-14 for BST_FP64, 4e-12 for BST_OZAKI, whose iterations run on the
+ *     tensor cores), or when the residual has stopped falling within
+ *     100 tol.  Falls back to BST_PROJ_GESVD after 480 steps, or when the
+ *     truncation keeps states within 16 of a sector's block edge.
+ *     The context remembers, per sector structure, what earlier calls found
+ *     and schedules later ones by it; the kept states and the residual test
+ *     are unaffected, the rounding of the result may differ from a first
+ *     call's (same context and call sequence: same bits):
+ *       - U(1): directly decomposed sectors all below the truncation cut
+ *         last time (Frobenius norm under the chi-th largest Ritz value)
+ *         are checked again after the first Rayleigh-Ritz step and then not
+ *         decomposed (they hold no kept state);
+ *       - BST_OZAKI: when the last call needed several rounds, the
+ *         intermediate Rayleigh-Ritz steps run in the mixed arithmetic and
+ *         one more round without iterations repeats it in FP64.
  *   BST_PROJ_GESVD: full FP64 SVD of every sector with cuSOLVER gesvd. */
 typedef enum { BST_PROJ_GESVD = 0, BST_PROJ_SUBSPACE = 1 } bst_proj_method;
 BST_API bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters);
