@@ -38,11 +38,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   const int ld = bp + 1;
   float* A = sh;
   float* V = A + bp * ld;
-  float* cs = V + bp * ld;      // cos per pair
-  float* sn = cs + bp / 2;      // sin per pair
-  int* pp = (int*)(sn + bp / 2);
-  int* qq = pp + bp / 2;
-  float* red = (float*)(qq + bp / 2);
+  // per pair: cos, sin and the two indices (as int bits), read with one
+  // 16-byte load (offset 2 bp (bp+1) floats: a multiple of 16 bytes)
+  float4* prm = reinterpret_cast<float4*>(V + bp * ld);
+  float* red = reinterpret_cast<float*>(prm + bp / 2);
   int* order = (int*)(red + 1024);
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* H = in + pr.in_off;
@@ -118,8 +117,6 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
           p = q;
           q = x;
         }
-        pp[k] = p;
-        qq[k] = q;
         const float apq = A[p * ld + q];
         float c = 1.f, s = 0.f;
         const float dd = fmaxf(fabsf(A[p * ld + p]), kTau) * fmaxf(fabsf(A[q * ld + q]), kTau);
@@ -130,8 +127,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
           c = rsqrtf(1.f + t * t);
           s = t * c;
         }
-        cs[k] = c;
-        sn[k] = s;
+        prm[k] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
       }
       __syncthreads();
       // rows: A <- J^T A; thread (column j, pair group g) applies the
@@ -141,9 +137,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
       if (grp < G) {
         const int j = jcol;
         for (int k = grp; k < npair; k += G) {
-          const float c = cs[k], s = sn[k];
+          const float4 pr = prm[k];
+          const float c = pr.x, s = pr.y;
           if (s == 0.f) continue;
-          const int p = pp[k], q = qq[k];
+          const int p = __float_as_int(pr.z), q = __float_as_int(pr.w);
           const float ap = A[p * ld + j], aq = A[q * ld + j];
           A[p * ld + j] = c * ap - s * aq;
           A[q * ld + j] = s * ap + c * aq;
@@ -154,9 +151,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
       if (grp < G) {
         const int i = jcol;
         for (int k = grp; k < npair; k += G) {
-          const float c = cs[k], s = sn[k];
+          const float4 pr = prm[k];
+          const float c = pr.x, s = pr.y;
           if (s == 0.f) continue;
-          const int p = pp[k], q = qq[k];
+          const int p = __float_as_int(pr.z), q = __float_as_int(pr.w);
           const float ap = A[i * ld + p], aq = A[i * ld + q];
           A[i * ld + p] = c * ap - s * aq;
           A[i * ld + q] = s * ap + c * aq;
