@@ -633,8 +633,11 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     }
     double worst = 0;
     if (!rp.empty()) {
-      gemm_any(ctx, "ss.ry", rrp, g_ry, Z, Xv, Z2, s);
-      gemm_any(ctx, "ss.rg", rrp, g_rg, Nm, Z2, Y, s);
+      // the residual only decides convergence: the call's arithmetic
+      // suffices (the mixed products' error, ~1e-13 of ||N||^2, is far
+      // below the 4e-12 tolerance)
+      gemm_any(ctx, "ss.ry", prec, g_ry, Z, Xv, Z2, s);
+      gemm_any(ctx, "ss.rg", prec, g_rg, Nm, Z2, Y, s);
       ResProb* drp = upload_cached(ctx, "proj.rp", rp, s);
       BST_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * valtot, s));
       ritz_residual<<<dim3(unsigned(rp.size()), unsigned(kmax)), 256, 0, s>>>(drp, Y, dV, lam, res);
