@@ -574,6 +574,9 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
         below[t] = cut > 0 && hfro[t] < 0.99 * cut;
         all_below = all_below && below[t];
       }
+      // the hints are per sector structure: keep the maps bounded over long
+      // runs whose structure keeps changing
+      if (ctx->direct_below_cut.size() >= 4096) ctx->direct_below_cut.clear();
       ctx->direct_below_cut[dir_key] = all_below;
       if (defer) {
         std::vector<GemmProb> g_rel;
@@ -658,6 +661,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     const bool ok = worst <= tol || (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol);
     if (ok && !mixed_rr) break;
     if (total >= max_total) {
+      if (ctx->multi_round.size() >= 4096) ctx->multi_round.clear();
       ctx->multi_round[rr_key] = true;
       return false;
     }
@@ -682,7 +686,10 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
         BST_CUDA(cudaMemcpyAsync(Q + x.q_off, dV + x.v_off, sizeof(double) * int64_t(x.N) * x.b,
                                  cudaMemcpyDeviceToDevice, s));
   }
-  if (prec != BST_FP64) ctx->multi_round[rr_key] = total > iters;
+  if (prec != BST_FP64) {
+    if (ctx->multi_round.size() >= 4096) ctx->multi_round.clear();
+    ctx->multi_round[rr_key] = total > iters;
+  }
   hSig.assign(valtot, 0.0);
   for (auto& x : secs) {
     x.s_off = x.val_off;
