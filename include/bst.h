@@ -111,6 +111,15 @@ BST_API const char* bst_last_error(void);
 BST_API bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream);
 /* Number of kernels this context launched so far (all calls). */
 BST_API int64_t bst_ctx_launch_count(bst_ctx ctx);
+/* Algorithmic work issued so far by this context's contractions, in
+ * FP64-equivalent flops: 2 M N K summed over the matched block pairs of
+ * every contraction (Sec. 2: the block products a symmetric contraction
+ * consists of; U(1) sector GEMMs, SU(2) reduced pair products, batched
+ * contractions) and over the projector's P and Pt products, enumerated
+ * from the cached plans whatever the arithmetic.  The projector's own
+ * eigensolver work (subspace iterations, Rayleigh-Ritz, refinement) is not
+ * counted.  0 for a NULL context. */
+BST_API double bst_ctx_work_flops(bst_ctx ctx);
 /* Eigensolver behind bst_svd_projector and bst_ctm_move.
  *   BST_PROJ_SUBSPACE (default): per sector of N, subspace iteration on
  *     N^T N with a block of b vectors (CholQR orthonormalisation; b = 160
@@ -242,17 +251,18 @@ BST_API bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a,
                         bst_prec prec, double alpha, double beta,
                         bst_layout C, double* c, bst_stream stream);
 
-/* bst_contract for callers that cannot allocate device memory, e.g. code
- * that runs while a stream is being captured into a CUDA graph, or a process
- * whose device memory is owned and pre-sized by another runtime.  The paper
- * has no counterpart: this is a packaging of the same contraction.
+/* bst_contract for callers that cannot allocate device memory: a process
+ * whose device memory is owned and pre-sized by another runtime (a
+ * framework's caching allocator, a fixed-budget serving process), where a
+ * cudaMalloc would fail or would synchronise the device at the wrong moment.
+ * The paper has no counterpart: this is a packaging of the same contraction.
  *
  * Same arguments and result as bst_contract with prec = BST_FP64, but the
  * call allocates nothing: its intermediates (relayout and GEMM tables, the
  * three sector matrices) live in one static device array of 64 MiB that the
  * library module carries, which every GPU that loads the library holds until
  * the process exits.  Runs on the current CUDA device.  The first call on a
- * device looks up that array's device address (once per device); make the
+ * device (per CUDA context) looks up that array's device address; make that
  * first call before any stream capture begins.  A contraction whose tables
  * and sector matrices need more than 64 MiB fails with BST_E_SHAPE.  All
  * calls share the array, so calls that overlap on the GPU (different streams
@@ -327,10 +337,15 @@ BST_API bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double*
 /* Batched dense symmetric eigendecomposition used by the projector: batch
  * row-major n x n symmetric matrices H (device, back to back, n <= 160) ->
  * eigenvectors X (device, same layout, column j = eigenvector j) and
- * eigenvalues lam (device, n per matrix, descending).  FP32 Jacobi followed
- * by three Ogita-Aishima refinement steps whose matrix products run in
- * `prec`.  No counterpart in the paper (a building block of the SVD it
- * uses). */
+ * eigenvalues lam (device, n per matrix, descending).  Two FP32 Jacobi
+ * passes followed by two Ogita-Aishima refinement steps whose matrix
+ * products run in `prec`.  Accuracy: eigenvalues above 1e-6 lambda_max (and
+ * their eigenvectors, where separated) reach FP64 accuracy (BST_FP64) or
+ * ~1e-12 lambda_max (BST_OZAKI); eigenvalues below 1e-6 lambda_max form one
+ * cluster the FP32 stage does not resolve and are accurate only to about
+ * 1e-9 lambda_max in absolute terms, with their eigenvectors spanning that
+ * cluster's subspace.  No counterpart in the paper (a building block of the
+ * SVD it uses). */
 BST_API bst_status bst_sym_eig(bst_ctx ctx, int32_t n, int32_t batch, const double* H, double* X,
                                double* lam, bst_prec prec, bst_stream stream);
 

@@ -69,6 +69,7 @@ def lib():
         "bst_ctx_destroy": [vp],
         "bst_ctx_sync": [vp, vp],
         "bst_ctx_launch_count": [vp],
+        "bst_ctx_work_flops": [vp],
         "bst_ctx_profile": [vp, i32],
         "bst_ctx_set_projector": [vp, i32, i32],
         "bst_ctx_set_autotune": [vp, i32],
@@ -101,6 +102,7 @@ def lib():
         fn.argtypes = args
         fn.restype = C.c_int
     L.bst_ctx_launch_count.restype = C.c_int64
+    L.bst_ctx_work_flops.restype = C.c_double
     L.bst_last_error.restype = C.c_char_p
     L.bst_last_error.argtypes = []
     _lib = L
@@ -235,6 +237,11 @@ class Context:
     @property
     def launches(self):
         return lib().bst_ctx_launch_count(self.h)
+
+    @property
+    def work_flops(self):
+        """Algorithmic flops of the method's contractions issued so far."""
+        return lib().bst_ctx_work_flops(self.h)
 
     def set_projector(self, method="subspace", iters=9):
         m = {"gesvd": 0, "subspace": 1}[method]

@@ -145,6 +145,8 @@ bst_status bst_ctx_sync(bst_ctx ctx, bst_stream stream) {
 
 int64_t bst_ctx_launch_count(bst_ctx ctx) { return ctx ? C_(ctx)->launches.load() : 0; }
 
+double bst_ctx_work_flops(bst_ctx ctx) { return ctx ? C_(ctx)->work_flops : 0.0; }
+
 bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters) {
   return guarded([&] {
     BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");

@@ -282,6 +282,7 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
   const std::string tag = "batch/" + std::to_string(uintptr_t(bp));
   if (ctx->autotune) autotune(ctx, bp, bases, n, prec, tag, s);
   double *Am = bp->Am, *Bm = bp->Bm, *Cm = bp->Cm;
+  ctx->work_flops += bp->g.flops;
   launch_rel(ctx, bp->ra, bases, Am, 0, 1.0, 0.0, s);
   launch_rel(ctx, bp->rb, bases + n, Bm, 0, 1.0, 0.0, s);
   if (prec == BST_FP64) {

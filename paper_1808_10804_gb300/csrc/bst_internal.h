@@ -214,6 +214,14 @@ struct Ctx {
   std::map<uint64_t, DevBuf> su2_weights;  // SU(2) layout id -> per-element 2J+1 (norms)
   int* d_err = nullptr;                     // device error word
   std::atomic<int64_t> launches{0};
+  // algorithmic work of the method's contractions issued so far: 2 M N K
+  // over the matched block pairs of every contraction (U(1) sector GEMMs,
+  // SU(2) pair products, batched contractions) and of the projector's
+  // P = Rb V S^-1/2 and Pt = S^-1/2 U^T Rt^T products; the projector's own
+  // iterations (subspace products, Rayleigh-Ritz, refinement) are not
+  // counted.  Enumerated from the plans, FP64-equivalent whatever the
+  // arithmetic.
+  double work_flops = 0;
   void* cusolver = nullptr;
   int proj_method = 1;   // 0: cuSOLVER gesvd per sector, 1: subspace iteration + small eigensolver
   int proj_iters = 9;    // subspace iterations

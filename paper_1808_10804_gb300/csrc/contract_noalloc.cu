@@ -1,19 +1,22 @@
 // bst_contract_noalloc: the FP64 block-sparse contraction without any device
 // allocation.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured into a graph, hosts whose device memory is owned and
-// pre-sized by another runtime (a framework's caching allocator, a
-// fixed-budget serving process), or contexts whose allocation would
+// Some callers cannot call cudaMalloc: hosts whose device memory is owned
+// and pre-sized by another runtime (a framework's caching allocator, a
+// fixed-budget serving process), or code for which an allocation would
 // synchronise the device at the wrong moment.  This entry point serves them:
 // the caller passes inputs and the output, and every intermediate (the
 // relayout task tables, the GEMM problem and tile tables and the three sector
 // matrices) lives in one file-scope device array of kScratchBytes.  That array
 // is part of the loaded module, so every GPU that loads the library holds it
 // until the process exits.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "bst_internal.h"
 
@@ -23,24 +26,43 @@ namespace bst {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// The CUDA context current on this thread (driver entry point, looked up
+// once through the runtime).
+static CUcontext current_context() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  static GetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    BST_CUDA(cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q));
+    BST_REQUIRE(p && q == cudaDriverEntryPointSuccess, BST_E_CUDA, "cuCtxGetCurrent unavailable");
+    fn = (GetCurrentFn)p;
+  }
+  CUcontext c = nullptr;
+  BST_REQUIRE(fn(&c) == CUDA_SUCCESS, BST_E_CUDA, "cuCtxGetCurrent failed");
+  return c;
+}
+
 // Device address of the scratch array for the current device.  The host-side
 // symbol is only a stand-in for the array: its address has to be looked up,
 // with the device current, before a kernel may be given it.  Looked up once
-// per device (the first call on a device does it; make that first call before
-// any stream capture begins).
+// per device and CUDA context (the first call on a device does it; make that
+// first call before any stream capture begins): a reset device or a
+// recreated primary context reloads the module, so an address is never
+// reused across contexts.
 static void* noalloc_scratch_ptr(int device) {
   static std::mutex mu;
-  static void* ptr[128] = {nullptr};
-  BST_REQUIRE(device >= 0 && device < 128, BST_E_ARG, "device index out of range");
+  static std::map<std::pair<int, CUcontext>, void*> ptr;
+  const CUcontext cur = current_context();
   std::lock_guard<std::mutex> g(mu);
-  if (!ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    BST_REQUIRE(e == cudaSuccess && p != nullptr, BST_E_CUDA,
-                std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") + cudaGetErrorString(e));
-    ptr[device] = p;
-  }
-  return ptr[device];
+  auto it = ptr.find({device, cur});
+  if (it != ptr.end()) return it->second;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  BST_REQUIRE(e == cudaSuccess && p != nullptr, BST_E_CUDA,
+              std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") + cudaGetErrorString(e));
+  ptr[{device, cur}] = p;
+  return p;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

@@ -202,6 +202,7 @@ void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, b
   double* Bm = (double*)ctx->buf("contract.B", sizeof(double) * std::max<int64_t>(p->bmat, 1), s);
   double* Cm = (double*)ctx->buf(cmat_out ? "contract.Ckeep" : "contract.C",
                                  sizeof(double) * std::max<int64_t>(p->cmat, 1), s);
+  ctx->work_flops += p->g.flops;
   launch_relayout(ctx, p->ra, a, Am, 0, 1.0, 0.0, s);
   launch_relayout(ctx, p->rb, b, Bm, 0, 1.0, 0.0, s);
   if (prec == BST_FP64) {

@@ -1029,6 +1029,8 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     uo += int64_t(x.M) * k;
     vo += int64_t(x.N) * k;
   }
+  for (auto* v : {&gpp, &gpt})
+    for (auto& g : *v) ctx->work_flops += 2.0 * double(g.M) * g.N * g.K;
   gemm_any(ctx, "proj.P", prec, gpp, Bt, Vs, Pm, s);
   gemm_any(ctx, "proj.Pt", prec, gpt, Us, At, Ptm, s);
   launch_relayout(ctx, vp->rel, p, Pm, 1, 1.0, 0.0, s);

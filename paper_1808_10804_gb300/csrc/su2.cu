@@ -695,6 +695,7 @@ void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double*
   if (C->nnz == 0) return;
   launch_relayout(ctx, p->ra, a, p->Am, 0, 1.0, 0.0, s);
   launch_relayout(ctx, p->rb, b, p->Bm, 0, 1.0, 0.0, s);
+  ctx->work_flops += p->g.flops;
   if (!p->probs.empty()) {
     if (prec == BST_FP64) {
       launch_gemm_f64(ctx, p->g, p->Am, p->Bm, p->P, s);

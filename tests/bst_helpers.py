@@ -47,3 +47,32 @@ def rel_err(x, ref):
     x = np.asarray(x, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def block_errors(legs, got, want):
+    """Per-block errors of a flat block-sparse array against the reference
+    (both in the canonical layout of `legs`): list of (||d_b||, ||ref_b||)
+    in block order, with the blocks enumerated by the oracle's layout."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    out, pos = [], 0
+    for b in u1.blocks(legs):
+        n = int(np.prod(u1.block_shape(legs, b)))
+        d = got[pos:pos + n] - want[pos:pos + n]
+        out.append((float(np.linalg.norm(d)), float(np.linalg.norm(want[pos:pos + n]))))
+        pos += n
+    assert pos == want.size
+    return out
+
+
+def check_blocks(legs, got, want, tol, own_tol, floor=1e-3):
+    """Every block: its error relative to the tensor norm below tol, and
+    relative to its own norm (floored at `floor` times the tensor norm)
+    below own_tol.  Returns the worst of each ratio."""
+    tn = max(float(np.linalg.norm(want)), 1e-300)
+    worst_t = worst_o = 0.0
+    for i, (e, n) in enumerate(block_errors(legs, got, want)):
+        rt, ro = e / tn, e / max(n, floor * tn)
+        worst_t, worst_o = max(worst_t, rt), max(worst_o, ro)
+        assert rt < tol and ro < own_tol, (i, rt, ro, n / tn)
+    return worst_t, worst_o

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 from oracle import ctm as octm  # noqa: E402
 from oracle import u1  # noqa: E402
 from workloads import u1_config, values  # noqa: E402
-from bst_helpers import gpu_network, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
+from bst_helpers import check_blocks, gpu_network, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
 
 TOL64 = 1e-12
 
@@ -228,12 +228,22 @@ def gpu_env(bst, ctx, name, chi_cap):
     return cfg, aL, ad, bst.Env(ctx, Ls, data, caps)
 
 
+# per-block bound: a block's error against its own norm (floored at 1e-3 of
+# the tensor norm) within OWN_FACTOR times the tensor tolerance
+OWN_FACTOR = 100.0
+
+
 def compare_env(env, net, roles, tol):
+    """Bit-exact legs; Frobenius error of every renewed tensor below tol;
+    every block's error below tol relative to the tensor norm and below
+    OWN_FACTOR * tol relative to its own norm (floor 1e-3 of the tensor)."""
     errs = {}
     for r in roles:
         legs, dense = net[r]
         assert [to_oracle_leg(l) for l in env.L[r].legs] == legs, r
-        errs[r] = rel_err(env.data(r).cpu().numpy(), u1.from_dense(legs, dense))
+        got, want = env.data(r).cpu().numpy(), u1.from_dense(legs, dense)
+        errs[r] = rel_err(got, want)
+        check_blocks(legs, got, want, tol, OWN_FACTOR * tol)
     assert max(errs.values()) < tol, errs
     return errs
 
@@ -347,3 +357,40 @@ def test_contract_many_tiles_with_empty_sectors(bst, ctx, prec, tol):
     got = cd.cpu().numpy()
     assert rel_err(got, ref) <= tol
     assert np.all(got[ref == 0] == 0)
+
+
+def matched_pair_flops(a_legs, la, b_legs, lb):
+    """2 M K N summed over every pair of allowed blocks of A and B that agree
+    on the contracted legs (Sec. 2's block-pair contraction), enumerated
+    from the oracle's block lists."""
+    tot = 0
+    bb = u1.blocks(b_legs)
+    for x in u1.blocks(a_legs):
+        for y in bb:
+            if all(a_legs[i].charges[x[i]] == b_legs[j].charges[y[j]] for i, j in zip(la, lb)):
+                sa = [a_legs[i].degs[x[i]] for i in range(len(a_legs))]
+                sb = [b_legs[j].degs[y[j]] for j in range(len(b_legs))]
+                k = int(np.prod([sa[i] for i in la]))
+                m = int(np.prod([sa[i] for i in range(len(sa)) if i not in la]))
+                n = int(np.prod([sb[j] for j in range(len(sb)) if j not in lb]))
+                tot += 2 * m * k * n
+    return tot
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_work_counter_counts_matched_block_pairs(bst, ctx, seed, prec):
+    """bst_ctx_work_flops grows by exactly the matched-block-pair work of a
+    contraction, whatever the arithmetic."""
+    rng = np.random.default_rng(500 + seed)
+    shared = rand_legs(rng, 2, 6)
+    ao, bo = rand_legs(rng, 1, 6), rand_legs(rng, 2, 6)
+    a_legs = [ao[0], shared[0], shared[1]]
+    b_legs = [shared[1].dual(), bo[0], shared[0].dual(), bo[1]]
+    A = u1.to_dense(a_legs, rng.standard_normal(u1.nnz(a_legs)))
+    B = u1.to_dense(b_legs, rng.standard_normal(u1.nnz(b_legs)))
+    AL, ad = upload(bst, ctx, a_legs, A)
+    BL, bd = upload(bst, ctx, b_legs, B)
+    w0 = ctx.work_flops
+    ctx.contract(AL, ad, BL, bd, [1, 2], [2, 0], prec=prec)
+    assert ctx.work_flops - w0 == matched_pair_flops(a_legs, [1, 2], b_legs, [2, 0])

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 from oracle import ctm as octm  # noqa: E402
 from oracle import u1  # noqa: E402
 from workloads import u1_config, values  # noqa: E402
-from bst_helpers import rel_err, to_oracle_leg  # noqa: E402
+from bst_helpers import check_blocks, rel_err, to_oracle_leg  # noqa: E402
 
 TOL64 = 1e-12
 TOL_MOVE_OZ = 1e-9
@@ -50,7 +50,11 @@ def compare(net, ref, roles, tol):
     for r in roles:
         legs, dense = ref[r]
         assert [to_oracle_leg(l) for l in net.env.L[r].legs] == legs, r
-        errs[r] = rel_err(net.env.data(r).cpu().numpy(), u1.from_dense(legs, dense))
+        got, want = net.env.data(r).cpu().numpy(), u1.from_dense(legs, dense)
+        errs[r] = rel_err(got, want)
+        # per block: below tol of the tensor norm, below 100 tol of its own
+        # norm (floored at 1e-3 of the tensor norm)
+        check_blocks(legs, got, want, tol, 100.0 * tol)
     assert max(errs.values()) < tol, errs
     return errs
 

@@ -149,3 +149,69 @@ def test_square_ice_lieb():
         net = ctm.full_move(net, 32)
     W4 = (4.0 / 3.0) ** 6
     assert abs(ctm.kappa(net) / W4 - 1) < 5e-5
+
+
+# One counter-clockwise quarter turn written out tensor by tensor (the
+# geometry, independent of the oracle's rotation tables): after the turn a
+# leg that pointed up points left, left -> down, down -> right, right -> up.
+# new role <- (old role, axes of the old tensor in the new role's leg order)
+HAND_CCW = {
+    "C1": ("C2", (1, 0)),        # [R, D] <- C2[L, D]: old D now points R, old L now D
+    "T4": ("T1", (2, 1, 0)),     # [U, R, D] <- T1[L, D, R]
+    "C4": ("C1", (0, 1)),        # [U, R] <- C1[R, D]
+    "T3": ("T4", (0, 1, 2)),     # [L, U, R] <- T4[U, R, D]
+    "C3": ("C4", (1, 0)),        # [U, L] <- C4[U, R]
+    "T2": ("T3", (2, 1, 0)),     # [U, L, D] <- T3[L, U, R]
+    "C2": ("C3", (0, 1)),        # [L, D] <- C3[U, L]
+    "T1": ("T2", (0, 1, 2)),     # [L, D, R] <- T2[U, L, D]
+    "a": ("a", (1, 2, 3, 0)),    # [L, U, R, D] <- a[L, U, R, D]: old U now L, R now U, ...
+}
+
+
+def hand_ccw(net):
+    out = {}
+    for new, (old, ax) in HAND_CCW.items():
+        legs, arr = net[old]
+        out[new] = ([legs[i] for i in ax], np.ascontiguousarray(np.transpose(arr, ax)))
+    return out
+
+
+def hand_rotate(net, k):
+    for _ in range(k % 4):
+        net = hand_ccw(net)
+    return net
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rotation_keeps_the_network_value(k):
+    """A rotated network is the same contraction: the 3x3 value of a random,
+    anisotropic network (distinct environment tensors, a site without
+    symmetry between its legs) does not change; the oracle's rotation equals
+    the hand-written quarter turns."""
+    net = ctm.u1_network(u1_config("tiny"))
+    ref = ctm.network_value(net)
+    rot = ctm.rotate(net, k)
+    assert abs(ctm.network_value(rot) / ref - 1) < 1e-12
+    hand = hand_rotate(net, k)
+    for r in ctm.ROLES:
+        assert rot[r][0] == hand[r][0], r
+        assert np.array_equal(rot[r][1], hand[r][1]), r
+
+
+@pytest.mark.parametrize("direction", ["U", "R", "D"])
+def test_directional_move_is_the_left_move_of_the_turned_network(direction):
+    """UP, RIGHT and DOWN moves equal a LEFT move on the network turned by
+    hand (1, 2, 3 counter-clockwise quarter turns) and turned back."""
+    k = {"U": 1, "R": 2, "D": 3}[direction]
+    net = ctm.u1_network(u1_config("tiny"))
+    chi = u1_config("tiny")["chi"]
+    got = ctm.move(net, direction, chi)
+    want = hand_rotate(ctm.left_move(hand_rotate(net, k), chi), 4 - k)
+    renewed = {"U": ("C1", "T1", "C2"), "R": ("C2", "T2", "C3"), "D": ("C3", "T3", "C4")}[direction]
+    for r in ctm.ROLES:
+        assert got[r][0] == want[r][0], r
+        assert np.allclose(got[r][1], want[r][1], rtol=0, atol=1e-14), r
+    for r in set(ctm.ROLES) - set(renewed):
+        assert np.array_equal(got[r][1], net[r][1]), r
+    for r in renewed:
+        assert not np.array_equal(got[r][1].shape, net[r][1].shape) or not np.allclose(got[r][1], net[r][1])

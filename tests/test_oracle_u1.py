@@ -148,3 +148,38 @@ def test_remover_makes_right_leg_equal_left_leg():
     assert legs[2].same_space(legs[0]) and legs[2].flow == -legs[0].flow
     assert legs[3].same_space(legs[1]) and legs[3].flow == -legs[1].flow
     assert np.all(a[~u1.allowed_mask(legs)] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["tiny", "d4chi16"])
+def test_remover_branch_equals_the_eight_index_sum(name):
+    """Pin of the remover branch (Sec. 3.1): unfusing the result gives, for
+    every ket/bra index pair, sum_{p,s,r,r~} A[p,l,u,r,d] A[p,l~,u~,r~,d~]
+    R[r,x,s] R[r~,x~,s], written out here with one einsum.  A transposed
+    rho, a mispaired s or a missing sum over s changes this sum."""
+    A_legs, A, R_legs, R = _site(name)
+    legs, a = u1.double_layer(A_legs, A, R_legs, R)
+    Fs = [u1.fuse([l, l.dual()])[1] for l in (A_legs[1], A_legs[2], R_legs[1], A_legs[4])]
+    un = np.einsum("abce,alL,buU,cxX,edD->lLuUxXdD", a, *Fs, optimize=True)
+    direct = np.einsum("plurd,pLUtD,rxs,tXs->lLuUxXdD", A, A, R, R, optimize=True)
+    assert np.allclose(un, direct, rtol=0, atol=1e-13 * np.abs(direct).max())
+    # the sum over s is not separable: the product of the two separate sums
+    # differs (so a mispaired s cannot pass)
+    wrong = np.einsum("plurd,pLUtD,rxs,tXz->lLuUxXdD", A, A, R, R, optimize=True)
+    assert np.abs(wrong - direct).max() > 1e-3 * np.abs(direct).max()
+
+
+@pytest.mark.parametrize("name", ["tiny", "d4chi16"])
+def test_remover_equals_double_layer_of_the_absorbed_site(name):
+    """a(A, R) = a(A') with A'[(p,s), l, u, x, d] = sum_r A[p,l,u,r,d] R[r,x,s]:
+    absorbing the remover into the site first and then forming the plain
+    double layer gives the same tensor (the physical and remover legs are
+    summed together)."""
+    A_legs, A, R_legs, R = _site(name)
+    legs, a = u1.double_layer(A_legs, A, R_legs, R)
+    P, FP = u1.fuse([A_legs[0], R_legs[2]])
+    Ap = np.einsum("Pps,plurd,rxs->Pluxd", FP, A, R, optimize=True)
+    Ap_legs = [P, A_legs[1], A_legs[2], R_legs[1], A_legs[4]]
+    assert np.all(Ap[~u1.allowed_mask(Ap_legs)] == 0.0)
+    legs2, a2 = u1.double_layer(Ap_legs, Ap)
+    assert legs2 == legs
+    assert np.allclose(a2, a, rtol=0, atol=1e-13 * np.abs(a).max())

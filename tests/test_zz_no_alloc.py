@@ -1,8 +1,10 @@
 """The allocation-free contraction (bst_contract_noalloc) for callers that
-cannot allocate device memory (stream capture, externally owned device
-memory).  Its output must match bst_contract's on the same inputs, for two
-calls in a row through the shared scratch array; a contraction above the
-scratch limit must be refused.  Kept in its own file so it is collected last."""
+cannot allocate device memory (a process whose device memory another runtime
+owns and has sized in advance).  Its output must match bst_contract's on the
+same inputs, for two calls in a row through the shared scratch array, and a
+call after the first must leave the device's free memory unchanged; a
+contraction above the scratch limit must be refused.  Kept in its own file
+so it is collected last."""
 import numpy as np
 import pytest
 
@@ -44,8 +46,14 @@ def test_noalloc_matches_contract_two_calls(bst):
         b = torch.tensor(rng.standard_normal(B.nnz), dtype=torch.float64, device="cuda:0")
         _, ref = ctx.contract(A, a, B, b, la, lb, Cl=Cl)
         c = torch.full((Cl.nnz,), float("nan"), dtype=torch.float64, device="cuda:0")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         ctx.contract_noalloc(A, a, B, b, la, lb, Cl, c)
         ctx.sync()
+        if call > 0:
+            # the first call may load the library's module (and with it the
+            # static scratch array); later calls take no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
         assert rel_err(c.cpu().numpy(), ref.cpu().numpy()) < 1e-13, call
         # alpha/beta accumulate into the caller's output
         c2 = ref.clone()
