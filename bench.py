@@ -9,8 +9,10 @@ The environment is restored from a device copy before every step.
 
 Prints one JSON line (rank 0).  --impl reference times the dense FP64 CPU
 oracle on the host cores instead.  With N>1 ranks every rank runs an
-independent replica (the move does not shard; no collective on the data
-path) and the value is the sum over ranks.
+independent replica of the move (it does not shard; no collective on the
+data path) and the value is the sum over ranks; the batch of independent
+contractions is split over the ranks instead (balanced by block-pair work,
+no exchange), timed as the slowest rank's share.
 """
 from __future__ import annotations
 
@@ -175,6 +177,19 @@ def run_reference(args):
 BATCH_LEGS = ((0, 2), (1, 0))   # X2[k_u, x_r, k_l, x_d] . a[k_l, k_u, k_r, k_d] over (k_u, k_l)
 
 
+def batch_partition(costs, world):
+    """Split independent contractions over `world` ranks with no exchange:
+    longest first, each to the least loaded rank (ties: lower index).
+    Returns one ascending index list per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load, parts = [0.0] * world, [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 def batch_instances(bst, ctx, dev, count=64):
     """The batch of independent corner contractions (D ~ U{4..8},
     chi ~ U{32,64,96,128}): per entry the double layer a of a seeded site
@@ -198,8 +213,15 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     scatter, replayed from a captured CUDA graph.  Returns the report."""
     import numpy as np
     import torch
+    rank, world, _ = dist_env()
     inst = batch_instances(bst, ctx, dev)
     la, lb = BATCH_LEGS
+    # the contractions are independent: with several ranks each takes its
+    # share (balanced by their block-pair work), no data exchange
+    costs = [ctx.contract_flops(i[0], i[2], la, lb) for i in inst]
+    parts = batch_partition(costs, world)
+    total_count, total_flops = len(inst), sum(costs)
+    inst = [inst[i] for i in parts[rank]]
     As, as_, Bs, bs = ([i[k] for i in inst] for k in range(4))
     Cls, c64 = ctx.contract_batched(As, as_, Bs, bs, la, lb, prec="fp64")
     Cls, cs = ctx.contract_batched(As, as_, Bs, bs, la, lb, prec=prec, Cls=Cls)
@@ -229,32 +251,37 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
 
     ms, nl = timed(prec, steps)
     ms64, _ = timed("fp64", max(3, steps // 2))
+    ms, ms64 = job_ms(ms, world), job_ms(ms64, world)   # the slowest rank's
     ctx.profile(True)
     w0 = ctx.work_flops
     ctx.contract_batched(As, as_, Bs, bs, la, lb, prec=prec, Cls=Cls, cs=cs)
     flops = ctx.work_flops - w0
+    local_flops = flops
+    flops = total_flops
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile(False)
     gk = "gemm_ozaki" if prec == "ozaki" else "gemm_f64"
     by_rel = prof["relayout"][3]
-    out = {"workload": "u1_batch64_corner_contractions", "count": len(inst),
+    out = {"workload": "u1_batch64_corner_contractions", "count": total_count,
            "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s (block-sparse, FP64-equivalent)",
-           "contractions_per_s": len(inst) / (ms / 1e3), "ms_per_step": ms, "fp64_path_ms_per_step": ms64,
+           "contractions_per_s": total_count / (ms / 1e3), "ms_per_step": ms, "fp64_path_ms_per_step": ms64,
+           "ranks": world, "per_rank_count": [len(p) for p in parts],
+           "partition": "longest first to the least loaded rank by block-pair flops; no exchange",
            "algorithmic_gflop": flops / 1e9, "rel_err_vs_fp64_path": err, "gpu_launches": int(nl),
            "timing": "median of CUDA-graph replays, L2 flushed between replays",
            "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()},
            "autotune": [ln.split(" ", 2)[2] for ln in ctx.tuning_log().splitlines() if "chosen" in ln]}
     tms = prof[gk][1] / 1e3
     if prec == "ozaki":
-        a = flops / tms / 1e12
+        a = local_flops / tms / 1e12
         out["roofline"] = {"kernel": gk, "bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"],
                            "unit": "TFLOP/s", "frac": a / pk["bf16_tflops"],
                            "work": "method flops (2MNK of the matched blocks, counted once)",
-                           "digit_product_tflops": 15.0 * flops / tms / 1e12}
+                           "digit_product_tflops": 15.0 * local_flops / tms / 1e12}
     else:
         peak = pk["bf16_tflops"] * 1.25 / 2250.0
-        a = flops / tms / 1e12
+        a = local_flops / tms / 1e12
         out["roofline"] = {"kernel": gk, "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s",
                            "frac": a / peak}
     rel_s = prof["relayout"][1] / 1e3

@@ -75,8 +75,14 @@ typedef enum {
  *            Condon-Shortley Clebsch-Gordan coefficients (no leg: J = 0; one
  *            leg: J = its spin).  Tree labels (bst_layout_tree): the in-tree
  *            intermediates, J, the out-tree intermediates, as doubled spins.
- *            Blocks are ordered by sector indices, then tree labels. */
-typedef enum { BST_U1 = 1, BST_SU2 = 2 } bst_group;
+ *            Blocks are ordered by sector indices, then tree labels.
+ *   BST_Z2:  charges are parities 0 or 1 (the paper's third symmetry, Sec. 4.1
+ *            compares none, Z2, U(1) and SU(2)); a block is allowed iff
+ *            sum_i q_i is even, a fused leg's charge is the parity of its
+ *            members' sum, and the pairing of sectors through a cut matches
+ *            equal parities.  Everything else is as for BST_U1: every
+ *            operation that takes BST_U1 layouts takes BST_Z2 layouts. */
+typedef enum { BST_U1 = 1, BST_SU2 = 2, BST_Z2 = 3 } bst_group;
 
 /* Arithmetic of the block GEMMs.
  *   BST_FP64:  plain FP64 (DMMA) grouped GEMM;
@@ -231,6 +237,16 @@ BST_API bst_status bst_fuse(bst_ctx ctx, bst_layout src, const double* src_data,
 BST_API bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs,
                                const int32_t* legsA, const int32_t* legsB,
                                bst_layout* C);
+
+/* Algorithmic work of contract(A, B) over the given leg pairs, without
+ * running it: 2 M K N summed over every pair of blocks of A and B that agree
+ * on the contracted legs (Sec. 2's block-pair contraction), in *flops.
+ * Plans on the host only, so a host-only context (device -1) may answer it
+ * (used to balance a batch of contractions over GPUs before any device
+ * work).  U(1) layouts (BST_E_UNSUPPORTED otherwise); errors as
+ * bst_contract_layout. */
+BST_API bst_status bst_contract_flops(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs,
+                                      const int32_t* legsA, const int32_t* legsB, double* flops);
 
 /* c = alpha * contract(a, b) + beta * c, with C the layout from
  * bst_contract_layout.  Matched block pairs are grouped by the conserved

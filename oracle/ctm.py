@@ -31,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .u1 import Leg
+from .u1 import Leg, modulus, reduce
 
 ROLE_DIRS = {"C1": "RD", "C2": "LD", "C3": "UL", "C4": "UR",
              "T1": "LDR", "T2": "ULD", "T3": "LUR", "T4": "URD", "a": "LURD"}
@@ -63,13 +63,14 @@ def rotate(net, k):
 
 
 def sector_keys(legs, sign):
-    """Charge carried through a composite index: sign * sum_i flow_i q_i."""
+    """Charge carried through a composite index: sign * sum_i flow_i q_i
+    (Z2: its parity)."""
     tot = np.zeros([l.dim for l in legs], dtype=np.int64)
     for ax, l in enumerate(legs):
         shape = [1] * len(legs)
         shape[ax] = l.dim
         tot = tot + l.flow * l.charge_vector().reshape(shape)
-    return (sign * tot).reshape(-1)
+    return reduce(sign * tot, modulus(legs)).reshape(-1)
 
 
 def quarters(net):
@@ -120,6 +121,7 @@ def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
     kb = sector_keys(beta_legs, -1)
     kbp = sector_keys(betap_legs, +1)
     f_new = L["C1"][1].flow                   # the new bond keeps C1.D's flow
+    mod = modulus(beta_legs)
     secs = {}
     cands = []
     for key in sorted(set(kb.tolist()) & set(kbp.tolist())):
@@ -128,7 +130,7 @@ def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
         U, S, Vt = np.linalg.svd(N[np.ix_(rows, cols)], full_matrices=False)
         secs[key] = (rows, cols, U, S, Vt.T)
         for j, s in enumerate(S):
-            cands.append((float(s), f_new * key, key, j))
+            cands.append((float(s), reduce(f_new * key, mod), key, j))
     kept = truncate(cands, chi, rel_cutoff)
     # new leg: ascending charge, descending sigma inside a sector
     by_q = {}
@@ -155,7 +157,7 @@ def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
             Pt[col, :] = (Rt_m[:, rows] @ u) / np.sqrt(s)
             svals[col] = s
             col += 1
-    new_leg = Leg(f_new, new_charges, new_degs)
+    new_leg = Leg(f_new, new_charges, new_degs, mod)
     C1, T1, C2, T2, C3, T3, C4, T4, a = (net[r][1] for r in ROLES)
     e = lambda s, *x: np.einsum(s, *x, optimize=True)
     X1 = q["X1"]                                            # [C1.D, T1.D, T1.R]
@@ -228,7 +230,7 @@ def env_legs(x_leg_charges, x_leg_degs, a_legs):
     a_legs = [L, U, R, D].  Environment bonds flow left-to-right along the
     rows and top-to-bottom along the columns; an edge tensor's site leg is
     the dual of the site leg it touches."""
-    X = lambda f: Leg(f, tuple(x_leg_charges), tuple(x_leg_degs))
+    X = lambda f: Leg(f, tuple(x_leg_charges), tuple(x_leg_degs), a_legs[0].mod)
     kl, ku, kr, kd = a_legs
     return {"C1": [X(-1), X(-1)], "C2": [X(1), X(-1)], "C3": [X(1), X(1)], "C4": [X(1), X(-1)],
             "T1": [X(1), ku.dual(), X(-1)], "T2": [X(1), kr.dual(), X(-1)],

@@ -1,4 +1,4 @@
-"""U(1)-symmetric tensors for the oracle: legs, canonical layout, dense expansion.
+"""U(1)- and Z2-symmetric tensors for the oracle: legs, canonical layout, dense expansion.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -9,6 +9,9 @@ satisfy the addition rule, and the rule can be enforced by hand instead of
 storing it (Sec. 2, text after Eq. "tensor-cgc").  No global charge shift
 is allowed (Sec. 2, end of the worked example), so the rule is
     sum_i flow_i * q_i = 0        (flow +1 incoming, -1 outgoing).
+For Z2 (the paper's third symmetry, compared in Sec. 4.1) the charges are
+parities 0 and 1 and the same rule holds modulo 2; a leg carries its
+modulus (0 for U(1), 2 for Z2) and every rule below reduces sums by it.
 
 Canonical layout (a reading: the paper fixes no storage order):
   * a leg's sectors have strictly ascending charges; its dense index is the
@@ -31,19 +34,23 @@ class Leg:
     flow: int           # +1 incoming, -1 outgoing
     charges: tuple      # strictly ascending sector charges
     degs: tuple         # reduced degeneracy (dimension) of each sector
+    mod: int = 0        # 0: U(1) integer charges; 2: Z2 parities
 
     def __post_init__(self):
         assert self.flow in (1, -1)
         assert len(self.charges) == len(self.degs)
         assert all(b > a for a, b in zip(self.charges, self.charges[1:]))
         assert all(d > 0 for d in self.degs)
+        assert self.mod in (0, 2)
+        if self.mod:
+            assert all(0 <= q < self.mod for q in self.charges)
 
     @property
     def dim(self):
         return int(sum(self.degs))
 
     def dual(self):
-        return Leg(-self.flow, self.charges, self.degs)
+        return Leg(-self.flow, self.charges, self.degs, self.mod)
 
     def charge_vector(self):
         """Charge of every dense index of the leg."""
@@ -57,15 +64,27 @@ class Leg:
 
 
 def leg_from_spec(spec):
-    return Leg(spec["flow"], tuple(spec["charges"]), tuple(spec["degs"]))
+    return Leg(spec["flow"], tuple(spec["charges"]), tuple(spec["degs"]), spec.get("mod", 0))
+
+
+def modulus(legs):
+    m = {l.mod for l in legs}
+    assert len(m) == 1, "legs of one tensor share their group"
+    return m.pop()
+
+
+def reduce(q, mod):
+    """Canonical representative of a charge sum: itself (U(1)) or its parity (Z2)."""
+    return q % mod if mod else q
 
 
 def blocks(legs):
     """Canonical list of allowed sector tuples (Sec. 2: blocks labelled by one
     charge per leg; forbidden blocks are identically zero)."""
+    mod = modulus(legs)
     out = []
     for idx in itertools.product(*[range(len(l.charges)) for l in legs]):
-        if sum(l.flow * l.charges[i] for l, i in zip(legs, idx)) == 0:
+        if reduce(sum(l.flow * l.charges[i] for l, i in zip(legs, idx)), mod) == 0:
             out.append(idx)
     return out
 
@@ -90,7 +109,8 @@ def allowed_mask(legs):
         shape = [1] * len(legs)
         shape[ax] = l.dim
         tot = tot + l.flow * l.charge_vector().reshape(shape)
-    return tot == 0
+    mod = modulus(legs)
+    return (tot % mod == 0) if mod else (tot == 0)
 
 
 def to_dense(legs, flat):
@@ -134,14 +154,15 @@ def fuse(legs):
     Returns (fused_leg, F) with F the dense 0/1 isometry F[k, i_0, i_1, ...].
     """
     f0 = legs[0].flow
+    mod = modulus(legs)
     by_q = {}
     for idx in itertools.product(*[range(len(l.charges)) for l in legs]):
-        q = sum(l.flow * l.charges[i] for l, i in zip(legs, idx)) * f0
+        q = reduce(sum(l.flow * l.charges[i] for l, i in zip(legs, idx)) * f0, mod)
         by_q.setdefault(q, []).append(idx)
     charges = tuple(sorted(by_q))
     degs = tuple(sum(int(np.prod([l.degs[i] for l, i in zip(legs, t)])) for t in by_q[q])
                  for q in charges)
-    fl = Leg(f0, charges, degs)
+    fl = Leg(f0, charges, degs, mod)
     F = np.zeros((fl.dim,) + tuple(l.dim for l in legs))
     offs = [l.sector_offsets() for l in legs]
     k = 0

@@ -87,6 +87,7 @@ def lib():
         "bst_permute": [vp, vp, vp, P(i32), P(vp), vp, vp],
         "bst_fuse": [vp, vp, vp, i32, P(i32), P(vp), vp, vp],
         "bst_contract_layout": [vp, vp, vp, i32, P(i32), P(i32), P(vp)],
+        "bst_contract_flops": [vp, vp, vp, i32, P(i32), P(i32), P(dbl)],
         "bst_contract": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), C.c_int, dbl, dbl, vp, vp, vp],
         "bst_double_layer": [vp, vp, vp, vp, vp, P(vp), vp, vp],
         "bst_contract_noalloc": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), dbl, dbl, vp, vp, vp],
@@ -275,9 +276,9 @@ class Context:
         return out
 
     def layout(self, legs, group="u1"):
-        """Layout of the given legs; group "u1" (charges 2Sz) or "su2"
-        (charges 2j, degeneracies = multiplet counts)."""
-        g = {"u1": 1, "su2": 2}[group]
+        """Layout of the given legs; group "u1" (charges 2Sz), "su2"
+        (charges 2j, degeneracies = multiplet counts) or "z2" (parities 0, 1)."""
+        g = {"u1": 1, "su2": 2, "z2": 3}[group]
         legs = [l if isinstance(l, Leg) else Leg(int(l["flow"]), tuple(l["charges"]), tuple(l["degs"]))
                 for l in legs]
         arr = (_Leg * len(legs))()
@@ -311,6 +312,12 @@ class Context:
         h = C.c_void_p()
         _check(lib().bst_contract_layout(self.h, A.h, B.h, len(legsA), _i32(legsA), _i32(legsB), C.byref(h)))
         return Layout(self, h)
+
+    def contract_flops(self, A, B, legsA, legsB):
+        """2 M K N over the matched block pairs of contract(A, B) (host-side plan)."""
+        f = C.c_double()
+        _check(lib().bst_contract_flops(self.h, A.h, B.h, len(legsA), _i32(legsA), _i32(legsB), C.byref(f)))
+        return f.value
 
     def contract(self, A, a, B, b, legsA, legsB, prec="fp64", alpha=1.0, beta=0.0, Cl=None, c=None,
                  stream=None):

@@ -344,6 +344,21 @@ bst_status bst_fuse(bst_ctx ctx, bst_layout src, const double* src_data, int32_t
   });
 }
 
+bst_status bst_contract_flops(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs, const int32_t* legsA,
+                              const int32_t* legsB, double* flops) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && A && B && flops && npairs >= 0, BST_E_ARG, "bad argument");
+    BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
+    std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    require_u1(L_(A));
+    require_u1(L_(B));
+    ContractPlan* p = get_contract_plan(C_(ctx), L_(A), L_(B), la, lb);
+    double f = 0;
+    for (auto& g : p->probs) f += 2.0 * double(g.M) * g.N * g.K;
+    *flops = f;
+  });
+}
+
 bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs, const int32_t* legsA,
                                const int32_t* legsB, bst_layout* C) {
   return guarded([&] {

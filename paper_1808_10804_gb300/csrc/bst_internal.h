@@ -39,6 +39,15 @@ struct Error : std::runtime_error {
       throw ::bst::Error(BST_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Charges of the abelian groups: U(1) charges are integers, Z2 charges are
+// parities.  cnorm maps a sum of (flow-signed) charges to its canonical
+// representative: itself for U(1), its parity (0 or 1) for Z2.
+inline int64_t cnorm(int group, int64_t q) {
+  if (group == BST_Z2) return q & 1;  // two's complement: parity of negative sums too
+  return q;
+}
+inline bool is_abelian(int group) { return group == BST_U1 || group == BST_Z2; }
+
 // One leg: flow and sectors (Sec. 2).  `off` are sector offsets in the dense
 // index of the leg.
 struct Leg {
@@ -175,6 +184,7 @@ struct ContractPlan {
   std::vector<GemmProb> probs; // per matched sector
   DevGemm g;
   OzakiPlan* oz = nullptr;
+  OzakiPlan* ozs = nullptr;    // the same GEMM with the output scattered into C's blocks
   int64_t amat = 0, bmat = 0, cmat = 0;  // matrix buffer sizes (elements)
   ~ContractPlan();
 };
@@ -225,6 +235,9 @@ struct Ctx {
   void* cusolver = nullptr;
   int proj_method = 1;   // 0: cuSOLVER gesvd per sector, 1: subspace iteration + small eigensolver
   int proj_iters = 9;    // subspace iterations
+  // Rayleigh-Ritz eigenproblems of the subspace iteration start from the
+  // nearly diagonal matrix itself (one relative Jacobi pass)
+  bool rr_near_diag = true;
   double* d_scratch_small = nullptr;
   bool autotune = true;      // time schedule candidates on the first batched call of a plan
   std::string tune_log;      // one line per tuning decision
@@ -249,8 +262,10 @@ struct Ctx {
 Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs);  // new reference
 void retain(Layout* l);
 void release(Layout* l);
-Leg fuse_legs(const std::vector<Leg>& legs, std::vector<std::vector<int32_t>>* tuples_per_sector = nullptr);
-std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& legs, int64_t target);
+Leg fuse_legs(const std::vector<Leg>& legs, std::vector<std::vector<int32_t>>* tuples_per_sector = nullptr,
+              int group = BST_U1);
+std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& legs, int64_t target,
+                                               int group = BST_U1);
 
 // plan.cpp
 MatView make_matview(const Layout* L, const std::vector<int>& rowlegs, const std::vector<int>& collegs,
@@ -284,6 +299,12 @@ extern const int kF64TileM, kF64TileN;
 
 // gemm_ozaki.cu
 void ozaki_prepare(Ctx* ctx, ContractPlan* p);
+// scatter variant: the epilogue writes c = alpha * A B + beta * c straight
+// into the output tensor's canonical blocks (no sector matrix, no scatter
+// launch)
+void ozaki_prepare_scatter(Ctx* ctx, ContractPlan* p);
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* c,
+                            double alpha, double beta, cudaStream_t s);
 void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
                     cudaStream_t s);
 void ozaki_free(OzakiPlan* oz);
@@ -338,7 +359,8 @@ void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double*
                   const std::vector<int>& lb, bst_prec prec, double alpha, double beta, Layout* C, double* c,
                   cudaStream_t s);
 inline void require_u1(const Layout* L) {
-  if (L->group != BST_U1) throw Error(BST_E_UNSUPPORTED, "this operation is implemented for U(1) tensors only");
+  if (!is_abelian(L->group))
+    throw Error(BST_E_UNSUPPORTED, "this operation is implemented for U(1) and Z2 tensors only");
 }
 
 // ctm.cpp

@@ -100,7 +100,7 @@ void contract_noalloc(Ctx* ctx, Layout* A, const double* a, Layout* B, const dou
   std::vector<GemmProb> probs;
   for (auto& cs : vc.secs) {
     const MatSector* as = va.find(cs.key);
-    const MatSector* bs = vb.find(-cs.key);
+    const MatSector* bs = vb.find(cnorm(A->group, -cs.key));
     GemmProb g{};
     g.M = int32_t(cs.rows);
     g.N = int32_t(cs.cols);

@@ -156,7 +156,7 @@ T absorb(Ctx* ctx, const std::string& name, T X, std::vector<int> lx, std::vecto
       groups.push_back(1);
     }
   }
-  Layout* XuL = make_layout(ctx, BST_U1, ul);
+  Layout* XuL = make_layout(ctx, A->group, ul);
   Layout* fused = nullptr;
   DevRelayout* up = get_fuse_plan(ctx, XuL, groups, &fused);
   release(fused);
@@ -298,7 +298,7 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
     if (a->rank == 5) {
       std::vector<Leg> dl;
       for (auto& l : r[SITE].L->legs) dl.push_back(l.dual());
-      site_dual = make_layout(ctx, BST_U1, dl);
+      site_dual = make_layout(ctx, a->group, dl);
       release(site_dual);  // interned
     }
     left_move(ctx, r, site_dual, chi, cutoff, prec, out, &pr, s);

@@ -130,37 +130,54 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
         prm[k] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
       }
       __syncthreads();
-      // rows: A <- J^T A; thread (column j, pair group g) applies the
-      // rotations k = g, g + G, ... (disjoint rows, so no conflicts)
-      const int G = nt / bp > 0 ? nt / bp : 1;
-      const int jcol = tid % bp, grp = tid / bp;
-      if (grp < G) {
-        const int j = jcol;
-        for (int k = grp; k < npair; k += G) {
-          const float4 pr = prm[k];
-          const float c = pr.x, s = pr.y;
-          if (s == 0.f) continue;
-          const int p = __float_as_int(pr.z), q = __float_as_int(pr.w);
-          const float ap = A[p * ld + j], aq = A[q * ld + j];
-          A[p * ld + j] = c * ap - s * aq;
-          A[q * ld + j] = s * ap + c * aq;
+      // A <- J^T A J by 2 x 2 blocks: the block of pair a (rows p_a, q_a) and
+      // pair b (columns p_b, q_b) becomes G_a^T X G_b (rows rotated first,
+      // then columns).  A is symmetric, so one thread takes the block and its
+      // mirror (a <= b): every entry is read and written once per round.
+      // Blocks whose two rotations are both the identity are left alone.
+      const int nblk = npair * (npair + 1) / 2;
+      for (int t = tid; t < nblk; t += nt) {
+        // t -> (a, bq) with a <= bq: t = bq (bq + 1) / 2 + a
+        int bq = int((sqrtf(8.f * float(t) + 1.f) - 1.f) * 0.5f);
+        while (bq * (bq + 1) / 2 > t) --bq;
+        while ((bq + 1) * (bq + 2) / 2 <= t) ++bq;
+        const int a = t - bq * (bq + 1) / 2;
+        const float4 ra = prm[a], rb = prm[bq];
+        if (ra.y == 0.f && rb.y == 0.f) continue;
+        const int pa = __float_as_int(ra.z), qa = __float_as_int(ra.w);
+        const int pb = __float_as_int(rb.z), qb = __float_as_int(rb.w);
+        const float x00 = A[pa * ld + pb], x01 = A[pa * ld + qb];
+        const float x10 = A[qa * ld + pb], x11 = A[qa * ld + qb];
+        // rows: Y = G_a^T X
+        const float y00 = ra.x * x00 - ra.y * x10, y01 = ra.x * x01 - ra.y * x11;
+        const float y10 = ra.y * x00 + ra.x * x10, y11 = ra.y * x01 + ra.x * x11;
+        // columns: X' = Y G_b
+        const float z00 = rb.x * y00 - rb.y * y01, z01 = rb.y * y00 + rb.x * y01;
+        const float z10 = rb.x * y10 - rb.y * y11, z11 = rb.y * y10 + rb.x * y11;
+        A[pa * ld + pb] = z00;
+        A[pa * ld + qb] = z01;
+        A[qa * ld + pb] = z10;
+        A[qa * ld + qb] = z11;
+        if (a != bq) {
+          A[pb * ld + pa] = z00;
+          A[qb * ld + pa] = z01;
+          A[pb * ld + qa] = z10;
+          A[qb * ld + qa] = z11;
         }
       }
-      __syncthreads();
-      // columns: A <- A J, V <- V J; thread (row i, pair group g)
+      // V <- V J: thread (row i, pair group g) applies the rotations
+      // k = g, g + G, ... to row i
+      const int G = nt / bp > 0 ? nt / bp : 1;
+      const int irow = tid % bp, grp = tid / bp;
       if (grp < G) {
-        const int i = jcol;
         for (int k = grp; k < npair; k += G) {
           const float4 pr = prm[k];
           const float c = pr.x, s = pr.y;
           if (s == 0.f) continue;
           const int p = __float_as_int(pr.z), q = __float_as_int(pr.w);
-          const float ap = A[i * ld + p], aq = A[i * ld + q];
-          A[i * ld + p] = c * ap - s * aq;
-          A[i * ld + q] = s * ap + c * aq;
-          const float vp = V[i * ld + p], vq = V[i * ld + q];
-          V[i * ld + p] = c * vp - s * vq;
-          V[i * ld + q] = s * vp + c * vq;
+          const float vp = V[irow * ld + p], vq = V[irow * ld + q];
+          V[irow * ld + p] = c * vp - s * vq;
+          V[irow * ld + q] = s * vp + c * vq;
         }
       }
       __syncthreads();
@@ -297,240 +314,260 @@ __device__ __forceinline__ void split_pow2(double x, int* k, float* r) {
   *r = f64_to_f32_scaled(x, -*k);
 }
 
-// FP32 Cholesky of M (b x b, FP64 in) and Rinv = (L^T)^-1 (upper, FP64 out).
-// 512 threads; b <= 160.
-__global__ void __launch_bounds__(512) cholinv_f32(const SmallProb* __restrict__ probs, const double* __restrict__ in,
-                                                  double* __restrict__ out, int* err) {
+// FP32 Cholesky factor M = L L^T (after scaling M to unit diagonal) and the
+// inverse of L^T, for the CholQR steps of the subspace iteration; b <= 160,
+// one CTA of 512 threads (16 warps) per problem.  Output Rinv (FP64, upper)
+// with Y Rinv orthonormal when M = Y^T Y.
+//
+// The scaled matrix is padded with the identity to bp (a multiple of 32), so
+// every panel is one full 32 x 32 block and no loop carries a bound check.
+// Per panel P (rows and columns kb = 32 P .. kb + 31), three phases between
+// barriers:
+//   1. warp 0 factors the diagonal block D in registers (lane r holds row r;
+//      pivots and column entries travel by warp shuffles) and, in the same
+//      pivot loop with the same broadcast column entries, eliminates below
+//      each pivot in the identity to form D^-1 (lane c holds column c);
+//      meanwhile the other warps
+//      form T = L[P, 0:P] Li[0:P, 0:P], the product block row P of the
+//      inverse needs, stashed transposed in the (otherwise unused) upper
+//      triangle of Li;
+//   2. the rows below the panel get L[i, P] = A[i, P] D^-T, and the inverse
+//      gets its block row Li[P, 0:P] = -D^-1 T;
+//   3. the trailing lower triangle gets A -= L[:, P] L[:, P]^T, 8-row
+//      quarters of 32 x 32 blocks per warp.
+// Operands that a lane reuses across rows (a column of D^-1, a row of the
+// panel) sit in registers; the shared row it meets them with is read by all
+// lanes at one address (a broadcast).  Columns whose pivot falls below 1e-6
+// (numerically dependent on earlier ones at FP32 level) are dropped: their
+// row and column of the factor become those of the identity, and their row
+// and column of Rinv are zero.
+constexpr int kCholThreads = 512;
+constexpr int kCholWarps = kCholThreads / 32;
+
+// Input: either the FP64 matrix M at in + in_off (nparts == 0), or nparts
+// FP32 partial sums of it, partial s at gin + in_off + s b^2, added in slice
+// order (gram_f32_kernel's output).
+__global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __restrict__ probs,
+                                                            const double* __restrict__ in, double* __restrict__ out,
+                                                            int* err, const float* __restrict__ gin, int nparts) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
-  const int b = pr.b, ld = b + 1, bb = b * b;
-  float* L = sh;            // b x ld
-  float* Li = L + b * ld;   // b x ld, inverse of L
-  int* drop = reinterpret_cast<int*>(Li + b * ld + b);
-  float* rsc = Li + b * ld;                                  // b row scales: mantissas
-  int* ksc = reinterpret_cast<int*>(Li + b * ld + 2 * b);    // b row scales: exponents
+  const int b = pr.b, bb = b * b;
+  const int bp = (b + 31) & ~31, ld = bp + 1, nbp = bp >> 5;
+  float* L = sh;                 // bp x ld: the matrix, overwritten by its factor (lower)
+  float* Li = L + bp * ld;       // bp x ld: inverse of the factor (lower); T stash (upper)
+  float* rsc = Li + bp * ld;     // bp row-scale mantissas
+  int* ksc = reinterpret_cast<int*>(rsc + bp);  // bp row-scale exponents
+  int* drop = ksc + bp;          // bp dropped-column flags
   const double* M = in + pr.in_off;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  // scale by the diagonal so the factorisation sees unit diagonal: row i is
-  // scaled by 1/sqrt(M_ii) = rsc[i] 2^ksc[i] (one FP64 square root and
-  // division per row); the entries take the power of two exactly in the
-  // conversion to FP32 and the mantissas as two FP32 products
-  for (int i = tid; i < b; i += nt) {
-    const double d = M[(long long)i * b + i];
+  const float* G = nparts > 0 ? gin + pr.in_off : nullptr;
+  // unit-diagonal scaling: row i times 1 / sqrt(M_ii) = rsc[i] 2^ksc[i]
+  for (int i = tid; i < bp; i += kCholThreads) {
     int k = 0;
     float r = 1.f;
-    if (d > 0) split_pow2(1.0 / sqrt(d), &k, &r);
+    if (i < b) {
+      double d;
+      if (G) {
+        float ds = 0.f;
+        for (int s = 0; s < nparts; ++s) ds += G[(long long)s * bb + (long long)i * b + i];
+        d = double(ds);
+      } else {
+        d = M[(long long)i * b + i];
+      }
+      if (d > 0) split_pow2(1.0 / sqrt(d), &k, &r);
+    }
     ksc[i] = k;
     rsc[i] = r;
+    drop[i] = 0;
   }
   __syncthreads();
-  // eight global loads in flight per thread
-  for (int q0 = tid; q0 < bb; q0 += 8 * nt) {
-    double v[8];
+  if (G) {
+    // FP32 partial sums: added in slice order, then scaled (the power of two
+    // exactly, the mantissas as two FP32 products)
+    for (int q = tid; q < bp * bp; q += kCholThreads) {
+      const int i = q / bp, j = q - i * bp;
+      float a;
+      if (i < b && j < b) {
+        float g = 0.f;
+        for (int s = 0; s < nparts; ++s) g += G[(long long)s * bb + (long long)i * b + j];
+        a = ldexpf(g, ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+      } else {
+        a = (i == j) ? 1.f : 0.f;
+      }
+      L[i * ld + j] = a;
+      Li[i * ld + j] = 0.f;
+    }
+  } else {
+  for (int q0 = tid; q0 < bp * bp; q0 += 4 * kCholThreads) {
+    double v[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = q0 + u * nt;
-      v[u] = q < bb ? M[q] : 0.0;
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * kCholThreads;
+      const int i = q / bp, j = q - i * bp;
+      v[u] = (q < bp * bp && i < b && j < b) ? M[(long long)i * b + j] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = q0 + u * nt;
-      if (q < bb) {
-        const int i = q / b, j = q - i * b;
-        L[i * ld + j] = f64_to_f32_scaled(v[u], ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * kCholThreads;
+      if (q < bp * bp) {
+        const int i = q / bp, j = q - i * bp;
+        float a;
+        if (i < b && j < b) a = f64_to_f32_scaled(v[u], ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+        else a = (i == j) ? 1.f : 0.f;
+        L[i * ld + j] = a;
         Li[i * ld + j] = 0.f;
       }
     }
   }
+  }
   __syncthreads();
-  // Blocked right-looking factorisation with 32-wide panels.  Warp 0
-  // factors the diagonal block D in registers (lane i holds row i, pivots
-  // and column entries travel by warp shuffles) and forms D^-1 column by
-  // lane (stored as the diagonal block of Li).  The panel below is then panel * D^-T, and
-  // all threads update the trailing lower triangle.  Columns whose pivot
-  // falls below 1e-6 (numerically dependent on earlier ones at FP32 level)
-  // are dropped: their row and column of the factor become the identity
-  // and their column of Rinv is zero.
-  for (int kb = 0; kb < b; kb += 32) {
-    const int w = min(32, b - kb);
+  for (int P = 0; P < nbp; ++P) {
+    const int kb = P << 5;
+    // ---- phase 1 ----
     if (warp == 0) {
       float row[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) row[c] = (lane < w && c < w) ? L[(kb + lane) * ld + kb + c] : 0.f;
+      for (int c = 0; c < 32; ++c) row[c] = L[(kb + lane) * ld + kb + c];
       int mydrop = 0;
-      float myinv = 1.f;  // 1 / D[lane][lane]
+      // column `lane` of D^-1, eliminated along with the factorisation:
+      // D x = e_lane, pivot by pivot (x_k /= D_kk, then x_j -= D_jk x_k)
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        if (k < w) {
-          const float dkk = __shfl_sync(0xffffffffu, row[k], k);
-          const bool dk = !(dkk > 1e-6f);  // the same on every lane
-          const float inv = dk ? 1.f : rsqrtf(dkk);
-          const bool me = lane == k;
-          row[k] = me ? (dk ? 1.f : dkk * inv) : (lane > k ? (dk ? 0.f : row[k] * inv) : row[k]);
-          mydrop = me ? int(dk) : mydrop;
-          myinv = me ? inv : myinv;
+        const float dkk = __shfl_sync(0xffffffffu, row[k], k);
+        const bool dk = !(dkk > 1e-6f);  // the same on every lane
+        const float inv = dk ? 1.f : rsqrtf(dkk);  // 1 / D_kk
+        if (lane == k) {
+          row[k] = dk ? 1.f : dkk * inv;
+          mydrop = int(dk);
           if (dk) {
-            // row k of the factor becomes that of the identity
 #pragma unroll
-            for (int c = 0; c < k; ++c) row[c] = me ? 0.f : row[c];
-          } else {
+            for (int c = 0; c < k; ++c) row[c] = 0.f;
+          }
+        } else if (lane > k) {
+          row[k] = dk ? 0.f : row[k] * inv;
+        }
+        x[k] *= inv;
+        if (!dk) {
 #pragma unroll
-            for (int j = k + 1; j < 32; ++j) {
-              const float ljk = __shfl_sync(0xffffffffu, row[k], j);
-              row[j] = lane >= j ? fmaf(-row[k], ljk, row[j]) : row[j];
-            }
+          for (int j = k + 1; j < 32; ++j) {
+            const float ljk = __shfl_sync(0xffffffffu, row[k], j);  // D_jk
+            if (lane >= j) row[j] = fmaf(-row[k], ljk, row[j]);
+            x[j] = fmaf(-ljk, x[k], x[j]);
           }
         }
       }
-      // column `lane` of D^-1 by forward substitution, D[i][k] and
-      // 1 / D[i][i] broadcast from lane i
-      float col[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        float acc = (i == lane) ? 1.f : 0.f;
+      for (int c = 0; c < 32; ++c) L[(kb + lane) * ld + kb + c] = (c <= lane) ? row[c] : 0.f;
 #pragma unroll
-        for (int k = 0; k < i; ++k) acc = fmaf(-__shfl_sync(0xffffffffu, row[k], i), col[k], acc);
-        col[i] = acc * __shfl_sync(0xffffffffu, myinv, i);
+      for (int i = 0; i < 32; ++i) Li[(kb + i) * ld + kb + lane] = (i >= lane) ? x[i] : 0.f;
+      drop[kb + lane] = mydrop;
+    } else if (P > 0) {
+      // T[r][j] = sum_{k >= j} L[kb + r][k] Li[k][j] for j < kb, stashed at
+      // Li[j][kb + r]; items: (column block J, 8 rows)
+      const int nitem = P * 4;
+      for (int it = warp - 1; it < nitem; it += kCholWarps - 1) {
+        const int J = it >> 2, r0 = (it & 3) * 8;
+        const int j = (J << 5) + lane;
+        float acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+        for (int k = J << 5; k < kb; ++k) {
+          const float li = Li[k * ld + j];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = fmaf(L[(kb + r0 + u) * ld + k], li, acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Li[j * ld + kb + r0 + u] = acc[u];
       }
-      if (lane < w) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < w) L[(kb + lane) * ld + kb + c] = row[c];
-        drop[kb + lane] = mydrop;
-      }
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i < w && lane < w) Li[(kb + i) * ld + kb + lane] = col[i];
     }
     __syncthreads();
-    // dropped columns of this block: zero their rows left of the block too
-    for (int c = 0; c < w; ++c)
-      if (drop[kb + c])
-        for (int j = tid; j < kb; j += nt) L[(kb + c) * ld + j] = 0.f;
-    // panel: rows i >= kb+w, L[i][kb..kb+w) <- L[i][kb..] D^-T; four threads
-    // per row, eight columns each; the row is read whole before any thread
-    // of it writes
-    const int m = b - kb - w;
-    for (int base = 0; base < 4 * m; base += nt) {
-      const int item = base + tid;
-      const bool act = item < 4 * m;
-      const int i = kb + w + (act ? item >> 2 : 0), g = item & 3;
-      float y[32];
+    // ---- phase 2 ----
+    {
+      // rows below the panel: L[i][kb + c] = sum_k A[i][kb + k] D^-1[c][k]
+      float dinv[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) y[c] = (act && c < w) ? L[i * ld + kb + c] : 0.f;
-      __syncthreads();
-      if (act) {
+      for (int k = 0; k < 32; ++k) dinv[k] = Li[(kb + lane) * ld + kb + k];
+      const bool dropc = drop[kb + lane] != 0;
+      // (rows in pairs, four partial sums each: short dependency chains)
+      for (int i = kb + 32 + warp; i < bp; i += 2 * kCholWarps) {
+        const int i2 = i + kCholWarps;
+        const bool two = i2 < bp;
+        float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = 8 * g + u;
-          if (c < w) {
-            // D^-1 is lower triangular (zeros above its diagonal); columns
-            // past the block (y = 0 there) read a valid entry instead
-            const float* dinv = Li + (kb + c) * ld + kb;
-            float acc = 0.f;
+        for (int k = 0; k < 32; ++k) {
+          s0[k & 3] = fmaf(L[i * ld + kb + k], dinv[k], s0[k & 3]);
+          if (two) s1[k & 3] = fmaf(L[i2 * ld + kb + k], dinv[k], s1[k & 3]);
+        }
+        __syncwarp();
+        L[i * ld + kb + lane] = dropc ? 0.f : (s0[0] + s0[1]) + (s0[2] + s0[3]);
+        if (two) L[i2 * ld + kb + lane] = dropc ? 0.f : (s1[0] + s1[1]) + (s1[2] + s1[3]);
+      }
+      // inverse block row: Li[kb + r][j] = -sum_k D^-1[r][k] T[k][j], j < kb;
+      // items: (column block J, 8 rows)
+      const int nitem = P * 4;
+      for (int it = warp; it < nitem; it += kCholWarps) {
+        const int J = it >> 2, r0 = (it & 3) * 8;
+        const int j = (J << 5) + lane;
+        float t[32];
 #pragma unroll
-            for (int cc = 0; cc < 32; ++cc) acc = fmaf(y[cc], dinv[cc < w ? cc : 0], acc);
-            L[i * ld + kb + c] = drop[kb + c] ? 0.f : acc;
+        for (int k = 0; k < 32; ++k) t[k] = Li[j * ld + kb + k];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          const int r = r0 + u;
+          float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            s0[k & 3] = fmaf(Li[(kb + r) * ld + kb + k], t[k], s0[k & 3]);
+            s1[k & 3] = fmaf(Li[(kb + r + 1) * ld + kb + k], t[k], s1[k & 3]);
           }
+          Li[(kb + r) * ld + j] = drop[kb + r] ? 0.f : -((s0[0] + s0[1]) + (s0[2] + s0[3]));
+          Li[(kb + r + 1) * ld + j] = drop[kb + r + 1] ? 0.f : -((s1[0] + s1[1]) + (s1[2] + s1[3]));
         }
       }
     }
     __syncthreads();
-    // trailing update: L[i][j] -= sum_c L[i][kb+c] L[j][kb+c], kb+w <= j <= i;
-    // a thread takes columns jj and m-1-jj (m+1 rows together, so the
-    // threads are balanced) and every P-th row of them
-    if (m > 0) {
-      const int half = (m + 1) / 2;
-      const int P = nt / half > 0 ? nt / half : 1;
-      const int pj = tid % half, ph = tid / half;
-      if (ph < P) {
-        for (int side = 0; side < 2; ++side) {
-          const int jj = side == 0 ? pj : m - 1 - pj;
-          if (side == 1 && jj == pj) break;  // odd m: the middle column once
-          const int j = kb + w + jj;
-          float lj[32];
+    // ---- phase 3: trailing update of the lower block triangle ----
+    const int nr = nbp - P - 1;
+    if (nr > 0) {
+      const int nblk = nr * (nr + 1) / 2;
+      for (int it = warp; it < 4 * nblk; it += kCholWarps) {
+        // block (I, J), I >= J, of the trailing part; quarter h of its rows
+        int blk = it >> 2, I = 0;
+        while (blk > I) {
+          blk -= I + 1;
+          ++I;
+        }
+        const int J = blk, h = it & 3;
+        const int jr = kb + 32 + (J << 5) + lane;  // this lane's column of A
+        float lj[32];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) lj[c] = c < w ? L[j * ld + kb + c] : 0.f;
-          for (int i = j + ph; i < b; i += P) {
-            float acc = 0.f;
+        for (int c = 0; c < 32; ++c) lj[c] = L[jr * ld + kb + c];
+        const int i0 = kb + 32 + (I << 5) + h * 8;
+        for (int i = i0; i < i0 + 8; i += 2) {
+          float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int c = 0; c < 32; ++c) acc += L[i * ld + kb + (c < w ? c : 0)] * lj[c];
-            L[i * ld + j] -= acc;
+          for (int c = 0; c < 32; ++c) {
+            s0[c & 3] = fmaf(L[i * ld + kb + c], lj[c], s0[c & 3]);
+            s1[c & 3] = fmaf(L[(i + 1) * ld + kb + c], lj[c], s1[c & 3]);
           }
+          L[i * ld + jr] -= (s0[0] + s0[1]) + (s0[2] + s0[3]);
+          L[(i + 1) * ld + jr] -= (s1[0] + s1[1]) + (s1[2] + s1[3]);
         }
       }
     }
     __syncthreads();
   }
-  // inverse of the lower factor by block rows (the diagonal blocks D^-1 are
-  // in place): Li[I][J] = -D_I^-1 sum_{K=J}^{I-1} L[I][K] Li[K][J].  Thread
-  // (warp ty, lane tx) owns rows ib+ty, ib+ty+16 and columns tx+32s, s < I.
-  const int nb = (b + 31) / 32;
-  for (int I = 1; I < nb; ++I) {
-    const int ib = I * 32;
-    const int r0 = min(ib + warp, b - 1), r1 = min(ib + warp + 16, b - 1);
-    // T[i][j] = sum_{k < ib} L[i][k] Li[k][j], stashed in the (unused)
-    // upper triangle of Li at [j][i]
-    float acc[2][4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = 0.f;
-    // k by 32-row segments: in segment g the column groups s <= g take part
-    // (Li[k][j] is zero for k < j, and the rows above block s hold earlier
-    // stashes)
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      if (g < I) {
-        for (int k = 32 * g; k < 32 * g + 32; ++k) {
-          const float a0 = L[r0 * ld + k], a1 = L[r1 * ld + k];
-#pragma unroll
-          for (int s = 0; s <= g; ++s) {
-            const float v = Li[k * ld + lane + 32 * s];
-            acc[0][s] = fmaf(a0, v, acc[0][s]);
-            acc[1][s] = fmaf(a1, v, acc[1][s]);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (s < I) {
-        const int j = lane + 32 * s;
-        if (ib + warp < b) Li[j * ld + ib + warp] = acc[0][s];
-        if (ib + warp + 16 < b) Li[j * ld + ib + warp + 16] = acc[1][s];
-      }
-    __syncthreads();
-    // Li[i][j] = -sum_{k in block I} D_I^-1[i][k] T[k][j]
-#pragma unroll
-    for (int s = 0; s < 4; ++s) acc[0][s] = acc[1][s] = 0.f;
-    const int wi = min(32, b - ib);
-    for (int kk = 0; kk < wi; ++kk) {
-      const int k = ib + kk;
-      const float a0 = Li[r0 * ld + k], a1 = Li[r1 * ld + k];
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (s < I) {
-          const float v = Li[(lane + 32 * s) * ld + k];
-          acc[0][s] = fmaf(a0, v, acc[0][s]);
-          acc[1][s] = fmaf(a1, v, acc[1][s]);
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (s < I) {
-        const int j = lane + 32 * s;
-        if (ib + warp < b) Li[(ib + warp) * ld + j] = -acc[0][s];
-        if (ib + warp + 16 < b) Li[(ib + warp + 16) * ld + j] = -acc[1][s];
-      }
-    __syncthreads();
-  }
-  // Rinv = D^-1/2-scaled (L^-1)^T:  M = D^1/2 L L^T D^1/2  =>  with
-  // Q = Y Rinv and Rinv[i][j] = dsc[i] * Li[j][i] = (rsc[i] Li[j][i]) 2^ksc[i]
+  // Rinv = S L^-T with S the unit-diagonal scaling: Rinv[i][j] = dsc[i] Li[j][i]
   double* R = out + pr.out_off;
-  for (int q0 = tid; q0 < bb; q0 += 4 * nt) {
+  for (int q0 = tid; q0 < bb; q0 += 4 * kCholThreads) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int q = q0 + u * nt;
+      const int q = q0 + u * kCholThreads;
       if (q < bb) {
         const int i = q / b, j = q - i * b;
         R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : f32_to_f64_scaled(rsc[i] * Li[j * ld + i], ksc[i]);
@@ -539,9 +576,67 @@ __global__ void __launch_bounds__(512) cholinv_f32(const SmallProb* __restrict__
   }
 }
 
+// Partial Gram matrices in FP32 for the CholQR steps (whose factor is FP32
+// anyway): CTA (p, s) adds x_r^T x_r over the rows r of slice s of problem p
+// (rows [s M / nparts, (s + 1) M / nparts) of the row-major FP64 block X at
+// x_off, row stride ld) and writes the b x b sum to out[out_off + s b^2].
+// 256 threads as 16 x 16: thread (ti, tj) owns entries (ti + 16u, tj + 16v),
+// u, v < 10 (b <= 160); rows are staged in shared memory 32 at a time.
+struct GramProb {
+  int32_t M, b;
+  int64_t x_off, ld, out_off;
+};
+
+constexpr int kGramRows = 32;
+
+__global__ void __launch_bounds__(256) gram_f32_kernel(const GramProb* __restrict__ probs, int nparts,
+                                                       const double* __restrict__ X, float* __restrict__ out) {
+  __shared__ float xs[kGramRows][kEigMax + 4];
+  const GramProb p = probs[blockIdx.x];
+  const int s = blockIdx.y;
+  const int r0 = int((long long)p.M * s / nparts), r1 = int((long long)p.M * (s + 1) / nparts);
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  for (int e = threadIdx.x; e < kGramRows * (kEigMax + 4); e += 256) (&xs[0][0])[e] = 0.f;
+  float acc[10][10];
+#pragma unroll
+  for (int u = 0; u < 10; ++u)
+#pragma unroll
+    for (int v = 0; v < 10; ++v) acc[u][v] = 0.f;
+  for (int rb = r0; rb < r1; rb += kGramRows) {
+    const int nr = min(kGramRows, r1 - rb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * p.b; e += 256) {
+      const int r = e / p.b, c = e - r * p.b;
+      xs[r][c] = float(X[p.x_off + (long long)(rb + r) * p.ld + c]);
+    }
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+      float a[10], c[10];
+#pragma unroll
+      for (int u = 0; u < 10; ++u) {
+        a[u] = xs[r][ti + 16 * u];
+        c[u] = xs[r][tj + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 10; ++u)
+#pragma unroll
+        for (int v = 0; v < 10; ++v) acc[u][v] = fmaf(a[u], c[v], acc[u][v]);
+    }
+  }
+  float* o = out + p.out_off + (long long)s * p.b * p.b;
+#pragma unroll
+  for (int u = 0; u < 10; ++u)
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+      const int i = ti + 16 * u, j = tj + 16 * v;
+      if (i < p.b && j < p.b) o[i * p.b + j] = acc[u][v];
+    }
+}
+
 size_t cholinv_smem(int b) {
-  // L, Li (b x (b+1) floats), rsc (b floats), drop (b ints), ksc (b ints)
-  return sizeof(float) * (2 * b * (b + 1) + 3 * b);
+  // L, Li (bp x (bp + 1) floats), rsc (bp floats), ksc and drop (bp ints each)
+  const int bp = (b + 31) & ~31;
+  return sizeof(float) * (2 * size_t(bp) * (bp + 1) + 3 * size_t(bp));
 }
 
 // out = alpha * I + beta * in (square blocks)

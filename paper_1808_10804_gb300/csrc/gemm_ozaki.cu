@@ -53,6 +53,22 @@ struct Prob {
   int32_t M, N, K, pad;
   int32_t arow, brow;  // first row of this problem in the split A / B buffers
   int64_t c_off, c_m, c_n;
+  // output scatter (scatter != 0): element (m, n) of the problem goes to
+  // C[bbase[bb_off + r ncc + c] + mi w + ni] with (r, mi) = rowtab[rt_off + m]
+  // and (c, ni, w) = coltab[ct_off + n]: the canonical block (r, c) of the
+  // output tensor, row-major [rows of config r x w], instead of a strided
+  // sector matrix
+  int32_t scatter, ncc;
+  int64_t rt_off, ct_off, bb_off;
+};
+
+// Output scatter tables of a plan (device pointers; all null for a plain
+// strided output) and the epilogue's C = alpha * A B + beta * C.
+struct Scatter {
+  const int2* rowtab;
+  const int4* coltab;
+  const long long* bbase;
+  double alpha, beta;
 };
 
 struct Tile {
@@ -190,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       const Prob* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
                       const int* __restrict__ expA, const int* __restrict__ expB, int rowsA, int rowsB,
-                      double* __restrict__ C, int* err) {
+                      double* __restrict__ C, const Scatter sc, int* err) {
   extern __shared__ uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -380,13 +396,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int gm = t.m0 + row;
       const bool row_ok = gm < p.M;
       const int ea = row_ok ? expA[p.arow + gm] : 0;
-      double* crow = C + p.c_off + (long long)gm * p.c_m;
+      if (p.scatter) {
+        // straight into the output tensor's canonical blocks: this row's
+        // block row r and row mi inside it; the columns' block, column and
+        // block width are the same for every lane (broadcast loads)
+        const int2 ri = row_ok ? sc.rowtab[p.rt_off + gm] : make_int2(0, 0);
+        const long long* bb = sc.bbase + p.bb_off + (long long)ri.x * p.ncc;
+        const bool plain = sc.alpha == 1.0 && sc.beta == 0.0;
 #pragma unroll
-      for (int jj = 0; jj < kHalf; ++jj) {
-        const int gn = t.n0 + c0 + jj;
-        if (row_ok && gn < p.N) {
-          const int e = ea + expB[p.brow + gn] - 43;
-          crow[(long long)gn * p.c_n] = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
+        for (int jj = 0; jj < kHalf; ++jj) {
+          const int gn = t.n0 + c0 + jj;
+          if (row_ok && gn < p.N) {
+            const int4 ci = sc.coltab[p.ct_off + gn];
+            const long long dst = bb[ci.x] + (long long)ri.y * ci.z + ci.y;
+            const int e = ea + expB[p.brow + gn] - 43;
+            const double v = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
+            if (plain) C[dst] = v;
+            else C[dst] = sc.beta == 0.0 ? sc.alpha * v : fma(sc.alpha, v, sc.beta * C[dst]);
+          }
+        }
+      } else {
+        double* crow = C + p.c_off + (long long)gm * p.c_m;
+#pragma unroll
+        for (int jj = 0; jj < kHalf; ++jj) {
+          const int gn = t.n0 + c0 + jj;
+          if (row_ok && gn < p.N) {
+            const int e = ea + expB[p.brow + gn] - 43;
+            crow[(long long)gn * p.c_n] = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
+          }
         }
       }
     }
@@ -542,7 +579,19 @@ struct OzakiPlan {
   // the CTA's mbarrier phases in step)
   GemmProb* d_zprobs = nullptr;
   int nzprobs = 0;
+  // output scatter into canonical blocks (plans built by
+  // ozaki_prepare_scatter): tables on the device, K == 0 problems listed
+  // by index for the beta-only pass
+  int2* d_rowtab = nullptr;
+  int4* d_coltab = nullptr;
+  long long* d_bbase = nullptr;
+  int* d_zidx = nullptr;
+  bool scatter = false;
   ~OzakiPlan() {
+    cudaFree(d_rowtab);
+    cudaFree(d_coltab);
+    cudaFree(d_bbase);
+    cudaFree(d_zidx);
     cudaFree(d_probs);
     cudaFree(d_tiles);
     cudaFree(d_sa);
@@ -579,7 +628,16 @@ static int num_sms() {
 // 0 problem order, row tiles outer; 1 longest K first (the tiles that take
 // longest start first, so the last wave is short); 2 problem order, column
 // tiles outer (CTAs that run together share B slices in L2).
-static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int order = 0) {
+struct ScatterSpec {
+  std::vector<int2> rowtab;
+  std::vector<int4> coltab;
+  std::vector<long long> bbase;
+  std::vector<int64_t> rt_off, ct_off, bb_off;  // per problem
+  std::vector<int32_t> ncc;                     // per problem
+};
+
+static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int order = 0,
+                             const ScatterSpec* sc = nullptr) {
   auto* P = new OzakiPlan();
   std::vector<oz::Prob> hp;
   std::vector<oz::Tile> ht;
@@ -603,6 +661,14 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
     q.c_off = g.c_off;
     q.c_m = g.c_m;
     q.c_n = g.c_n;
+    if (sc) {
+      const size_t pi = hp.size();
+      q.scatter = 1;
+      q.ncc = sc->ncc[pi];
+      q.rt_off = sc->rt_off[pi];
+      q.ct_off = sc->ct_off[pi];
+      q.bb_off = sc->bb_off[pi];
+    }
     sa.push_back({g.M, g.K, P->rowsA, 0, g.a_off, g.a_m, g.a_k});
     sb.push_back({g.N, g.K, P->rowsB, 0, g.b_off, g.b_n, g.b_k});
     P->rowsA += g.M;
@@ -642,6 +708,16 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   P->nzprobs = int(zp.size());
   up(&P->d_sa, sa);
   up(&P->d_sb, sb);
+  if (sc) {
+    P->scatter = true;
+    up(&P->d_rowtab, sc->rowtab);
+    up(&P->d_coltab, sc->coltab);
+    up(&P->d_bbase, sc->bbase);
+    std::vector<int> zi;
+    for (int i = 0; i < int(hp.size()); ++i)
+      if (hp[i].K == 0) zi.push_back(i);
+    up(&P->d_zidx, zi);
+  }
   // split buffers: 5 slices x rows x kpitch BF16, with room for a full tile
   // past the end so TMA boxes of the last rows stay inside the allocation
   const int64_t ra = int64_t(oz::kSlices) * std::max(P->rowsA, 1) + oz::kTM;
@@ -664,10 +740,30 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   return P;
 }
 
+// Scatter plans: the output blocks of K == 0 problems (no matched block
+// pair) become beta * C (0 for beta == 0), through the same tables as the
+// GEMM epilogue.
+__global__ void zero_scatter_kernel(const oz::Prob* __restrict__ probs, const int* __restrict__ zidx,
+                                    const oz::Scatter sc, double* __restrict__ C) {
+  const oz::Prob p = probs[zidx[blockIdx.y]];
+  const long long n = (long long)p.M * p.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int m = int(e / p.N), c = int(e - (long long)m * p.N);
+    const int2 ri = sc.rowtab[p.rt_off + m];
+    const int4 ci = sc.coltab[p.ct_off + c];
+    const long long dst = sc.bbase[p.bb_off + (long long)ri.x * p.ncc + ci.x] + (long long)ri.y * ci.z + ci.y;
+    C[dst] = sc.beta == 0.0 ? 0.0 : sc.beta * C[dst];
+  }
+}
+
 static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s,
-                     bool split_a = true) {
+                     bool split_a = true, double alpha = 1.0, double beta = 0.0) {
+  const oz::Scatter sc{P->d_rowtab, P->d_coltab, P->d_bbase, alpha, beta};
   if (P->nzprobs) {
-    zero_probs_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_zprobs, C);
+    if (P->scatter)
+      zero_scatter_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_probs, P->d_zidx, sc, C);
+    else
+      zero_probs_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_zprobs, C);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
@@ -689,12 +785,62 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
   const int grid = std::min(P->ntiles, num_sms());
   oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(
       P->mapA, b_from_a ? P->mapBA : P->mapB, P->d_probs, P->d_tiles, P->ntiles, P->eA, b_from_a ? P->eA : P->eB,
-      P->rowsA, P->rowsB, C, ctx->d_err);
+      P->rowsA, P->rowsB, C, sc, ctx->d_err);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
 }
 
 void ozaki_prepare(Ctx* ctx, ContractPlan* p) { p->oz = build_plan(ctx, p->probs); }
+
+// Plan whose epilogue writes every product element into the output
+// tensor's canonical block (Sec. 2: the reduced pair products land in the
+// output block of their output quantum numbers).  C's legs are A's open
+// legs then B's, so the block of (row config r, column config c) is a
+// row-major [rows of r x columns of c] matrix: element (m, n) of a sector
+// goes to offset(r, c) + mi * width(c) + ni.
+void ozaki_prepare_scatter(Ctx* ctx, ContractPlan* p) {
+  ScatterSpec sc;
+  const Layout* C = p->C;
+  std::vector<int32_t> tup(C->rank);
+  size_t pi = 0;
+  for (auto& cs : p->vc.secs) {
+    if (!(cs.rows > 0 && cs.cols > 0)) continue;
+    BST_REQUIRE(pi < p->probs.size() && p->probs[pi].M == cs.rows && p->probs[pi].N == cs.cols, BST_E_SHAPE,
+                "scatter plan: problem list does not follow the output sectors");
+    sc.rt_off.push_back(int64_t(sc.rowtab.size()));
+    sc.ct_off.push_back(int64_t(sc.coltab.size()));
+    sc.bb_off.push_back(int64_t(sc.bbase.size()));
+    sc.ncc.push_back(int32_t(cs.ccfg.size()));
+    std::vector<int64_t> width(cs.ccfg.size());
+    for (size_t c = 0; c < cs.ccfg.size(); ++c) {
+      const int64_t w = (c + 1 < cs.ccfg.size() ? cs.coff[c + 1] : cs.cols) - cs.coff[c];
+      width[c] = w;
+      for (int64_t ni = 0; ni < w; ++ni) sc.coltab.push_back(make_int4(int(c), int(ni), int(w), 0));
+    }
+    for (size_t r = 0; r < cs.rcfg.size(); ++r) {
+      const int64_t h = (r + 1 < cs.rcfg.size() ? cs.roff[r + 1] : cs.rows) - cs.roff[r];
+      for (int64_t mi = 0; mi < h; ++mi) sc.rowtab.push_back(make_int2(int(r), int(mi)));
+      for (size_t c = 0; c < cs.ccfg.size(); ++c) {
+        size_t k = 0;
+        for (int32_t x : cs.rcfg[r]) tup[k++] = x;
+        for (int32_t x : cs.ccfg[c]) tup[k++] = x;
+        const int64_t b = C->block_of(tup.data());
+        BST_REQUIRE(b >= 0, BST_E_SHAPE, "scatter plan: missing output block");
+        sc.bbase.push_back((long long)C->offset[b]);
+      }
+    }
+    ++pi;
+  }
+  BST_REQUIRE(pi == p->probs.size(), BST_E_SHAPE, "scatter plan: problem count mismatch");
+  BST_REQUIRE(sc.rowtab.size() < (size_t(1) << 31) && sc.coltab.size() < (size_t(1) << 31), BST_E_UNSUPPORTED,
+              "scatter plan: too many rows");
+  p->ozs = build_plan(ctx, p->probs, 0, &sc);
+}
+
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* c,
+                            double alpha, double beta, cudaStream_t s) {
+  run_plan(ctx, p->ozs, Amat, Bmat, c, s, true, alpha, beta);
+}
 
 void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
                     cudaStream_t s) {

@@ -1,7 +1,7 @@
-// Canonical block layouts of U(1)-symmetric tensors (Sec. 2).
+// Canonical block layouts of U(1)- and Z2-symmetric tensors (Sec. 2).
 //
 // A block is one sector per leg; it is allowed iff sum_i flow_i q_i = 0
-// (no global charge shift, Sec. 2).  Blocks are kept in lexicographic order
+// (no global charge shift, Sec. 2), for Z2 modulo 2.  Blocks are kept in lexicographic order
 // of their per-leg sector indices (leg 0 most significant), each stored
 // dense row-major, back to back.  Layouts are interned per context by their
 // structure, so equal structures are the same object and plans keyed by
@@ -45,8 +45,24 @@ static std::string layout_key(int group, const std::vector<Leg>& legs) {
 
 // Depth-first enumeration of allowed sector tuples in lexicographic order,
 // pruned with the reachable range of the remaining partial sums.
-static void enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& out) {
+static void enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& out, int group) {
   const int r = int(legs.size());
+  if (group == BST_Z2) {
+    // parities: every tuple whose charges add up to an even number
+    std::vector<int32_t> cur(r);
+    std::function<void(int, int64_t)> rec = [&](int i, int64_t sum) {
+      if (i == r) {
+        if (cnorm(group, sum) == 0) out.insert(out.end(), cur.begin(), cur.end());
+        return;
+      }
+      for (int s = 0; s < int(legs[i].q.size()); ++s) {
+        cur[i] = s;
+        rec(i + 1, sum + legs[i].q[s]);
+      }
+    };
+    rec(0, 0);
+    return;
+  }
   std::vector<int64_t> lo(r + 1, 0), hi(r + 1, 0);
   for (int i = r - 1; i >= 0; --i) {
     int64_t a = int64_t(legs[i].flow) * legs[i].q.front();
@@ -70,7 +86,8 @@ static void enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& out)
 }
 
 Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
-  BST_REQUIRE(group == BST_U1 || group == BST_SU2, BST_E_ARG, "group must be BST_U1 or BST_SU2");
+  BST_REQUIRE(group == BST_U1 || group == BST_SU2 || group == BST_Z2, BST_E_ARG,
+              "group must be BST_U1, BST_SU2 or BST_Z2");
   BST_REQUIRE(!legs_in.empty() && legs_in.size() <= kMaxRank, BST_E_ARG, "rank must be 1..8");
   std::vector<Leg> legs = legs_in;
   for (auto& l : legs) {
@@ -81,6 +98,7 @@ Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
       BST_REQUIRE(l.d[i] > 0, BST_E_ARG, "degeneracies must be positive");
       if (i) BST_REQUIRE(l.q[i] > l.q[i - 1], BST_E_ARG, "charges must be strictly ascending");
       if (group == BST_SU2) BST_REQUIRE(l.q[i] >= 0 && l.q[i] <= 64, BST_E_ARG, "SU(2) labels 2j must be 0..64");
+      if (group == BST_Z2) BST_REQUIRE(l.q[i] == 0 || l.q[i] == 1, BST_E_ARG, "Z2 charges must be 0 or 1");
     }
     l.finish();
   }
@@ -102,7 +120,7 @@ Layout* make_layout(Ctx* ctx, int group, const std::vector<Leg>& legs_in) {
     L->ntree = su2_ntree(legs);
     su2_enum_blocks(legs, L->sect, L->tree);
   } else {
-    enum_blocks(legs, L->sect);
+    enum_blocks(legs, L->sect, group);
   }
   L->nblocks = int64_t(L->sect.size()) / L->rank;
   L->offset.resize(L->nblocks);
@@ -136,12 +154,28 @@ void release(Layout* l) {
   if (--l->refs == 0) delete l;
 }
 
-std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& legs, int64_t target) {
-  // all sector tuples over `legs` with sum_i flow_i q_i == target, lexicographic
+std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& legs, int64_t target, int group) {
+  // all sector tuples over `legs` with sum_i flow_i q_i == target (Z2: of the
+  // same parity), lexicographic
   std::vector<std::vector<int32_t>> out;
   const int r = int(legs.size());
   if (r == 0) {
-    if (target == 0) out.push_back({});
+    if (cnorm(group, target) == 0) out.push_back({});
+    return out;
+  }
+  if (group == BST_Z2) {
+    std::vector<int32_t> cur(r);
+    std::function<void(int, int64_t)> rec = [&](int i, int64_t sum) {
+      if (i == r) {
+        if (cnorm(group, sum - target) == 0) out.push_back(cur);
+        return;
+      }
+      for (int s = 0; s < int(legs[i]->q.size()); ++s) {
+        cur[i] = s;
+        rec(i + 1, sum + legs[i]->q[s]);
+      }
+    };
+    rec(0, 0);
     return out;
   }
   std::vector<int64_t> lo(r + 1, 0), hi(r + 1, 0);
@@ -168,15 +202,16 @@ std::vector<std::vector<int32_t>> enum_configs(const std::vector<const Leg*>& le
 }
 
 // Fused leg (Sec. 3.2, merging legs): flow of the first member, charge
-// flow_0 * sum_i flow_i q_i, sectors ascending, member tuples ascending
-// lexicographically inside a sector, inner index row-major over members.
-Leg fuse_legs(const std::vector<Leg>& legs, std::vector<std::vector<int32_t>>* tuples) {
+// flow_0 * sum_i flow_i q_i (Z2: its parity), sectors ascending, member
+// tuples ascending lexicographically inside a sector, inner index row-major
+// over members.
+Leg fuse_legs(const std::vector<Leg>& legs, std::vector<std::vector<int32_t>>* tuples, int group) {
   const int f0 = legs[0].flow;
   std::map<int64_t, std::vector<std::vector<int32_t>>> byq;
   std::vector<int32_t> cur(legs.size());
   std::function<void(size_t, int64_t)> rec = [&](size_t i, int64_t sum) {
     if (i == legs.size()) {
-      byq[sum * f0].push_back(cur);
+      byq[cnorm(group, sum * f0)].push_back(cur);
       return;
     }
     for (int s = 0; s < int(legs[i].q.size()); ++s) {

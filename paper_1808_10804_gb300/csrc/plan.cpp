@@ -31,14 +31,14 @@ MatView make_matview(const Layout* L, const std::vector<int>& rowlegs, const std
   for (int64_t b = 0; b < L->nblocks; ++b) {
     int64_t k = 0;
     for (int i : collegs) k += int64_t(L->legs[i].flow) * L->legs[i].q[L->sect[b * L->rank + i]];
-    keys[k] = true;
+    keys[cnorm(L->group, k)] = true;
   }
   int64_t off = 0;
   for (auto& kv : keys) {
     MatSector s;
     s.key = kv.first;
-    s.rcfg = enum_configs(rl, -s.key);
-    s.ccfg = enum_configs(cl, s.key);
+    s.rcfg = enum_configs(rl, -s.key, L->group);
+    s.ccfg = enum_configs(cl, s.key, L->group);
     for (auto& t : s.rcfg) {
       int64_t n = 1;
       for (size_t j = 0; j < t.size(); ++j) n *= rl[j]->d[t[j]];
@@ -73,6 +73,7 @@ MatView make_matview(const Layout* L, const std::vector<int>& rowlegs, const std
     int64_t k = 0;
     std::vector<int32_t> rt, ct;
     for (int i : collegs) k += int64_t(L->legs[i].flow) * L->legs[i].q[sb[i]];
+    k = cnorm(L->group, k);
     for (int i : rowlegs) rt.push_back(sb[i]);
     for (int i : collegs) ct.push_back(sb[i]);
     const MatSector& s = v.secs[v.by_key.at(k)];
@@ -111,6 +112,7 @@ ContractPlan::~ContractPlan() {
   rc.free_all();
   g.free_all();
   if (oz) ozaki_free(oz);
+  if (ozs) ozaki_free(ozs);
   release(A);
   release(B);
   release(C);
@@ -119,6 +121,7 @@ ContractPlan::~ContractPlan() {
 static Layout* contract_out_layout(Ctx* ctx, Layout* A, Layout* B, const std::vector<int>& la,
                                    const std::vector<int>& lb, std::vector<int>* oa, std::vector<int>* ob) {
   BST_REQUIRE(la.size() == lb.size(), BST_E_ARG, "leg pair lists differ in length");
+  BST_REQUIRE(A->group == B->group, BST_E_ARG, "A and B belong to different symmetry groups");
   std::vector<bool> ua(A->rank, false), ub(B->rank, false);
   for (size_t i = 0; i < la.size(); ++i) {
     BST_REQUIRE(la[i] >= 0 && la[i] < A->rank && lb[i] >= 0 && lb[i] < B->rank, BST_E_ARG,
@@ -165,7 +168,7 @@ ContractPlan* get_contract_plan(Ctx* ctx, Layout* A, Layout* B, const std::vecto
   // one GEMM per C sector: A sector key s pairs with B sector key -s
   for (auto& cs : p->vc.secs) {
     const MatSector* as = p->va.find(cs.key);
-    const MatSector* bs = p->vb.find(-cs.key);
+    const MatSector* bs = p->vb.find(cnorm(A->group, -cs.key));
     GemmProb g{};
     g.M = int32_t(cs.rows);
     g.N = int32_t(cs.cols);
@@ -200,11 +203,17 @@ void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, b
                   double beta, double* c, cudaStream_t s, bool scatter, double** cmat_out) {
   double* Am = (double*)ctx->buf("contract.A", sizeof(double) * std::max<int64_t>(p->amat, 1), s);
   double* Bm = (double*)ctx->buf("contract.B", sizeof(double) * std::max<int64_t>(p->bmat, 1), s);
-  double* Cm = (double*)ctx->buf(cmat_out ? "contract.Ckeep" : "contract.C",
-                                 sizeof(double) * std::max<int64_t>(p->cmat, 1), s);
   ctx->work_flops += p->g.flops;
   launch_relayout(ctx, p->ra, a, Am, 0, 1.0, 0.0, s);
   launch_relayout(ctx, p->rb, b, Bm, 0, 1.0, 0.0, s);
+  if (prec != BST_FP64 && scatter && !cmat_out) {
+    // the tensor-core GEMM's epilogue writes C's blocks directly
+    if (!p->ozs) ozaki_prepare_scatter(ctx, p);
+    run_gemm_ozaki_scatter(ctx, p, Am, Bm, c, alpha, beta, s);
+    return;
+  }
+  double* Cm = (double*)ctx->buf(cmat_out ? "contract.Ckeep" : "contract.C",
+                                 sizeof(double) * std::max<int64_t>(p->cmat, 1), s);
   if (prec == BST_FP64) {
     launch_gemm_f64(ctx, p->g, Am, Bm, Cm, s);
   } else {
@@ -283,7 +292,7 @@ DevRelayout* get_fuse_plan(Ctx* ctx, Layout* src, const std::vector<int>& groups
   for (int g = 0; g < ng; ++g) {
     std::vector<Leg> mem(src->legs.begin() + first, src->legs.begin() + first + groups[g]);
     std::vector<std::vector<int32_t>> tuples;
-    fl[g] = fuse_legs(mem, &tuples);
+    fl[g] = fuse_legs(mem, &tuples, src->group);
     size_t ti = 0;
     for (size_t s = 0; s < fl[g].q.size(); ++s) {
       int64_t acc = 0;

@@ -118,7 +118,12 @@ struct ResProb {
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
 __global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double);
 __global__ void add_inplace(double*, const double*, long long);
-__global__ void cholinv_f32(const SmallProb*, const double*, double*, int*);
+__global__ void cholinv_f32(const SmallProb*, const double*, double*, int*, const float*, int);
+struct GramProb {
+  int32_t M, b;
+  int64_t x_off, ld, out_off;
+};
+__global__ void gram_f32_kernel(const GramProb*, int, const double*, float*);
 __global__ void ident_combo(const SmallProb*, const double*, double*, double, double);
 __global__ void randn_fill(double*, long long, uint64_t);
 __global__ void ritz_residual(const ResProb*, const double*, const double*, const double*, double*);
@@ -221,6 +226,9 @@ static T* upload_cached(Ctx* ctx, const std::string& name, const std::vector<T>&
   return d;
 }
 
+struct PSec;
+static bool cut_unresolved(const PSec& x, const std::vector<double>& hSig, double kmin);
+
 struct PSec {
   const MatSector *cs, *as, *bs;
   int M, N;        // N_s is M x N (rows: right cut of Rt, cols: right cut of Rb)
@@ -232,6 +240,18 @@ struct PSec {
   int64_t q_off, z_off, sm_off, val_off;
   int64_t kmax;    // most states the truncation can keep from this sector (0: chi)
 };
+
+// The small eigensolver resolves a sector's eigenvalues of N^T N below
+// 1e-6 of its largest only to ~1e-9 of the largest (one unresolved
+// cluster): singular values below sqrt(1e-5) of the sector's largest (a
+// tenfold margin) cannot decide the truncation.  True when the smallest
+// kept value kmin falls in that range of a sector that has values above
+// it: the candidates are then recomputed by the full FP64 SVD.
+static bool cut_unresolved(const PSec& x, const std::vector<double>& hSig, double kmin) {
+  if (x.c <= 0) return false;
+  const double top = hSig[x.s_off];  // candidates are sorted descending
+  return top > kmin && kmin * kmin < 1e-5 * top * top;
+}
 
 static void setup_attrs() {
   static bool done = false;
@@ -252,8 +272,14 @@ static void setup_attrs() {
 // are treated as one unresolved cluster.  `pre` prefixes every workspace,
 // plan and table name, so calls with different prefixes may run on
 // different streams at the same time.
+// near_diag: H is already close to diagonal (the Rayleigh-Ritz matrix of a
+// block from orthogonal iteration: CholQR keeps the columns in the order of
+// the singular values they converge to, so only close pairs still mix); the
+// first, absolute Jacobi pass and the rotation into its basis are skipped
+// and the relative pass starts from H itself.
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
-                      int64_t smtot, int64_t valtot, cudaStream_t s, const std::string& pre = "") {
+                      int64_t smtot, int64_t valtot, cudaStream_t s, const std::string& pre = "",
+                      bool near_diag = false) {
   if (sp.empty()) return;
   setup_attrs();
   SmallProb* dsp = upload_cached(ctx, pre + "eig.sp", sp, s);
@@ -280,21 +306,28 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   // rounds of b/2 rotations, each touching 2 rows and 2 columns of A and V
   double jac_flops = 0;
   for (auto& p : sp) jac_flops += 7.0 * double(p.b) * p.b * 18.0 * p.b / 2.0;
-  {
+  if (near_diag) {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 10, 1e-5f, 0.f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
+  } else {
+    {
+      ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
+      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
+    gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X1, T, s, false, ws);
+    gemm_any(ctx, pre + "oa.s", prec, g_s, X1, T, H1, s, false, ws);
+    {
+      ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
+      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
+    gemm_any(ctx, pre + "oa.xe", prec, g_xe, X1, T, X, s, false, ws);  // X = X1 X2
   }
-  gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X1, T, s, false, ws);
-  gemm_any(ctx, pre + "oa.s", prec, g_s, X1, T, H1, s, false, ws);
-  {
-    ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f);
-    BST_CUDA(cudaGetLastError());
-    count_launch(ctx);
-  }
-  gemm_any(ctx, pre + "oa.xe", prec, g_xe, X1, T, X, s, false, ws);  // X = X1 X2
   for (int it = 0; it < 2; ++it) {
     gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
     gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
@@ -400,9 +433,41 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   for (auto& x : secs) bmax = std::max(bmax, x.b);
   double chol_flops = 0;
   for (auto& x : sp_it) chol_flops += 2.0 * 2.0 * double(x.b) * x.b * x.b / 3.0;  // factor + inverse, FMA = 2
-  auto cholinv = [&]() {
+  // CholQR of a block X (rows of every iterated sector at its q_off or z_off,
+  // row stride b): the Gram matrix only feeds the FP32 factor, so it is
+  // formed in FP32 by K-sliced partial sums (gram_f32_kernel, all SMs),
+  // which the Cholesky kernel adds in slice order while it loads
+  std::vector<SmallProb> sp_g;
+  std::vector<GramProb> gq, gz;
+  int64_t gtot = 0;
+  int nparts = 1;
+  if (!sp_it.empty()) {
+    nparts = int(std::max<int64_t>(1, std::min<int64_t>(16, (152 + int64_t(sp_it.size()) - 1) / int64_t(sp_it.size()))));
+    for (auto& x : secs) {
+      if (x.direct) continue;
+      sp_g.push_back(SmallProb{x.b, 0, gtot, x.sm_off, x.val_off});
+      gq.push_back(GramProb{x.N, x.b, x.q_off, x.b, gtot});
+      gz.push_back(GramProb{x.M, x.b, x.z_off, x.b, gtot});
+      gtot += int64_t(nparts) * x.b * x.b;
+    }
+  }
+  SmallProb* dsp_g = sp_g.empty() ? nullptr : upload_cached(ctx, "proj.spg", sp_g, s);
+  GramProb* dgq = gq.empty() ? nullptr : upload_cached(ctx, "proj.gq", gq, s);
+  GramProb* dgz = gz.empty() ? nullptr : upload_cached(ctx, "proj.gz", gz, s);
+  float* Gp = (float*)ctx->buf("proj.gparts", sizeof(float) * std::max<int64_t>(gtot, 1), s);
+  double gram_flops = 0;
+  for (auto& x : secs)
+    if (!x.direct) gram_flops += 2.0 * double(std::max(x.M, x.N)) * x.b * x.b;
+  auto cholqr_factor = [&](const double* X, bool z_side) {
+    {
+      ProfScope ps(ctx, s, "gram_f32", gram_flops, 0.0);
+      gram_f32_kernel<<<dim3(unsigned(sp_g.size()), unsigned(nparts)), 256, 0, s>>>(z_side ? dgz : dgq, nparts, X,
+                                                                                   Gp);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
     ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
-    cholinv_f32<<<int(sp_it.size()), 512, cholinv_smem(bmax), s>>>(dsp_it, Msm, Rinv, ctx->d_err);
+    cholinv_f32<<<int(sp_g.size()), 512, cholinv_smem(bmax), s>>>(dsp_g, Msm, Rinv, ctx->d_err, Gp, nparts);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   };
@@ -414,20 +479,17 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   auto iterate = [&](int n) {
     for (int t = 0; t < n; ++t) {
       gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s, n_split);
-      gemm_any(ctx, "ss.gz", prec, g_gz, Z, Z, Msm, s);
-      cholinv();
+      cholqr_factor(Z, true);
       gemm_any(ctx, "ss.qz", prec, g_qz, Z, Rinv, Z2, s);
       gemm_any(ctx, "ss.y", prec, g_y, Nm, Z2, Y, s, n_split);
       n_split = true;
-      gemm_any(ctx, "ss.gy", prec, g_gy, Y, Y, Msm, s);
-      cholinv();
+      cholqr_factor(Y, false);
       gemm_any(ctx, "ss.qy", prec, g_qy, Y, Rinv, Q, s);
     }
   };
   // second CholQR pass and two first-order polishes: orthonormal to FP64
   auto orthonormalise = [&]() {
-    gemm_any(ctx, "ss.gy", prec, g_gy, Q, Q, Msm, s);
-    cholinv();
+    cholqr_factor(Q, false);
     gemm_any(ctx, "ss.qy", prec, g_qy, Q, Rinv, Y, s);
     for (int r = 0; r < 2; ++r) {
       double* src = (r == 0) ? Y : Q;
@@ -541,7 +603,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       gemm_any(ctx, "ss.zrr", rrp, g_z, Nm, Q, Z, s);
       gemm_any(ctx, "ss.h", rrp, g_h, Z, Z, Msm, s);
     }
-    small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s);
+    small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s, "", ctx->rr_near_diag);
     // V = Q W (iterative) or W (direct, once the second stream is joined)
     if (!g_v.empty()) gemm_any(ctx, "ss.v", rrp, g_v, Q, Xv, dV, s);
     if (forked) {
@@ -805,7 +867,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   std::vector<PSec> secs;
   for (auto& cs : pn->vc.secs) {
     const MatSector* as = pn->va.find(cs.key);
-    const MatSector* bs = pn->vb.find(-cs.key);
+    const MatSector* bs = pn->vb.find(cnorm(Rt->group, -cs.key));
     if (!as || !bs || as->cols == 0 || cs.rows == 0 || cs.cols == 0) continue;
     PSec x{};
     x.cs = &cs;
@@ -908,7 +970,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
       for (int j = 0; j < secs[i].c; ++j) {
         const double v = hSig[secs[i].s_off + j];
         BST_REQUIRE(std::isfinite(v), BST_E_NUMERIC, "projector: non-finite singular value");
-        cand.push_back({v, int(new_flow * secs[i].cs->key), int(i), j});
+        cand.push_back({v, int(cnorm(Rt->group, new_flow * secs[i].cs->key)), int(i), j});
         smax = std::max(smax, v);
         ssum += v;
       }
@@ -936,14 +998,17 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
         BST_REQUIRE(hSig[secs[i].s_off + j] <= hSig[secs[i].s_off + j - 1], BST_E_NUMERIC, "projector: unsorted");
     bool edge = false;
     if (done)
-      for (size_t i = 0; i < secs.size(); ++i) edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c);
+      for (size_t i = 0; i < secs.size(); ++i)
+        edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c) || cut_unresolved(secs[i], hSig, kmin);
     if (!edge) break;
+    if (ctx->tune_log.size() < (1u << 20))
+      ctx->tune_log += "projector: truncation outside the resolved candidates, full SVD\n";
     use_subspace = false;
   }
 
   std::vector<std::pair<int, int>> order;  // (charge, sec)
   for (size_t i = 0; i < secs.size(); ++i)
-    if (kcount[i] > 0) order.push_back({int(new_flow * secs[i].cs->key), int(i)});
+    if (kcount[i] > 0) order.push_back({int(cnorm(Rt->group, new_flow * secs[i].cs->key)), int(i)});
   std::sort(order.begin(), order.end());
   Leg nl;
   nl.flow = new_flow;
@@ -1244,7 +1309,8 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     BST_REQUIRE(kept > 0, BST_E_NUMERIC, "projector: nothing kept");
     bool edge = false;
     if (done)
-      for (size_t i = 0; i < secs.size(); ++i) edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c);
+      for (size_t i = 0; i < secs.size(); ++i)
+        edge = edge || (!secs[i].direct && kcount[i] + 16 > secs[i].c) || cut_unresolved(secs[i], hSig, kmin);
     if (!edge) break;
     use_subspace = false;
   }

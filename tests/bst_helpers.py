@@ -76,3 +76,21 @@ def check_blocks(legs, got, want, tol, own_tol, floor=1e-3):
         worst_t, worst_o = max(worst_t, rt), max(worst_o, ro)
         assert rt < tol and ro < own_tol, (i, rt, ro, n / tn)
     return worst_t, worst_o
+
+
+def matched_pair_flops(a_legs, la, b_legs, lb):
+    """2 M K N summed over every pair of allowed blocks of A and B that agree
+    on the contracted legs (Sec. 2's block-pair contraction), enumerated
+    from the oracle's block lists."""
+    tot = 0
+    bb = u1.blocks(b_legs)
+    for x in u1.blocks(a_legs):
+        for y in bb:
+            if all(a_legs[i].charges[x[i]] == b_legs[j].charges[y[j]] for i, j in zip(la, lb)):
+                sa = [a_legs[i].degs[x[i]] for i in range(len(a_legs))]
+                sb = [b_legs[j].degs[y[j]] for j in range(len(b_legs))]
+                k = int(np.prod([sa[i] for i in la]))
+                m = int(np.prod([sa[i] for i in range(len(sa)) if i not in la]))
+                n = int(np.prod([sb[j] for j in range(len(sb)) if j not in lb]))
+                tot += 2 * m * k * n
+    return tot

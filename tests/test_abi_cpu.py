@@ -90,3 +90,23 @@ def test_batched_call_checks_and_tuning_switch(hctx):
     hctx.set_autotune(False)
     hctx.set_autotune(True)
     assert hctx.tuning_log() == ""
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_contract_flops_counts_matched_block_pairs(hctx, seed):
+    """bst_contract_flops plans on the host (no device) and reports 2 M K N
+    over the matched block pairs, enumerated independently from the
+    oracle's block lists."""
+    from bst_helpers import matched_pair_flops
+    rng = np.random.default_rng(900 + seed)
+
+    def leg(flow):
+        qs = sorted(rng.choice(np.arange(-3, 4), size=int(rng.integers(1, 4)), replace=False))
+        return u1.Leg(flow, tuple(int(q) for q in qs), tuple(int(d) for d in rng.integers(1, 6, size=len(qs))))
+    s0, s1 = leg(1), leg(-1)
+    a_legs = [leg(1), s0, leg(-1), s1]
+    b_legs = [s1.dual(), leg(1), s0.dual()]
+    A = hctx.layout([bst.Leg(l.flow, l.charges, l.degs) for l in a_legs])
+    B = hctx.layout([bst.Leg(l.flow, l.charges, l.degs) for l in b_legs])
+    f = hctx.contract_flops(A, B, [1, 3], [2, 0])
+    assert f == matched_pair_flops(a_legs, [1, 3], b_legs, [2, 0])

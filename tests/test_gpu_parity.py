@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 from oracle import ctm as octm  # noqa: E402
 from oracle import u1  # noqa: E402
 from workloads import u1_config, values  # noqa: E402
-from bst_helpers import check_blocks, gpu_network, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
+from bst_helpers import check_blocks, gpu_network, matched_pair_flops, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
 
 TOL64 = 1e-12
 
@@ -142,6 +142,11 @@ def test_contract_ozaki_matches_oracle(bst, ctx, seed, maxdeg):
     c_legs = [a_legs[0], b_legs[1]]
     want = u1.from_dense(c_legs, ref)
     assert rel_err(cd.cpu().numpy(), want) < TOL_OZ
+    # alpha/beta through the GEMM epilogue's block scatter
+    c2 = cd.clone()
+    ctx.contract(AL, ad, BL, bd, la, lb, prec="ozaki", alpha=2.0, beta=-0.5, Cl=CL, c=c2)
+    ctx.sync()
+    assert rel_err(c2.cpu().numpy(), 1.5 * want) < TOL_OZ
     # wide dynamic range inside rows: the per-row scale keeps relative accuracy
     A2 = A * np.exp(rng.uniform(-20, 20, size=A.shape[0]))[:, None, None]
     ref2 = np.tensordot(A2, B, axes=(la, lb))
@@ -357,24 +362,12 @@ def test_contract_many_tiles_with_empty_sectors(bst, ctx, prec, tol):
     got = cd.cpu().numpy()
     assert rel_err(got, ref) <= tol
     assert np.all(got[ref == 0] == 0)
-
-
-def matched_pair_flops(a_legs, la, b_legs, lb):
-    """2 M K N summed over every pair of allowed blocks of A and B that agree
-    on the contracted legs (Sec. 2's block-pair contraction), enumerated
-    from the oracle's block lists."""
-    tot = 0
-    bb = u1.blocks(b_legs)
-    for x in u1.blocks(a_legs):
-        for y in bb:
-            if all(a_legs[i].charges[x[i]] == b_legs[j].charges[y[j]] for i, j in zip(la, lb)):
-                sa = [a_legs[i].degs[x[i]] for i in range(len(a_legs))]
-                sb = [b_legs[j].degs[y[j]] for j in range(len(b_legs))]
-                k = int(np.prod([sa[i] for i in la]))
-                m = int(np.prod([sa[i] for i in range(len(sa)) if i not in la]))
-                n = int(np.prod([sb[j] for j in range(len(sb)) if j not in lb]))
-                tot += 2 * m * k * n
-    return tot
+    # alpha/beta: the K = 0 sectors keep beta times their old values
+    old = torch.tensor(np.random.default_rng(12).standard_normal(LC.nnz), dtype=torch.float64, device="cuda:0")
+    c2 = old.clone()
+    ctx.contract(LA, a, LB, b, (1,), (0,), prec=prec, alpha=-1.5, beta=0.25, Cl=LC, c=c2)
+    torch.cuda.synchronize()
+    assert rel_err(c2.cpu().numpy(), -1.5 * ref + 0.25 * old.cpu().numpy()) <= tol
 
 
 @pytest.mark.parametrize("seed", range(3))
