@@ -155,6 +155,14 @@ BST_API double bst_ctx_work_flops(bst_ctx ctx);
  *   BST_PROJ_GESVD: full FP64 SVD of every sector with cuSOLVER gesvd. */
 typedef enum { BST_PROJ_GESVD = 0, BST_PROJ_SUBSPACE = 1 } bst_proj_method;
 BST_API bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters);
+/* Bound of every wait inside the tensor-core GEMM's pipeline (a thread
+ * polling an mbarrier for a copy, a product or a drained accumulator), in
+ * polls; 0 restores the default (2^28).  When a wait runs out the kernel
+ * records BST_E_TIMEOUT (returned by the next bst_ctx_sync), waits for the
+ * copies and products it has already issued (they always complete), frees
+ * its tensor memory and returns; the context stays usable.  A small bound
+ * makes the waits of a normal launch run out (for testing that path). */
+BST_API bst_status bst_ctx_set_wait_limit(bst_ctx ctx, int64_t tries);
 /* Autotuner of bst_contract_batched (on by default).  When on, the first
  * call of a new batch (per arithmetic) times every candidate schedule on
  * the call's own data, keeps the fastest for all later calls and appends
@@ -247,6 +255,21 @@ BST_API bst_status bst_contract_layout(bst_ctx ctx, bst_layout A, bst_layout B, 
  * bst_contract_layout. */
 BST_API bst_status bst_contract_flops(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs,
                                       const int32_t* legsA, const int32_t* legsB, double* flops);
+
+/* Self-check of the sector matching (Sec. 2: block pairs matched by the
+ * charges on the contracted legs, results reduced by the output charges).
+ * Contraction plans take their relayout task lists (every block's place in
+ * its sector matrix, and the launch's chunk table) from a device planner:
+ * one CTA per view enumerates the leg configurations with their charges and
+ * extents, offsets them within each charge, keeps the sector keys some block
+ * carries and writes one task per block; a second kernel matches the sectors
+ * of A, B and C into the GEMM problem list.  This call builds those tables
+ * on the device for contract(A, B) and compares them with the host
+ * planner's, entry by entry: *mismatches receives the number of entries
+ * that differ (0 when they are identical).  U(1) and Z2 layouts.
+ * Synchronises the device. */
+BST_API bst_status bst_plan_check(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs, const int32_t* legsA,
+                                  const int32_t* legsB, int64_t* mismatches);
 
 /* c = alpha * contract(a, b) + beta * c, with C the layout from
  * bst_contract_layout.  Matched block pairs are grouped by the conserved

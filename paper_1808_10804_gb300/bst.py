@@ -73,6 +73,7 @@ def lib():
         "bst_ctx_profile": [vp, i32],
         "bst_ctx_set_projector": [vp, i32, i32],
         "bst_ctx_set_autotune": [vp, i32],
+        "bst_ctx_set_wait_limit": [vp, i64],
         "bst_ctx_tuning_log": [vp, C.c_char_p, C.c_size_t, P(C.c_size_t)],
         "bst_ctx_profile_read": [vp, i32, C.c_char_p, i32, P(i64), P(dbl), P(dbl), P(dbl)],
         "bst_layout_create": [vp, C.c_int, i32, P(_Leg), P(vp)],
@@ -88,6 +89,7 @@ def lib():
         "bst_fuse": [vp, vp, vp, i32, P(i32), P(vp), vp, vp],
         "bst_contract_layout": [vp, vp, vp, i32, P(i32), P(i32), P(vp)],
         "bst_contract_flops": [vp, vp, vp, i32, P(i32), P(i32), P(dbl)],
+        "bst_plan_check": [vp, vp, vp, i32, P(i32), P(i32), P(i64)],
         "bst_contract": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), C.c_int, dbl, dbl, vp, vp, vp],
         "bst_double_layer": [vp, vp, vp, vp, vp, P(vp), vp, vp],
         "bst_contract_noalloc": [vp, vp, vp, vp, vp, i32, P(i32), P(i32), dbl, dbl, vp, vp, vp],
@@ -248,6 +250,10 @@ class Context:
         m = {"gesvd": 0, "subspace": 1}[method]
         _check(lib().bst_ctx_set_projector(self.h, m, iters))
 
+    def set_wait_limit(self, tries=0):
+        """Bound of the tensor-core GEMM's pipeline waits in polls (0: default)."""
+        _check(lib().bst_ctx_set_wait_limit(self.h, int(tries)))
+
     def set_autotune(self, enable=True):
         _check(lib().bst_ctx_set_autotune(self.h, 1 if enable else 0))
 
@@ -312,6 +318,13 @@ class Context:
         h = C.c_void_p()
         _check(lib().bst_contract_layout(self.h, A.h, B.h, len(legsA), _i32(legsA), _i32(legsB), C.byref(h)))
         return Layout(self, h)
+
+    def plan_check(self, A, B, legsA, legsB):
+        """Entries in which the device-built sector matching of contract(A, B)
+        differs from the host planner's (0: identical)."""
+        n = C.c_int64()
+        _check(lib().bst_plan_check(self.h, A.h, B.h, len(legsA), _i32(legsA), _i32(legsB), C.byref(n)))
+        return n.value
 
     def contract_flops(self, A, B, legsA, legsB):
         """2 M K N over the matched block pairs of contract(A, B) (host-side plan)."""

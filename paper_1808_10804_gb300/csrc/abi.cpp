@@ -157,6 +157,14 @@ bst_status bst_ctx_set_projector(bst_ctx ctx, int32_t method, int32_t iters) {
   });
 }
 
+bst_status bst_ctx_set_wait_limit(bst_ctx ctx, int64_t tries) {
+  return guarded([&] {
+    BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
+    BST_REQUIRE(tries >= 0, BST_E_ARG, "tries must be >= 0");
+    C_(ctx)->spin_limit = tries;
+  });
+}
+
 bst_status bst_ctx_set_autotune(bst_ctx ctx, int32_t enable) {
   return guarded([&] {
     BST_REQUIRE(ctx, BST_E_ARG, "ctx is NULL");
@@ -341,6 +349,20 @@ bst_status bst_fuse(bst_ctx ctx, bst_layout src, const double* src_data, int32_t
       launch_relayout(c, *rp, src_data, dst_data, 0, 1.0, 0.0, (cudaStream_t)stream);
     }
     *dst = H_(D);
+  });
+}
+
+bst_status bst_plan_check(bst_ctx ctx, bst_layout A, bst_layout B, int32_t npairs, const int32_t* legsA,
+                          const int32_t* legsB, int64_t* mismatches) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && A && B && mismatches && npairs >= 0, BST_E_ARG, "bad argument");
+    BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    require_u1(L_(A));
+    require_u1(L_(B));
+    std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
+    *mismatches = plan_check(c, L_(A), L_(B), la, lb, 0);
   });
 }
 

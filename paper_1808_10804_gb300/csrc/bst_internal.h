@@ -223,6 +223,7 @@ struct Ctx {
   std::map<std::string, std::shared_ptr<ProjView>> projviews; // deleter bound in projector.cu
   std::map<uint64_t, DevBuf> su2_weights;  // SU(2) layout id -> per-element 2J+1 (norms)
   int* d_err = nullptr;                     // device error word
+  long long spin_limit = 0;                 // bound of a pipeline wait in tries (0: the default)
   std::atomic<int64_t> launches{0};
   // algorithmic work of the method's contractions issued so far: 2 M N K
   // over the matched block pairs of every contraction (U(1) sector GEMMs,
@@ -277,6 +278,12 @@ DevRelayout* get_fuse_plan(Ctx* ctx, Layout* src, const std::vector<int>& groups
 void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, bst_prec prec,
                   double alpha, double beta, double* c, cudaStream_t s, bool scatter = true,
                   double** cmat_out = nullptr);
+
+// plan_dev.cu: the sector matching of a contraction on the device
+void plan_relayouts_on_device(Ctx* ctx, ContractPlan* p, const std::vector<int>& oa, const std::vector<int>& la,
+                              const std::vector<int>& ob, const std::vector<int>& lb, cudaStream_t s);
+int64_t plan_check(Ctx* ctx, Layout* A, Layout* B, const std::vector<int>& la, const std::vector<int>& lb,
+                   cudaStream_t s);
 
 // relayout.cu
 std::vector<int2> relayout_chunks(const std::vector<RelTask>& t);  // chunk table of a task list

@@ -19,9 +19,12 @@
 //
 // Kernel: persistent, one CTA per SM walking the plan's 128 x 64 output
 // tiles; warp 0 drives TMA (64-byte swizzled K-major tiles, 3-stage ring),
-// warp 1 issues tcgen05.mma from one thread, warps 2..9 drain tensor memory.  All waits are bounded: on expiry
-// the kernel records BST_E_TIMEOUT in the context's error word, lets its
-// copies drain (bounded), frees tensor memory and returns.
+// warp 1 issues tcgen05.mma from one thread, warps 2..9 drain tensor memory.  Every wait of the pipeline
+// is bounded by the launch's spin limit: on expiry the kernel records
+// BST_E_TIMEOUT in the context's error word and every role leaves its loop;
+// before tensor memory is freed and the CTA exits, the TMA copies it has
+// issued and the products it has issued are waited for (they always
+// complete; those waits carry a separate, much larger bound).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -44,7 +47,8 @@ constexpr int kBBytes = kTN * kTK * 2;   // 4 KB per slice
 constexpr int kStageBytes = kSlices * (kABytes + kBBytes);
 constexpr int kThreads = 320;            // 10 warps: TMA, MMA, 8 epilogue
 constexpr int kTmemCols = 512;
-constexpr long long kSpinLimit = 1ll << 28;
+constexpr long long kSpinLimit = 1ll << 28;   // default bound of a pipeline wait (tries)
+constexpr long long kDrainLimit = 1ll << 30;  // bound of the waits for issued copies and products
 // tensor memory columns of the accumulators: d0, d1, d2 double-buffered,
 // d3 and d4 single (5 x 64 + 3 x 64 = 512 columns)
 constexpr int kColD0 = 0, kColD1 = 128, kColD2 = 256, kColD3 = 384;
@@ -107,8 +111,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 
 // Bounded wait; returns false (and raises the abort flag) on expiry or when
 // another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
+                                          long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
   }
@@ -190,6 +195,7 @@ struct Smem {
   uint64_t full[kStages], empty[kStages];
   uint64_t acc_full[2], acc_empty[2];
   uint64_t acc34_empty;  // the epilogue has read d3, d4 of the previous tile
+  uint64_t mma_drain;    // abort path: every product issued so far has completed
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       const Prob* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
                       const int* __restrict__ expA, const int* __restrict__ expB, int rowsA, int rowsB,
-                      double* __restrict__ C, const Scatter sc, int* err) {
+                      double* __restrict__ C, const Scatter sc, int* err, long long spin) {
   extern __shared__ uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -221,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.acc_empty[b], 256);
     }
     mbar_init(&sm.acc34_empty, 256);
+    mbar_init(&sm.mma_drain, 1);
     sm.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nk = (p.K + kTK - 1) / kTK;
         for (int c = 0; c < nk; ++c, ++g) {
           const int s = int(g % kStages);
-          if (g >= kStages && !mbar_wait(&sm.empty[s], int((g / kStages) - 1) & 1, abort_flag, err)) {
+          if (g >= kStages && !mbar_wait(&sm.empty[s], int((g / kStages) - 1) & 1, abort_flag, err, spin)) {
             ok = false;
             break;
           }
@@ -260,12 +267,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(base + kSlices * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
         }
       }
-      if (*abort_flag) {
-        // let the copies in flight land before the CTA exits (bounded)
-        for (long long c = (g > kStages ? g - kStages : 0); c < g; ++c) {
-          const int s = int(c % kStages);
-          for (long long i = 0; i < kSpinLimit && !mbar_try(&sm.full[s], int(c / kStages) & 1); ++i) {
-          }
+      // every copy issued has landed before the CTA may exit, whichever
+      // role aborted and when (after a normal run these phases are already
+      // complete: the products consumed them)
+      for (long long c = (g > kStages ? g - kStages : 0); c < g; ++c) {
+        const int s = int(c % kStages);
+        for (long long i = 0; i < kDrainLimit && !mbar_try(&sm.full[s], int(c / kStages) & 1); ++i) {
         }
       }
     }
@@ -286,15 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const long long pc = pg + (c >> 1);
           const int buf = int(pc & 1);
           const bool first = (c & 1) == 0;
-          if (!mbar_wait(&sm.full[s], int(g / kStages) & 1, abort_flag, err)) {
+          if (!mbar_wait(&sm.full[s], int(g / kStages) & 1, abort_flag, err, spin)) {
             ok = false;
             break;
           }
-          if (first && pc >= 2 && !mbar_wait(&sm.acc_empty[buf], int((pc >> 1) - 1) & 1, abort_flag, err)) {
+          if (first && pc >= 2 && !mbar_wait(&sm.acc_empty[buf], int((pc >> 1) - 1) & 1, abort_flag, err, spin)) {
             ok = false;
             break;
           }
-          if (c == 0 && tn > 0 && !mbar_wait(&sm.acc34_empty, (tn - 1) & 1, abort_flag, err)) {
+          if (c == 0 && tn > 0 && !mbar_wait(&sm.acc34_empty, (tn - 1) & 1, abort_flag, err, spin)) {
             ok = false;
             break;
           }
@@ -325,6 +332,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         pg += (nk + 1) >> 1;
       }
+      // every product issued has written tensor memory before it is freed,
+      // whichever role aborted and when (the commit arrives once they have
+      // all completed; with none issued, at once)
+      mma_commit(&sm.mma_drain);
+      for (long long i = 0; i < kDrainLimit && !mbar_try(&sm.mma_drain, 0); ++i) {
+      }
     }
   } else {
     // ---------------- epilogue: warps 2..9 ----------------
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int pp = 0; pp < npair; ++pp) {
         const long long pc = pg + pp;
         const int buf = int(pc & 1);
-        ok = mbar_wait(&sm.acc_full[buf], int(pc >> 1) & 1, abort_flag, err);
+        ok = mbar_wait(&sm.acc_full[buf], int(pc >> 1) & 1, abort_flag, err, spin);
         if (!ok) break;
         tc_fence_after();
         uint32_t v[32];
@@ -785,7 +798,7 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
   const int grid = std::min(P->ntiles, num_sms());
   oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(
       P->mapA, b_from_a ? P->mapBA : P->mapB, P->d_probs, P->d_tiles, P->ntiles, P->eA, b_from_a ? P->eA : P->eB,
-      P->rowsA, P->rowsB, C, sc, ctx->d_err);
+      P->rowsA, P->rowsB, C, sc, ctx->d_err, ctx->spin_limit > 0 ? ctx->spin_limit : oz::kSpinLimit);
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
 }

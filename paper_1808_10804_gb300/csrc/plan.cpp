@@ -188,9 +188,9 @@ ContractPlan* get_contract_plan(Ctx* ctx, Layout* A, Layout* B, const std::vecto
     if (g.M > 0 && g.N > 0) p->probs.push_back(g);
   }
   if (ctx->device >= 0) {  // host-only contexts plan without device tables
-    p->ra.upload(p->va.tasks);
-    p->rb.upload(p->vb.tasks);
-    p->rc.upload(p->vc.tasks);
+    // the relayout task lists (every block's place in its sector matrix)
+    // are built by the device planner, which matches the same sectors
+    plan_relayouts_on_device(ctx, p.get(), oa, la, ob, lb, 0);
     p->g.upload(p->probs, kF64TileM, kF64TileN);
   }
   ContractPlan* raw = p.get();
