@@ -252,6 +252,16 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     ms, nl = timed(prec, steps)
     ms64, _ = timed("fp64", max(3, steps // 2))
     ms, ms64 = job_ms(ms, world), job_ms(ms64, world)   # the slowest rank's
+    cheap = None
+    if prec != "bf16x3":
+        _, c3 = ctx.contract_batched(As, as_, Bs, bs, la, lb, prec="bf16x3", Cls=Cls)
+        torch.cuda.synchronize()
+        err3 = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(c3, c64))
+        ms3, _ = timed("bf16x3", max(3, steps // 2))
+        ms3 = job_ms(ms3, world)
+        cheap = {"prec": "bf16x3", "ms_per_step": ms3, "value": total_flops / (ms3 / 1e3) / 1e12,
+                 "rel_err_vs_fp64_path": err3}
+        del c3
     ctx.profile(True)
     w0 = ctx.work_flops
     ctx.contract_batched(As, as_, Bs, bs, la, lb, prec=prec, Cls=Cls, cs=cs)
@@ -261,7 +271,7 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile(False)
-    gk = "gemm_ozaki" if prec == "ozaki" else "gemm_f64"
+    gk = "gemm_f64" if prec == "fp64" else "gemm_ozaki"
     by_rel = prof["relayout"][3]
     out = {"workload": "u1_batch64_corner_contractions", "count": total_count,
            "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s (block-sparse, FP64-equivalent)",
@@ -271,14 +281,15 @@ def batch_bench(bst, ctx, dev, prec, steps, warmup, flush, pk):
            "algorithmic_gflop": flops / 1e9, "rel_err_vs_fp64_path": err, "gpu_launches": int(nl),
            "timing": "median of CUDA-graph replays, L2 flushed between replays",
            "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()},
-           "autotune": [ln.split(" ", 2)[2] for ln in ctx.tuning_log().splitlines() if "chosen" in ln]}
+           "autotune": [ln.split(" ", 2)[2] for ln in ctx.tuning_log().splitlines() if "chosen" in ln],
+           "cheaper_mode": cheap}
     tms = prof[gk][1] / 1e3
-    if prec == "ozaki":
+    if prec != "fp64":
         a = local_flops / tms / 1e12
         out["roofline"] = {"kernel": gk, "bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"],
                            "unit": "TFLOP/s", "frac": a / pk["bf16_tflops"],
                            "work": "method flops (2MNK of the matched blocks, counted once)",
-                           "digit_product_tflops": 15.0 * local_flops / tms / 1e12}
+                           "digit_product_tflops": (15.0 if prec == "ozaki" else 6.0) * local_flops / tms / 1e12}
     else:
         peak = pk["bf16_tflops"] * 1.25 / 2250.0
         a = local_flops / tms / 1e12
@@ -471,7 +482,7 @@ def single_layer_bench(bst, dev, local, prec, steps, warmup, flush, pk):
         torch.cuda.synchronize()
         prof = ctx.profile_read()
         ctx.profile(False)
-        gk = "gemm_ozaki" if prec == "ozaki" else "gemm_f64"
+        gk = "gemm_f64" if prec == "fp64" else "gemm_ozaki"
         out = {"workload": "u1_D8_chi256_single_layer_left_move", "value": 1e3 / ms, "unit": "moves/s",
                "ms_per_step": ms, "fp64_path_ms_per_step": ms64, "rel_err_vs_fp64_path": err,
                "kept": stats["kept"][0], "algorithmic_gflop": flops / 1e9,
@@ -646,6 +657,34 @@ def run_ours(args):
         torch.cuda.synchronize()
         fp64_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev2)
 
+    # the cheaper arithmetic (three BF16 slices in the block contractions,
+    # the projector in the five-slice one): speed and error of the same step
+    cheap = None
+    if prec != "bf16x3":
+        one_step("bf16x3")
+        torch.cuda.synchronize()
+        errc = {}
+        for r in bst.ROLES:
+            if net.env.L[r] == refL[r]:
+                x = net.env.data(r).cpu().numpy()
+                errc[r] = float(np.linalg.norm(x - ref64[r]) / np.linalg.norm(ref64[r]))
+            else:
+                errc[r] = float("inf")
+        ev3 = []
+        for i in range(max(3, args.steps // 2)):
+            flush.fill_(float(i))
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_step("bf16x3")
+            b_.record(stream)
+            ev3.append((a, b_))
+        torch.cuda.synchronize()
+        cms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev3)
+        cheap = {"workload": "u1_D6_chi72_full_move", "prec": "bf16x3", "value": 1e3 / cms, "unit": "moves/s",
+                 "ms_per_step": cms, "fp64_path_ms_per_step": fp64_ms, "rel_err_vs_fp64_path": max(errc.values()),
+                 "rel_err_vs_fp64_path_by_tensor": {r: float(f"{e:.3e}") for r, e in errc.items()},
+                 "note": "block contractions in three BF16 slices (6 products); projector in five"}
+
     pk = peaks()
     batched = su2 = su2m = large = None
     if not args.no_batch:
@@ -672,7 +711,7 @@ def run_ours(args):
             return {"kernel": name, "bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"],
                     "unit": "TFLOP/s", "frac": a / pk["bf16_tflops"],
                     "work": "method flops of the step, counted once",
-                    "digit_product_tflops": 15.0 * fl / sec / 1e12}
+                    "digit_product_tflops": (15.0 if prec == "ozaki" else 6.0) * fl / sec / 1e12}
         if name == "gemm_f64":
             peak = pk["bf16_tflops"] * 1.25 / 2250.0   # FP64 tensor peak from the nominal ratio
             a = algo_flops / sec / 1e12
@@ -703,7 +742,8 @@ def run_ours(args):
     v = job_value(ms_step, world)
     # the sub-workloads first, one JSON line each on stderr; the headline
     # line (stdout) stays short and carries their key numbers
-    subs = {"batched": batched, "su2_corner": su2, "su2_left_move": su2m, "single_layer_large": large}
+    subs = {"cheaper_mode": cheap, "batched": batched, "su2_corner": su2, "su2_left_move": su2m,
+            "single_layer_large": large}
     for name, rep in subs.items():
         if rep:
             print(json.dumps({"sub_workload": name, **rep}), file=sys.stderr, flush=True)
@@ -713,7 +753,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16x5-slices->f64",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "ozaki": "bf16x5-slices->f64", "bf16x3": "bf16x3-slices->f64"}[prec],
         "data": "synthetic",
         "config": {"workload": "u1_D6_chi72_full_move", "D": 6, "chi": 72, "prec": prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
@@ -744,7 +785,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="ozaki", choices=["fp64", "ozaki"])
+    ap.add_argument("--prec", default="ozaki", choices=["fp64", "ozaki", "bf16x3"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-contraction report")
     ap.add_argument("--quick", action="store_true", help="warm-up and steps only, no report (for profilers)")

@@ -85,13 +85,23 @@ typedef enum {
 typedef enum { BST_U1 = 1, BST_SU2 = 2, BST_Z2 = 3 } bst_group;
 
 /* Arithmetic of the block GEMMs.
- *   BST_FP64:  plain FP64 (DMMA) grouped GEMM;
- *   BST_OZAKI: FP64 operands split into integer-valued BF16 slices with a
- *              shared power-of-two scale per row; slice products run on the
- *              tcgen05 tensor cores with FP32 accumulation in tensor memory,
- *              exact over short K chunks, and are recombined with FP64
- *              weights in the epilogue.  ~44 significant bits. */
-typedef enum { BST_FP64 = 0, BST_OZAKI = 1 } bst_prec;
+ *   BST_FP64:   plain FP64 (DMMA) grouped GEMM;
+ *   BST_OZAKI:  FP64 operands split into five integer-valued BF16 slices
+ *               with a shared power-of-two scale per row; slice products run
+ *               on the tcgen05 tensor cores with FP32 accumulation in tensor
+ *               memory, exact over short K chunks, and are recombined with
+ *               FP64 weights in the epilogue.  ~44 significant bits (the 15
+ *               slice products of weight >= 2^-36 of the leading one);
+ *   BST_BF16X3: the cheaper mode: three slices (26 bits of each operand)
+ *               and their 6 products of weight >= 2^-18, accumulated
+ *               exactly; relative error ~2^-25 of sum |a||b| (FP32 class)
+ *               at 40% of BST_OZAKI's tensor-core work and 60% of its
+ *               operand bytes.  The block contractions run in it; the
+ *               projector's eigensolver and subspace iterations, which must
+ *               resolve singular values far below the largest, run in
+ *               BST_OZAKI.
+ * Any other value: BST_E_ARG. */
+typedef enum { BST_FP64 = 0, BST_OZAKI = 1, BST_BF16X3 = 2 } bst_prec;
 
 typedef struct {
   int32_t flow;           /* +1 incoming, -1 outgoing */
@@ -434,6 +444,76 @@ typedef struct {
 BST_API bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a,
                         bst_env* env, int64_t chi, double rel_cutoff, bst_prec prec,
                         bst_ctm_stats* stats, bst_stream stream);
+
+/* ---- observables and the CTM error procedure ------------------------------ */
+
+/* Open double layer of a site A[p,l,u,r,d] (Sec. 3.2 with the physical legs
+ * kept open): ket and bra multiplied without the sum over p, virtual ket/bra
+ * legs fused pairwise as in bst_double_layer, the remover R[r,l',s]
+ * (Sec. 3.1; its extra leg traced between ket and bra) absorbed on the
+ * right leg when R is non-NULL.  Legs [L, U, R, D, p, p'] (p the ket's
+ * physical leg, p' the bra's, its dual).  Summing p = p' gives
+ * bst_double_layer's tensor.  Two calls as for bst_double_layer: a == NULL
+ * returns the layout in *a_layout (new reference); then a device buffer of
+ * nnz(*a_layout) doubles.  U(1) and Z2. */
+BST_API bst_status bst_double_layer_open(bst_ctx ctx, bst_layout A, const double* A_data, bst_layout R,
+                                         const double* R_data, bst_layout* a_layout, double* a, bst_stream stream);
+
+/* Two-site reduced density matrix of a bond of the one-site cell from its
+ * environment (the observable of Sec. 3's error procedure and of Sec. 4.1's
+ * energies): bond 0 = horizontal (the site and its right neighbour, the
+ * 3 x 4 network C1 T1 T1 C2 / T4 a a T2 / C4 T3 T3 C3 with both sites
+ * open), 1 = vertical (the site and the one below: the network turned by a
+ * quarter turn).  site is the open double layer [L,U,R,D,p,p'].  Result
+ * rho[p_i, p_i', p_j, p_j'] (not normalised; Tr rho is the closed network's
+ * value) in *rho_layout (new reference); its nnz(*rho_layout) doubles are
+ * copied to the device buffer rho if rho is non-NULL (capacity rho_cap
+ * doubles, BST_E_SHAPE if too small).  The contractions run in prec. */
+BST_API bst_status bst_ctm_bond_rdm(bst_ctx ctx, int32_t bond, bst_layout site, const double* site_data,
+                                    bst_env* env, bst_prec prec, bst_layout* rho_layout, double* rho,
+                                    int64_t rho_cap, bst_stream stream);
+
+/* sum_i x_i y_i over the nnz(layout) stored elements of two tensors with the
+ * same layout (for U(1) and Z2 the Frobenius inner product; Tr(rho H) when H
+ * is the operator's tensor in rho's layout), in FP64 with a fixed summation
+ * order, into *out (host).  Synchronises the stream. */
+BST_API bst_status bst_dot(bst_ctx ctx, bst_layout layout, const double* x, const double* y, double* out,
+                           bst_stream stream);
+
+typedef struct {
+  double value;          /* observable at the last chi */
+  double error;          /* max(error_steps, error_chi) */
+  double error_steps;    /* largest change among the last three steps at the last chi */
+  double error_chi;      /* change between the last two fixed-chi results (0 with one chi) */
+  int64_t chi_final;     /* chi of the last fixed-chi run */
+  int32_t steps_total;   /* full CTM moves done */
+  int32_t nchi;          /* fixed-chi runs done */
+  int64_t chi[8];        /* per run (the first 8): chi, result and moves */
+  double value_at_chi[8];
+  int32_t steps_at_chi[8];
+} bst_ctm_converge_stats;
+
+/* The CTM error procedure of Sec. 3 (implementation details) on a one-site
+ * cell: full moves (bst_ctm_move, dir 4) at fixed chi until the energy per
+ * site changes by less than tol or max_steps moves are done (the paper:
+ * 1e-8 and 15); the first error is the largest change among the last three
+ * moves.  chi is then doubled and the procedure repeated until two
+ * fixed-chi results differ by less than tol or doubling would exceed
+ * chi_max (the paper: 128); the second error is the change between the last
+ * two fixed-chi results; stats->error is the larger.  The energy per site is
+ * the sum over the horizontal and vertical bonds of Tr(rho H) / Tr(rho)
+ * (bst_ctm_bond_rdm, bst_dot), H a two-site operator given as a tensor with
+ * rho's layout (H[p_i, p_i', p_j, p_j'] = <p_i p_j|h|p_i' p_j'>; for the
+ * Heisenberg coupling S.S it conserves the charge, Sec. 3.1's charged
+ * operators being combined on the bond).  a is the closed site (as for
+ * bst_ctm_move), site the open one; env buffers need capacity for chi_max.
+ * Synchronises the stream after every move (the stopping rule is a host
+ * decision). */
+BST_API bst_status bst_ctm_converge(bst_ctx ctx, bst_layout a_layout, const double* a, bst_layout site,
+                                    const double* site_data, bst_layout H_layout, const double* H, bst_env* env,
+                                    int64_t chi0, int64_t chi_max, double tol, int32_t max_steps,
+                                    double rel_cutoff, bst_prec prec, bst_ctm_converge_stats* stats,
+                                    bst_stream stream);
 
 #ifdef __cplusplus
 }

@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbst.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bst.h")
 
-FP64, OZAKI = 0, 1
-PREC = {"fp64": FP64, "ozaki": OZAKI, FP64: FP64, OZAKI: OZAKI}
+FP64, OZAKI, BF16X3 = 0, 1, 2
+PREC = {"fp64": FP64, "ozaki": OZAKI, "bf16x3": BF16X3, FP64: FP64, OZAKI: OZAKI, BF16X3: BF16X3}
 LEFT, UP, RIGHT, DOWN, ALL = 0, 1, 2, 3, 4
 ROLES = ("C1", "C2", "C3", "C4", "T1", "T2", "T3", "T4")
 
@@ -46,6 +46,13 @@ class _Env(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("kept", C.c_int64 * 4), ("smin_over_smax", C.c_double * 4),
                 ("trunc_weight", C.c_double * 4)]
+
+
+class _ConvStats(C.Structure):
+    _fields_ = [("value", C.c_double), ("error", C.c_double), ("error_steps", C.c_double),
+                ("error_chi", C.c_double), ("chi_final", C.c_int64), ("steps_total", C.c_int32),
+                ("nchi", C.c_int32), ("chi", C.c_int64 * 8), ("value_at_chi", C.c_double * 8),
+                ("steps_at_chi", C.c_int32 * 8)]
 
 
 def exported_names():
@@ -99,6 +106,11 @@ def lib():
                               P(dbl), P(i64), vp],
         "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
         "bst_sym_eig": [vp, i32, i32, vp, vp, vp, C.c_int, vp],
+        "bst_double_layer_open": [vp, vp, vp, vp, vp, P(vp), vp, vp],
+        "bst_ctm_bond_rdm": [vp, i32, vp, vp, P(_Env), C.c_int, P(vp), vp, i64, vp],
+        "bst_dot": [vp, vp, vp, vp, P(dbl), vp],
+        "bst_ctm_converge": [vp, vp, vp, vp, vp, vp, vp, P(_Env), i64, i64, dbl, i32, dbl, C.c_int,
+                             P(_ConvStats), vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -216,6 +228,20 @@ class Layout:
         h = C.c_void_p()
         _check(lib().bst_layout_dual(self.h, C.byref(h)))
         return Layout(self.ctx, h)
+
+    def from_dense(self, dense):
+        """Flat canonical-order data of a dense array (its allowed blocks,
+        block by block, row-major): host-side marshalling of inputs such as
+        operators."""
+        import numpy as np
+        dense = np.asarray(dense, dtype=np.float64)
+        offs = [np.concatenate([[0], np.cumsum(l.degs)]) for l in self.legs]
+        out = np.zeros(self.nnz)
+        for sect, off, shape in self.blocks():
+            sl = tuple(slice(int(o[s]), int(o[s]) + int(d)) for o, s, d in zip(offs, sect, shape))
+            n = int(np.prod(shape))
+            out[off:off + n] = dense[sl].reshape(-1)
+        return out
 
     def empty(self, device=None):
         return torch.empty(max(self.nnz, 0), dtype=torch.float64,
@@ -374,6 +400,54 @@ class Context:
         _check(lib().bst_double_layer(self.h, A.h, _ptr(a), R.h if R else None, _ptr(r) if R else None,
                                       C.byref(h), _ptr(out), _stream(stream)))
         return L, out
+
+    def double_layer_open(self, A, a, R=None, r=None, stream=None):
+        """Open double layer [L, U, R, D, p, p'] (physical legs kept open)."""
+        h = C.c_void_p()
+        _check(lib().bst_double_layer_open(self.h, A.h, _ptr(a), R.h if R else None, _ptr(r) if R else None,
+                                           C.byref(h), None, _stream(stream)))
+        L = Layout(self, h)
+        out = torch.empty(L.nnz, dtype=torch.float64, device=a.device)
+        _check(lib().bst_double_layer_open(self.h, A.h, _ptr(a), R.h if R else None, _ptr(r) if R else None,
+                                           C.byref(h), _ptr(out), _stream(stream)))
+        return L, out
+
+    def bond_rdm(self, env, site_layout, site, bond, prec="fp64", stream=None):
+        """Two-site density matrix rho[p_i, p_i', p_j, p_j'] of a horizontal
+        (bond 0) or vertical (bond 1) bond."""
+        h = C.c_void_p()
+        dp = site_layout.legs[4].dim
+        out = torch.empty(dp ** 4, dtype=torch.float64, device=site.device)  # at least nnz(rho)
+        e = env.to_c()
+        try:
+            _check(lib().bst_ctm_bond_rdm(self.h, bond, site_layout.h, _ptr(site), C.byref(e), PREC[prec],
+                                          C.byref(h), _ptr(out), out.numel(), _stream(stream)))
+        finally:
+            env.from_c(e)
+        L = Layout(self, h)
+        return L, out[:L.nnz]
+
+    def dot(self, L, x, y, stream=None):
+        out = C.c_double()
+        _check(lib().bst_dot(self.h, L.h, _ptr(x), _ptr(y), C.byref(out), _stream(stream)))
+        return out.value
+
+    def ctm_converge(self, env, a_layout, a, site_layout, site, H_layout, H, chi0, chi_max, tol=1e-8, max_steps=15,
+                     rel_cutoff=1e-14, prec="fp64", stream=None):
+        """The CTM error procedure of Sec. 3 with the energy per site as the
+        observable; returns a dict of the stats."""
+        st = _ConvStats()
+        e = env.to_c()
+        try:
+            _check(lib().bst_ctm_converge(self.h, a_layout.h, _ptr(a), site_layout.h, _ptr(site), H_layout.h,
+                                          _ptr(H), C.byref(e), chi0, chi_max, tol, max_steps, rel_cutoff,
+                                          PREC[prec], C.byref(st), _stream(stream)))
+        finally:
+            env.from_c(e)
+        n = min(st.nchi, 8)
+        return {"value": st.value, "error": st.error, "error_steps": st.error_steps, "error_chi": st.error_chi,
+                "chi_final": st.chi_final, "steps_total": st.steps_total,
+                "runs": [(st.chi[i], st.value_at_chi[i], st.steps_at_chi[i]) for i in range(n)]}
 
     def double_layer_layout(self, A, R=None):
         """Layout of the double layer of A (with the remover R) without

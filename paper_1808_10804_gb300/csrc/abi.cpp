@@ -406,7 +406,7 @@ bst_status bst_contract(bst_ctx ctx, bst_layout A, const double* a, bst_layout B
   return guarded([&] {
     BST_REQUIRE(ctx && A && B && C && npairs >= 0, BST_E_ARG, "bad argument");
     BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
-    BST_REQUIRE(prec == BST_FP64 || prec == BST_OZAKI, BST_E_ARG, "unknown precision mode");
+    require_prec(prec);
     Ctx* cx = C_(ctx);
     set_dev(cx);
     std::vector<int> la(legsA, legsA + npairs), lb(legsB, legsB + npairs);
@@ -442,7 +442,7 @@ bst_status bst_contract_batched(bst_ctx ctx, int32_t nbatch, const bst_layout* A
   return guarded([&] {
     BST_REQUIRE(ctx && nbatch >= 1 && A && a && B && b && C && c && npairs >= 0, BST_E_ARG, "bad argument");
     BST_REQUIRE(npairs == 0 || (legsA && legsB), BST_E_ARG, "leg lists are NULL");
-    BST_REQUIRE(prec == BST_FP64 || prec == BST_OZAKI, BST_E_ARG, "unknown precision mode");
+    require_prec(prec);
     Ctx* cx = C_(ctx);
     set_dev(cx);
     std::vector<Layout*> la_(nbatch), lb_(nbatch), lc_(nbatch);
@@ -541,6 +541,7 @@ bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double* rtop, b
                              bst_layout* P, double* p, bst_layout* Pt, double* pt, double* svals, int64_t* kept,
                              bst_stream stream) {
   return guarded([&] {
+    require_prec(prec);
     BST_REQUIRE(ctx && Rtop && Rbot && rtop && rbot && P && p && Pt && pt && kept, BST_E_ARG, "null argument");
     require_u1(L_(Rtop));
     Ctx* c = C_(ctx);
@@ -558,21 +559,89 @@ bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double* rtop, b
 bst_status bst_sym_eig(bst_ctx ctx, int32_t n, int32_t batch, const double* H, double* X, double* lam,
                        bst_prec prec, bst_stream stream) {
   return guarded([&] {
+    require_prec(prec);
     BST_REQUIRE(ctx && H && X && lam, BST_E_ARG, "null argument");
     Ctx* c = C_(ctx);
     set_dev(c);
-    sym_eig_batched(c, n, batch, H, X, lam, prec, (cudaStream_t)stream);
+    // the refinement's products need the FP64-accurate arithmetic
+    sym_eig_batched(c, n, batch, H, X, lam, prec == BST_BF16X3 ? BST_OZAKI : prec, (cudaStream_t)stream);
   });
 }
 
 bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a, bst_env* env, int64_t chi,
                         double rel_cutoff, bst_prec prec, bst_ctm_stats* stats, bst_stream stream) {
   return guarded([&] {
+    require_prec(prec);
     BST_REQUIRE(ctx && a_layout && a && env, BST_E_ARG, "null argument");
     BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
     Ctx* c = C_(ctx);
     set_dev(c);
     ctm_move(c, dir, L_(a_layout), a, env, chi, rel_cutoff, prec, stats, (cudaStream_t)stream);
+  });
+}
+
+bst_status bst_double_layer_open(bst_ctx ctx, bst_layout A, const double* A_data, bst_layout R, const double* R_data,
+                                 bst_layout* a_layout, double* a, bst_stream stream) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && A && a_layout, BST_E_ARG, "null argument");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    Layout* out = double_layer_open(c, L_(A), A_data, R ? L_(R) : nullptr, R_data, a, (cudaStream_t)stream);
+    if (a) {
+      const bool same = *a_layout == H_(out);
+      release(out);
+      BST_REQUIRE(same, BST_E_SHAPE, "a_layout is not the open double-layer layout");
+    } else {
+      *a_layout = H_(out);
+    }
+  });
+}
+
+bst_status bst_ctm_bond_rdm(bst_ctx ctx, int32_t bond, bst_layout site, const double* site_data, bst_env* env,
+                            bst_prec prec, bst_layout* rho_layout, double* rho, int64_t rho_cap, bst_stream stream) {
+  return guarded([&] {
+    require_prec(prec);
+    BST_REQUIRE(ctx && site && site_data && env && rho_layout, BST_E_ARG, "null argument");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* r = nullptr;
+    Layout* RL = bond_rdm(c, bond, L_(site), site_data, env, prec, &r, s);
+    if (rho) {
+      if (RL->nnz > rho_cap) {
+        release(RL);
+        throw Error(BST_E_SHAPE, "rho buffer capacity too small");
+      }
+      BST_CUDA(cudaMemcpyAsync(rho, r, sizeof(double) * RL->nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    *rho_layout = H_(RL);
+  });
+}
+
+bst_status bst_dot(bst_ctx ctx, bst_layout layout, const double* x, const double* y, double* out, bst_stream stream) {
+  return guarded([&] {
+    BST_REQUIRE(ctx && layout && out, BST_E_ARG, "null argument");
+    BST_REQUIRE(L_(layout)->nnz == 0 || (x && y), BST_E_ARG, "data pointer is NULL");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    *out = block_dot(c, x, y, L_(layout)->nnz, (cudaStream_t)stream);
+  });
+}
+
+bst_status bst_ctm_converge(bst_ctx ctx, bst_layout a_layout, const double* a, bst_layout site, const double* site_data,
+                            bst_layout H_layout, const double* H, bst_env* env, int64_t chi0, int64_t chi_max,
+                            double tol, int32_t max_steps, double rel_cutoff, bst_prec prec,
+                            bst_ctm_converge_stats* stats, bst_stream stream) {
+  return guarded([&] {
+    require_prec(prec);
+    BST_REQUIRE(ctx && a_layout && a && site && site_data && H_layout && H && env && stats, BST_E_ARG,
+                "null argument");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    bst_ctm_converge_stats st;
+    ctm_converge(c, L_(a_layout), a, L_(site), site_data, L_(H_layout), H, env, chi0, chi_max, tol, max_steps,
+                 rel_cutoff, prec, &st, (cudaStream_t)stream);
+    *stats = st;
   });
 }
 

@@ -49,8 +49,11 @@ struct BatchPlan {
   DevGemm g;
   // schedule chosen by the autotuner (defaults until tuned)
   bool tuned_rel = false;
-  bool tuned[2] = {false, false};  // per arithmetic (BST_FP64, BST_OZAKI)
-  int order[2] = {0, 0};
+  // per arithmetic (BST_FP64, BST_OZAKI, BST_BF16X3): tile schedule and,
+  // for the tensor-core GEMM, the output tile width (128 x 64 or 128 x 32)
+  bool tuned[3] = {false, false, false};
+  int order[3] = {0, 0, 0};
+  int tn[3] = {0, 0, 0};
   // data pointers (a[0..n), b[0..n), c[0..n)) -> device copy of that table
   std::map<std::vector<const void*>, double**> tables;
   // the plan's own sector-matrix buffers: a captured graph of this batch
@@ -141,7 +144,9 @@ static float time_ms(cudaStream_t s, int reps, F&& f) {
 // plan's own buffers are written while tuning; the caller's outputs are not.
 //   relayout: elements per CTA of the gathers and the scatter (1K..8K);
 //   GEMM: tile schedule (problem order / longest K first / column tiles
-//   outer for the tensor-core GEMM; problem order / longest K first for FP64).
+//   outer for the tensor-core GEMM; problem order / longest K first for FP64)
+//   and, for the tensor-core GEMM, the output tile shape (128 x 64, or
+//   128 x 32: twice the tiles, half the padding of narrow sectors).
 static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bst_prec prec, const std::string& tag,
                      cudaStream_t s) {
   const bool prof = ctx->prof;
@@ -168,31 +173,39 @@ static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bs
     ctx->tune_log += line;
     bp->tuned_rel = true;
   }
-  const int pi = prec == BST_FP64 ? 0 : 1;
+  const int pi = int(prec);
   if (!bp->tuned[pi]) {
     launch_rel(ctx, bp->ra, bases, bp->Am, 0, 1.0, 0.0, s);
     launch_rel(ctx, bp->rb, bases + n, bp->Bm, 0, 1.0, 0.0, s);
     const int norders = prec == BST_FP64 ? 2 : 3;
+    const int S = ozaki_slices(prec);
+    const char* kname = prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki";
     float best = 1e30f;
-    int bo = 0;
-    for (int o = 0; o < norders; ++o) {
-      float t;
-      if (prec == BST_FP64) {
-        bp->g.upload(bp->probs, kF64TileM, kF64TileN, o);
-        t = time_ms(s, 3, [&] { launch_gemm_f64(ctx, bp->g, bp->Am, bp->Bm, bp->Cm, s); });
-      } else {
-        t = time_ms(s, 3, [&] { run_gemm_ozaki_probs(ctx, tag, bp->probs, bp->Am, bp->Bm, bp->Cm, s, o); });
+    int bo = 0, btn = 64;
+    for (int tn : {64, 32}) {
+      if (prec == BST_FP64 && tn != 64) continue;
+      for (int o = 0; o < norders; ++o) {
+        float t;
+        if (prec == BST_FP64) {
+          bp->g.upload(bp->probs, kF64TileM, kF64TileN, o);
+          t = time_ms(s, 3, [&] { launch_gemm_f64(ctx, bp->g, bp->Am, bp->Bm, bp->Cm, s); });
+        } else {
+          t = time_ms(s, 3, [&] {
+            run_gemm_ozaki_probs(ctx, tag, bp->probs, bp->Am, bp->Bm, bp->Cm, s, o, true, S, tn);
+          });
+        }
+        snprintf(line, sizeof(line), "batch %p %s tile 128x%d order %d: %.4f ms\n", (void*)bp, kname,
+                 prec == BST_FP64 ? kF64TileN : tn, o, t);
+        ctx->tune_log += line;
+        if (t < best) best = t, bo = o, btn = tn;
       }
-      snprintf(line, sizeof(line), "batch %p %s tile order %d: %.4f ms\n", (void*)bp,
-               prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki", o, t);
-      ctx->tune_log += line;
-      if (t < best) best = t, bo = o;
     }
     if (prec == BST_FP64) bp->g.upload(bp->probs, kF64TileM, kF64TileN, bo);
     bp->order[pi] = bo;
+    bp->tn[pi] = btn;
     bp->tuned[pi] = true;
-    snprintf(line, sizeof(line), "batch %p %s tile order chosen %d\n", (void*)bp,
-             prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki", bo);
+    snprintf(line, sizeof(line), "batch %p %s tile order chosen %d, tile 128x%d\n", (void*)bp, kname, bo,
+             prec == BST_FP64 ? kF64TileN : btn);
     ctx->tune_log += line;
   }
   ctx->prof = prof;
@@ -290,7 +303,8 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
   } else {
     // the same grouped tensor-core GEMM as a single contraction, over the
     // problems of all contractions
-    run_gemm_ozaki_probs(ctx, tag, bp->probs, Am, Bm, Cm, s, bp->order[1]);
+    run_gemm_ozaki_probs(ctx, tag, bp->probs, Am, Bm, Cm, s, bp->order[int(prec)], true, ozaki_slices(prec),
+                         bp->tn[int(prec)]);
   }
   launch_rel(ctx, bp->rc, bases + 2 * n, Cm, 1, alpha, beta, s);
 }

@@ -183,8 +183,9 @@ struct ContractPlan {
   DevRelayout ra, rb, rc;      // A->Amat, B->Bmat, Cmat->C
   std::vector<GemmProb> probs; // per matched sector
   DevGemm g;
-  OzakiPlan* oz = nullptr;
-  OzakiPlan* ozs = nullptr;    // the same GEMM with the output scattered into C's blocks
+  // tensor-core GEMM plans by digit count and output form: [S == 3][scatter]
+  // (scatter: the output written straight into C's blocks)
+  OzakiPlan* oz[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int64_t amat = 0, bmat = 0, cmat = 0;  // matrix buffer sizes (elements)
   ~ContractPlan();
 };
@@ -305,24 +306,30 @@ void launch_gemm_f64_splitk(Ctx* ctx, const DevGemm& g, int ksplit, const double
 extern const int kF64TileM, kF64TileN;
 
 // gemm_ozaki.cu
-void ozaki_prepare(Ctx* ctx, ContractPlan* p);
+// digit slices per operand of a tensor-core arithmetic (5 for BST_OZAKI,
+// 3 for BST_BF16X3)
+int ozaki_slices(bst_prec prec);
+// output tile width for a problem list: 64, or 32 when 128 x 64 tiles
+// would leave SMs idle or pad narrow problems by more than half
+int ozaki_pick_tn(const std::vector<GemmProb>& probs);
+// plain variant: the epilogue writes the sector matrices Cmat
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* Cmat,
+                    cudaStream_t s);
 // scatter variant: the epilogue writes c = alpha * A B + beta * c straight
 // into the output tensor's canonical blocks (no sector matrix, no scatter
 // launch)
-void ozaki_prepare_scatter(Ctx* ctx, ContractPlan* p);
-void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* c,
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* c,
                             double alpha, double beta, cudaStream_t s);
-void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
-                    cudaStream_t s);
 void ozaki_free(OzakiPlan* oz);
 // generic Ozaki GEMM over a problem list (used by the projector)
 // `order` selects the tile schedule (0 problem order, 1 longest K first,
 // 2 column tiles outer); each schedule is its own cached plan
 // split_a = false reuses the A digits of this plan's previous call (the
 // caller guarantees that A has not changed since)
+// S digit slices (5 or 3); TN the output tile width (0: ozaki_pick_tn)
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs,
                           const double* A, const double* B, double* C, cudaStream_t s, int order = 0,
-                          bool split_a = true);
+                          bool split_a = true, int S = 5, int TN = 0);
 
 // projector.cu
 struct ProjResult {
@@ -365,6 +372,10 @@ Layout* su2_contract_layout(Ctx* ctx, Layout* A, Layout* B, const std::vector<in
 void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double* b, const std::vector<int>& la,
                   const std::vector<int>& lb, bst_prec prec, double alpha, double beta, Layout* C, double* c,
                   cudaStream_t s);
+inline void require_prec(bst_prec prec) {
+  BST_REQUIRE(prec == BST_FP64 || prec == BST_OZAKI || prec == BST_BF16X3, BST_E_ARG, "unknown precision mode");
+}
+
 inline void require_u1(const Layout* L) {
   if (!is_abelian(L->group))
     throw Error(BST_E_UNSUPPORTED, "this operation is implemented for U(1) and Z2 tensors only");
@@ -373,6 +384,16 @@ inline void require_u1(const Layout* L) {
 // ctm.cpp
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,
               bst_prec prec, bst_ctm_stats* stats, cudaStream_t s);
+
+// ctm.cpp / observe.cu: observables and the CTM error procedure
+Layout* bond_rdm(Ctx* ctx, int bond, Layout* site, const double* sd, bst_env* env, bst_prec prec, double** rho,
+                 cudaStream_t s);
+Layout* double_layer_open(Ctx* ctx, Layout* LA, const double* A, Layout* LR, const double* R, double* out,
+                          cudaStream_t s);
+double block_dot(Ctx* ctx, const double* x, const double* y, int64_t n, cudaStream_t s);
+void ctm_converge(Ctx* ctx, Layout* a, const double* ad, Layout* site, const double* sd, Layout* HL,
+                  const double* H, bst_env* env, int64_t chi0, int64_t chi_max, double tol, int32_t max_steps,
+                  double rel_cutoff, bst_prec prec, bst_ctm_converge_stats* st, cudaStream_t s);
 
 // misc kernels (relayout.cu)
 void launch_scale(Ctx* ctx, double* x, int64_t n, const double* dev_scalar_inv, cudaStream_t s);

@@ -345,4 +345,65 @@ void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int6
   }
 }
 
+// Two-site reduced density matrix of a bond of the one-site cell from its
+// environment (the observable of Sec. 3's error procedure and Sec. 4.1's
+// energies).  The horizontal bond (site i and its right neighbour j) is the
+// 3 x 4 network C1 T1 T1 C2 / T4 a_i a_j T2 / C4 T3 T3 C3 with both sites
+// open: site[L, U, R, D, p, p'] (the open double layer); the vertical bond
+// (i above j) is the horizontal bond of the network turned by a quarter
+// turn.  Left half: ((((C1 T1) T4) C4) T3) a_i -> [T1.R, T3.R, a.R, p, p'];
+// right half: ((((T1 C2) T2) C3) T3) a_j -> [T1.L, T3.L, a.L, p, p']; their
+// product over the three cut bonds is rho[p_i, p_i', p_j, p_j'].
+Layout* bond_rdm(Ctx* ctx, int bond, Layout* site, const double* sd, bst_env* env, bst_prec prec, double** rho,
+                 cudaStream_t s) {
+  BST_REQUIRE(bond == 0 || bond == 1, BST_E_ARG, "bond must be 0 (horizontal) or 1 (vertical)");
+  BST_REQUIRE(site->rank == 6, BST_E_ARG, "the open site must have legs [L, U, R, D, p, p']");
+  require_u1(site);
+  for (int i = 0; i < 4; ++i) {
+    BST_REQUIRE(env->C[i] && env->T[i] && env->c[i] && env->t[i], BST_E_ARG, "env has a null entry");
+    BST_REQUIRE(L_(env->C[i])->group == site->group && L_(env->T[i])->group == site->group, BST_E_ARG,
+                "environment and site belong to different symmetry groups");
+  }
+  const int k = bond;  // quarter turns: the upper site of a vertical bond becomes the left one
+  std::vector<Src> rot = rotation(k);
+  T orig[NROLE], r[NROLE];
+  for (int i = 0; i < 4; ++i) {
+    orig[C1 + i] = {L_(env->C[i]), env->c[i]};
+    orig[T1 + i] = {L_(env->T[i]), env->t[i]};
+  }
+  orig[SITE] = {site, sd};
+  for (int n = 0; n < NROLE; ++n) {
+    std::vector<int> perm = rot[n].perm;
+    if (n == SITE) {
+      perm.push_back(4);  // the physical legs stay last
+      perm.push_back(5);
+    }
+    if (is_identity(perm)) {
+      r[n] = orig[rot[n].role];
+    } else {
+      Layout* dst = nullptr;
+      DevRelayout* rp = get_permute_plan(ctx, orig[rot[n].role].L, perm, &dst);
+      std::string nm = "rdm.rot" + std::to_string(n);
+      double* buf = (double*)ctx->buf(nm, sizeof(double) * std::max<int64_t>(dst->nnz, 1), s);
+      launch_relayout(ctx, *rp, orig[rot[n].role].d, buf, 0, 1.0, 0.0, s);
+      release(dst);  // interned
+      r[n] = {dst, buf};
+    }
+  }
+  T X1 = contract(ctx, "rdm.X1", r[C1], r[T1], {0}, {0}, prec, s);          // [C1.D, T1.D, T1.R]
+  T X2 = contract(ctx, "rdm.X2", X1, r[T4], {0}, {0}, prec, s);             // [T1.D, T1.R, T4.R, T4.D]
+  T X3 = contract(ctx, "rdm.X3", X2, r[C4], {3}, {0}, prec, s);             // [T1.D, T1.R, T4.R, C4.R]
+  T X4 = contract(ctx, "rdm.X4", X3, r[T3], {3}, {0}, prec, s);             // [T1.D, T1.R, T4.R, T3.U, T3.R]
+  T Li = contract(ctx, "rdm.Li", X4, r[SITE], {0, 2, 3}, {1, 0, 3}, prec, s);  // [T1.R, T3.R, a.R, p, p']
+  T Y1 = contract(ctx, "rdm.Y1", r[T1], r[C2], {2}, {0}, prec, s);          // [T1.L, T1.D, C2.D]
+  T Y2 = contract(ctx, "rdm.Y2", Y1, r[T2], {2}, {0}, prec, s);             // [T1.L, T1.D, T2.L, T2.D]
+  T Y3 = contract(ctx, "rdm.Y3", Y2, r[C3], {3}, {0}, prec, s);             // [T1.L, T1.D, T2.L, C3.L]
+  T Y4 = contract(ctx, "rdm.Y4", Y3, r[T3], {3}, {2}, prec, s);             // [T1.L, T1.D, T2.L, T3.L, T3.U]
+  T Rj = contract(ctx, "rdm.Rj", Y4, r[SITE], {1, 2, 4}, {1, 2, 3}, prec, s);  // [T1.L, T3.L, a.L, p, p']
+  T R = contract(ctx, "rdm.rho", Li, Rj, {0, 1, 2}, {0, 1, 2}, prec, s);     // [p_i, p_i', p_j, p_j']
+  *rho = const_cast<double*>(R.d);
+  retain(R.L);
+  return R.L;
+}
+
 }  // namespace bst

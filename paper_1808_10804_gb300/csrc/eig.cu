@@ -71,23 +71,37 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   }
   __syncthreads();
   const int npair = bp / 2;
-  constexpr float kTau = 1e-5f;
+  // diagonal floor of the rotation test: 1e-5 of the scale, or the
+  // convergence floor when that is lower (a graded matrix whose small
+  // entries are accurate: pairs are then rotated relative to their own size)
+  const float kTau = fminf(1e-5f, fmaxf(tfloor, 1e-30f));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test relative to the diagonal (keeps small eigenvalues
     // accurate) with a floor tfloor below which values are not resolved:
     // max_{i<j} a_ij^2 / (max(|a_ii|, tfloor) max(|a_jj|, tfloor)); with a
-    // floor of 1 (the scale) the test is absolute.  Pairs whose diagonal
-    // entries are both below `junk` are left out (a cluster at the FP32
-    // rounding level of the input, where rotations only move noise); one
-    // thread per row
+    // floor of 1 (the scale) the test is absolute.  A pair also counts as
+    // converged once the rotation it still needs is below 1e-6 rad,
+    // a_ij^2 <= 1e-12 (a_ii - a_jj)^2: FP32 rounding keeps a_ij near
+    // 6e-8 max(|a_ii|, |a_jj|), which the relative test cannot pass for a
+    // pair of very different sizes, and the FP64 refinement that follows
+    // converges from such angles.  Pairs whose diagonal entries are both
+    // below `junk` are left out (a cluster at the FP32 rounding level of
+    // the input, where rotations only move noise); one thread per row
     float worst = 0.f;
     for (int i = tid; i < b; i += nt) {
-      const float ai = fabsf(A[i * ld + i]);
+      const float aii = A[i * ld + i];
+      const float ai = fabsf(aii);
       const float di = fmaxf(ai, tfloor);
       for (int j = i + 1; j < b; ++j) {
         const float a = A[i * ld + j];
-        const float aj = fabsf(A[j * ld + j]);
-        if (fmaxf(ai, aj) >= junk) worst = fmaxf(worst, a * a / (di * fmaxf(aj, tfloor)));
+        const float ajj = A[j * ld + j];
+        const float aj = fabsf(ajj);
+        if (fmaxf(ai, aj) >= junk) {
+          const float rel = a * a / (di * fmaxf(aj, tfloor));
+          const float gap = aii - ajj;
+          const float ang = 0.1f * (a * a) / fmaxf(gap * gap, 1e-37f);
+          worst = fmaxf(worst, fminf(rel, ang));
+        }
       }
     }
     red[tid] = worst;
@@ -213,14 +227,16 @@ size_t jacobi_smem(int b) {
 // Ogita-Aishima step, elementwise part.  In: XtX (b x b), S = X^T H X.
 // Out: E (b x b) and lam (b):  R = I - XtX, lam_i = S_ii / (1 - R_ii),
 // E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when the pair is separated,
-// |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|) and not both below
-// junk * max|lam| (values the FP32 stage cannot resolve), else R_ij / 2.
+// |lam_i - lam_j| > rel_delta * max(|lam_i|, |lam_j|) and
+// > acc * sqrt(max|lam|) (sqrt|lam_i| + sqrt|lam_j|) (the rounding of S
+// when it is formed as W^T W, W = N X), and not both below junk * max|lam|
+// (values the FP32 stage cannot resolve), else R_ij / 2.
 // Grid (problem, slice): every CTA forms the b values in shared memory
 // (slice 0 also stores them) and then its slice of the b x b entries, so
 // the FP64 divisions spread over the whole GPU.
 __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __restrict__ XtX,
                           const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam,
-                          double rel_delta, double junk) {
+                          double rel_delta, double junk, double acc) {
   const SmallProb pr = probs[blockIdx.x];
   const int b = pr.b;
   const double* xx = XtX + pr.in_off;
@@ -251,7 +267,8 @@ __global__ void oa_update(const SmallProb* __restrict__ probs, const double* __r
   for (int q = q0 + int(threadIdx.x); q < q1; q += blockDim.x) {
     const int i = q / b, j = q - i * b;
     const double rij = (i == j ? 1.0 : 0.0) - xx[q];
-    const double delta = rel_delta * fmax(fabs(l[i]), fabs(l[j])) + 1e-300 * smax;
+    const double delta = fmax(rel_delta * fmax(fabs(l[i]), fabs(l[j])),
+                              acc * sqrt(smax) * (sqrt(fabs(l[i])) + sqrt(fabs(l[j])))) + 1e-300 * smax;
     const bool unresolved = fabs(l[i]) < junk * smax && fabs(l[j]) < junk * smax;
     double v;
     if (i == j || unresolved || fabs(l[i] - l[j]) <= delta) v = 0.5 * rij;

@@ -37,21 +37,34 @@ namespace bst {
 
 namespace oz {
 
-constexpr int kSlices = 5;
 constexpr int kTM = 128;           // tile rows (M)
-constexpr int kTN = 64;            // tile cols (N)
 constexpr int kTK = 32;            // K per stage (64 bytes of BF16)
-constexpr int kStages = 3;
 constexpr int kABytes = kTM * kTK * 2;   // 8 KB per slice
-constexpr int kBBytes = kTN * kTK * 2;   // 4 KB per slice
-constexpr int kStageBytes = kSlices * (kABytes + kBBytes);
 constexpr int kThreads = 320;            // 10 warps: TMA, MMA, 8 epilogue
-constexpr int kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 28;   // default bound of a pipeline wait (tries)
 constexpr long long kDrainLimit = 1ll << 30;  // bound of the waits for issued copies and products
-// tensor memory columns of the accumulators: d0, d1, d2 double-buffered,
-// d3 and d4 single (5 x 64 + 3 x 64 = 512 columns)
-constexpr int kColD0 = 0, kColD1 = 128, kColD2 = 256, kColD3 = 384;
+
+// Shape of one instantiation: S digit slices per operand (5: the FP64-
+// accurate split; 3: 26 bits, the cheaper arithmetic), output tiles of
+// 128 x TN (TN = 64, or 32 for narrow problems: twice the tiles).
+//   tensor memory: d0, d1, d2 double-buffered (6 TN columns), then for
+//   S = 5 the whole-K diagonals d3 and d4 (2 TN more); allocated as the
+//   next power of two.
+template <int S, int TN>
+struct Cfg {
+  static_assert(S == 5 || S == 3, "digit slices");
+  static_assert(TN == 64 || TN == 32, "tile width");
+  static constexpr int kBBytes = TN * kTK * 2;
+  static constexpr int kStageBytes = S * (kABytes + kBBytes);
+  static constexpr int kStages = (196608 / kStageBytes) < 6 ? (196608 / kStageBytes) : 6;
+  static constexpr int kColD3 = 6 * TN;
+  static constexpr int kCols = 6 * TN + (S - 3) * TN;
+  static constexpr int kTmemCols = kCols <= 256 ? 256 : 512;
+  // C = T 2^(ea + eb - kShift): T = S0 2^27 + S1 2^18 + S2 2^9 + S3 + S4 2^-9
+  // (S = 5) or S0 2^18 + S1 2^9 + S2 (S = 3)
+  static constexpr int kShift = S == 5 ? 43 : 34;
+  static constexpr int kTopBits = 9 * S - 1;  // bits of the scaled integer (44 or 26)
+};
 
 struct Prob {
   int32_t M, N, K, pad;
@@ -143,15 +156,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major.
+template <int TN>
 __host__ __device__ constexpr uint32_t instr_desc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
 }
 
+template <int TN>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(instr_desc()), "r"(acc));
+      "l"(a), "l"(b), "r"(instr_desc<TN>()), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -180,6 +195,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+// kHalf (32 or 16) consecutive columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[32]) { tmem_ld32(taddr, r); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[16]) { tmem_ld16(taddr, r); }
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -190,9 +209,10 @@ __device__ __forceinline__ double pow2i(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+template <int S, int TN>
 struct Smem {
-  alignas(1024) uint8_t stage[kStages][kStageBytes];
-  uint64_t full[kStages], empty[kStages];
+  alignas(1024) uint8_t stage[Cfg<S, TN>::kStages][Cfg<S, TN>::kStageBytes];
+  uint64_t full[Cfg<S, TN>::kStages], empty[Cfg<S, TN>::kStages];
   uint64_t acc_full[2], acc_empty[2];
   uint64_t acc34_empty;  // the epilogue has read d3, d4 of the previous tile
   uint64_t mma_drain;    // abort path: every product issued so far has completed
@@ -208,13 +228,19 @@ struct Smem {
 // epilogue of one tile overlaps the copies and products of the next: d0..d2
 // are double-buffered per pair of chunks, d3 and d4 are released as soon as
 // the epilogue has folded them into its integer accumulators.
+template <int S, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       const Prob* __restrict__ probs, const Tile* __restrict__ tiles, int ntiles,
                       const int* __restrict__ expA, const int* __restrict__ expB, int rowsA, int rowsB,
                       double* __restrict__ C, const Scatter sc, int* err, long long spin) {
+  using CF = Cfg<S, TN>;
+  constexpr int kStages = CF::kStages;
+  constexpr int kStageBytes = CF::kStageBytes;
+  constexpr int kBBytes = CF::kBBytes;
+  constexpr int kColD3 = CF::kColD3;
   extern __shared__ uint8_t smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem<S, TN>& sm = *reinterpret_cast<Smem<S, TN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -234,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                 "r"(kTmemCols));
+                 "r"(CF::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -261,10 +287,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(&sm.full[s], kStageBytes);
           uint8_t* base = sm.stage[s];
           const int k0 = c * kTK;
-          for (int i = 0; i < kSlices; ++i)
+          for (int i = 0; i < S; ++i)
             tma_load_2d(base + i * kABytes, &mapA, k0, i * rowsA + p.arow + t.m0, &sm.full[s]);
-          for (int j = 0; j < kSlices; ++j)
-            tma_load_2d(base + kSlices * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
+          for (int j = 0; j < S; ++j)
+            tma_load_2d(base + S * kABytes + j * kBBytes, &mapB, k0, j * rowsB + p.brow + t.n0, &sm.full[s]);
         }
       }
       // every copy issued has landed before the CTA may exit, whichever
@@ -301,29 +327,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          if (c == 0 && tn > 0 && !mbar_wait(&sm.acc34_empty, (tn - 1) & 1, abort_flag, err, spin)) {
+          if (S == 5 && c == 0 && tn > 0 && !mbar_wait(&sm.acc34_empty, (tn - 1) & 1, abort_flag, err, spin)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(sm.stage[s]);
-          const uint32_t b0 = a0 + kSlices * kABytes;
+          const uint32_t b0 = a0 + S * kABytes;
           for (int ks = 0; ks < kTK / 16; ++ks) {
-            for (int d = 0; d <= 4; ++d) {
+            for (int d = 0; d < S; ++d) {
               for (int i = 0; i <= d; ++i) {
                 const int j = d - i;
                 uint32_t col;
                 uint32_t acc;
                 if (d <= 2) {
-                  col = kColD0 + d * 2 * kTN + buf * kTN;
+                  col = d * 2 * TN + buf * TN;
                   acc = (!first || ks > 0 || i > 0) ? 1u : 0u;
                 } else {
-                  col = kColD3 + (d - 3) * kTN;
+                  col = kColD3 + (d - 3) * TN;
                   acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
                 }
                 const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
                 const uint64_t bd = smem_desc(b0 + j * kBBytes + ks * 32);
-                mma_bf16(tmem + col, ad, bd, acc);
+                mma_bf16<TN>(tmem + col, ad, bd, acc);
               }
             }
           }
@@ -343,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: warps 2..9 ----------------
     // warp w may access tensor-memory lanes 32*(w%4)..+31; the two warps of a
     // lane quarter split the 64 columns
-    constexpr int kHalf = kTN / 2;
+    constexpr int kHalf = TN / 2;
     const int q = warp & 3;
     const int c0 = ((warp - 2) >> 2) * kHalf;
     const int row = q * 32 + lane;
@@ -365,17 +391,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = mbar_wait(&sm.acc_full[buf], int(pc >> 1) & 1, abort_flag, err, spin);
         if (!ok) break;
         tc_fence_after();
-        uint32_t v[32];
+        uint32_t v[kHalf];
         // exact FP32 integers below 2^24: one round-to-nearest conversion each
-        tmem_ld32(lane_base + kColD0 + buf * kTN + c0, v);
+        tmem_ld_cols(lane_base + 0 * 2 * TN + buf * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
-        tmem_ld32(lane_base + kColD1 + buf * kTN + c0, v);
+        tmem_ld_cols(lane_base + 1 * 2 * TN + buf * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
-        tmem_ld32(lane_base + kColD2 + buf * kTN + c0, v);
+        tmem_ld_cols(lane_base + 2 * 2 * TN + buf * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));
@@ -384,23 +410,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       pg += npair;
-      // X = S0 2^27 + S1 2^18 + S2 2^9 + (S3 + S4 2^-9), folded into T; then
-      // d3 and d4 are released to the next tile's products
+      // S = 5: X = S0 2^27 + S1 2^18 + S2 2^9 + (S3 + S4 2^-9), folded into
+      // T; then d3 and d4 are released to the next tile's products
+      if constexpr (S == 5) {
 #pragma unroll
-      for (int h = 0; h < kHalf / 16; ++h) {
-        uint32_t w3[16], w4[16];
-        if (nk > 0) {
-          tmem_ld16(lane_base + kColD3 + 0 * kTN + c0 + h * 16, w3);
-          tmem_ld16(lane_base + kColD3 + 1 * kTN + c0 + h * 16, w4);
-          tmem_wait_ld();
-        } else {
+        for (int h = 0; h < kHalf / 16; ++h) {
+          uint32_t w3[16], w4[16];
+          if (nk > 0) {
+            tmem_ld16(lane_base + kColD3 + 0 * TN + c0 + h * 16, w3);
+            tmem_ld16(lane_base + kColD3 + 1 * TN + c0 + h * 16, w4);
+            tmem_wait_ld();
+          } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) w3[j] = w4[j] = 0u;
-        }
+            for (int j = 0; j < 16; ++j) w3[j] = w4[j] = 0u;
+          }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float small = __uint_as_float(w3[j]) + __uint_as_float(w4[j]) * (1.0f / 512.0f);
-          T[h * 16 + j] = (T[h * 16 + j] << 9) + __float2ll_rn(small);
+          for (int j = 0; j < 16; ++j) {
+            const float small = __uint_as_float(w3[j]) + __uint_as_float(w4[j]) * (1.0f / 512.0f);
+            T[h * 16 + j] = (T[h * 16 + j] << 9) + __float2ll_rn(small);
+          }
         }
       }
       tc_fence_before();
@@ -422,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (row_ok && gn < p.N) {
             const int4 ci = sc.coltab[p.ct_off + gn];
             const long long dst = bb[ci.x] + (long long)ri.y * ci.z + ci.y;
-            const int e = ea + expB[p.brow + gn] - 43;
+            const int e = ea + expB[p.brow + gn] - CF::kShift;
             const double v = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
             if (plain) C[dst] = v;
             else C[dst] = sc.beta == 0.0 ? sc.alpha * v : fma(sc.alpha, v, sc.beta * C[dst]);
@@ -434,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int jj = 0; jj < kHalf; ++jj) {
           const int gn = t.n0 + c0 + jj;
           if (row_ok && gn < p.N) {
-            const int e = ea + expB[p.brow + gn] - 43;
+            const int e = ea + expB[p.brow + gn] - CF::kShift;
             crow[(long long)gn * p.c_n] = (double)T[jj] * pow2i(e >> 1) * pow2i(e - (e >> 1));
           }
         }
@@ -445,12 +473,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::kTmemCols));
   }
 }
 
-// Split FP64 rows into the five BF16 digit slices (integer arithmetic on the
-// bit pattern).  One warp per row; digits for k in [K, roundup(K, 32)) are 0.
+// Split FP64 rows into S BF16 digit slices (integer arithmetic on the bit
+// pattern).  One warp per row; digits for k in [K, roundup(K, 32)) are 0.
 // One launch splits both operands: CTAs [0, ga) take the rows of A, the
 // others those of B.  The task of a row is found by binary search over the
 // tasks' first rows (ascending).
@@ -462,13 +490,14 @@ struct SplitJob {
   int* ex;
 };
 
+template <int S>
 __global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch) {
   const bool is_a = int(blockIdx.x) < ga;
   const SplitJob& J = is_a ? ja : jb;
   const SplitTask* __restrict__ tasks = J.tasks;
   const int ntasks = J.ntasks, rows_total = J.rows_total;
   const double* __restrict__ X = J.X;
-  __nv_bfloat16* __restrict__ S = J.S;
+  __nv_bfloat16* __restrict__ Sd = J.S;
   int* __restrict__ ex = J.ex;
   const int warp_g = ((int(blockIdx.x) - (is_a ? 0 : ga)) * int(blockDim.x) + int(threadIdx.x)) >> 5;
   const int lane = threadIdx.x & 31;
@@ -508,8 +537,8 @@ __global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch)
       const int E = int((b >> 52) & 0x7FF);
       if (E != 0) {  // subnormals of a row with a normal maximum are below 2^-44 of it
         const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-        // X = round(m * 2^(E - 1075 - e + 44))
-        const int sh = E - 1075 - e + 44;
+        // X = round(m * 2^(E - 1075 - e + 9 S - 1)), |X| < 2^(9 S - 1)
+        const int sh = E - 1075 - e + 9 * S - 1;
         if (sh >= 0) {
           Xi = m << sh;
         } else if (sh > -64) {
@@ -519,18 +548,18 @@ __global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch)
         if (b >> 63) Xi = -Xi;
       }
     }
-    // signed digits: X = a0 2^36 + a1 2^27 + a2 2^18 + a3 2^9 + a4, |a_i| <= 256
-    int dig[kSlices];
+    // signed digits: X = sum_i a_i 2^(9 (S - 1 - i)), |a_i| <= 256
+    int dig[S];
 #pragma unroll
-    for (int i = kSlices - 1; i >= 1; --i) {
+    for (int i = S - 1; i >= 1; --i) {
       long long lo = ((Xi + 256) & 511) - 256;
       dig[i] = int(lo);
       Xi = (Xi - lo) >> 9;
     }
     dig[0] = int(Xi);
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i)
-      S[((long long)i * rows_total + grow) * kpitch + k] = __int2bfloat16_rn(dig[i]);
+    for (int i = 0; i < S; ++i)
+      Sd[((long long)i * rows_total + grow) * kpitch + k] = __int2bfloat16_rn(dig[i]);
   }
 }
 
@@ -570,6 +599,7 @@ static CUtensorMap make_map(void* base, int kpitch, int rows, int box_rows) {
 }
 
 struct OzakiPlan {
+  int S = 5, TN = 64;  // digit slices per operand, output tile width
   int nprobs = 0, ntiles = 0;
   int rowsA = 0, rowsB = 0, kpitch = 32;
   oz::Prob* d_probs = nullptr;
@@ -585,7 +615,7 @@ struct OzakiPlan {
   bool ab_same = false;
   CUtensorMap mapBA;
   double flops = 0;
-  double split_bytes = 0;  // FP64 read + 5 BF16 digits written per element, exponent per row
+  double split_bytes = 0;  // FP64 read + S BF16 digits written per element, exponent per row
   // K == 0 problems (no matched block pair): written as zeros by a separate
   // launch, so every tile of the persistent GEMM has at least one K chunk
   // (its epilogue then always waits for products of that tile, which keeps
@@ -627,7 +657,17 @@ __global__ void zero_probs_kernel(const GemmProb* __restrict__ zp, double* __res
   }
 }
 
-static size_t smem_bytes() { return sizeof(oz::Smem) + 1024; }
+template <int S, int TN>
+static size_t smem_bytes() { return sizeof(oz::Smem<S, TN>) + 1024; }
+
+template <int S, int TN>
+static void set_kernel_attrs() {
+  static bool done = false;
+  if (done) return;
+  BST_CUDA(cudaFuncSetAttribute(oz::ozaki_gemm_kernel<S, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem_bytes<S, TN>())));
+  done = true;
+}
 
 // streaming multiprocessors of the current device (one persistent CTA each)
 static int num_sms() {
@@ -650,8 +690,11 @@ struct ScatterSpec {
 };
 
 static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int order = 0,
-                             const ScatterSpec* sc = nullptr) {
+                             const ScatterSpec* sc = nullptr, int S = 5, int TN = 64) {
+  BST_REQUIRE((S == 5 || S == 3) && (TN == 64 || TN == 32), BST_E_ARG, "Ozaki GEMM: unsupported shape");
   auto* P = new OzakiPlan();
+  P->S = S;
+  P->TN = TN;
   std::vector<oz::Prob> hp;
   std::vector<oz::Tile> ht;
   std::vector<oz::SplitTask> sa, sb;
@@ -691,14 +734,14 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
     if (g.K == 0) {
       zp.push_back(g);
     } else if (order == 2) {
-      for (int n0 = 0; n0 < g.N; n0 += oz::kTN)
+      for (int n0 = 0; n0 < g.N; n0 += TN)
         for (int m0 = 0; m0 < g.M; m0 += oz::kTM) ht.push_back({pi, m0, n0, 0});
     } else {
       for (int m0 = 0; m0 < g.M; m0 += oz::kTM)
-        for (int n0 = 0; n0 < g.N; n0 += oz::kTN) ht.push_back({pi, m0, n0, 0});
+        for (int n0 = 0; n0 < g.N; n0 += TN) ht.push_back({pi, m0, n0, 0});
     }
     P->flops += 2.0 * double(g.M) * g.N * g.K;
-    P->split_bytes += double(g.M + g.N) * g.K * (8.0 + 2.0 * oz::kSlices) + 4.0 * (g.M + g.N);
+    P->split_bytes += double(g.M + g.N) * g.K * (8.0 + 2.0 * S) + 4.0 * (g.M + g.N);
   }
   if (order == 1)
     std::stable_sort(ht.begin(), ht.end(),
@@ -707,7 +750,7 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   P->ntiles = int(ht.size());
   P->nsa = int(sa.size());
   P->nsb = int(sb.size());
-  BST_REQUIRE(int64_t(P->rowsA) * oz::kSlices < (1ll << 31) && int64_t(P->rowsB) * oz::kSlices < (1ll << 31),
+  BST_REQUIRE(int64_t(P->rowsA) * S < (1ll << 31) && int64_t(P->rowsB) * S < (1ll << 31),
               BST_E_UNSUPPORTED, "Ozaki GEMM: too many rows");
   auto up = [](auto** dst, const auto& v) {
     using T = typename std::remove_reference<decltype(v)>::type::value_type;
@@ -731,10 +774,10 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
       if (hp[i].K == 0) zi.push_back(i);
     up(&P->d_zidx, zi);
   }
-  // split buffers: 5 slices x rows x kpitch BF16, with room for a full tile
+  // split buffers: S slices x rows x kpitch BF16, with room for a full tile
   // past the end so TMA boxes of the last rows stay inside the allocation
-  const int64_t ra = int64_t(oz::kSlices) * std::max(P->rowsA, 1) + oz::kTM;
-  const int64_t rb = int64_t(oz::kSlices) * std::max(P->rowsB, 1) + oz::kTN;
+  const int64_t ra = int64_t(S) * std::max(P->rowsA, 1) + oz::kTM;
+  const int64_t rb = int64_t(S) * std::max(P->rowsB, 1) + std::max(TN, oz::kTM);
   BST_CUDA(cudaMalloc(&P->SA, sizeof(__nv_bfloat16) * ra * P->kpitch));
   BST_CUDA(cudaMalloc(&P->SB, sizeof(__nv_bfloat16) * rb * P->kpitch));
   BST_CUDA(cudaMemset(P->SA, 0, sizeof(__nv_bfloat16) * ra * P->kpitch));
@@ -742,14 +785,8 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   BST_CUDA(cudaMalloc(&P->eA, sizeof(int) * std::max(P->rowsA, 1)));
   BST_CUDA(cudaMalloc(&P->eB, sizeof(int) * std::max(P->rowsB, 1)));
   P->mapA = make_map(P->SA, P->kpitch, int(ra), oz::kTM);
-  P->mapB = make_map(P->SB, P->kpitch, int(rb), oz::kTN);
-  if (P->ab_same) P->mapBA = make_map(P->SA, P->kpitch, int(ra), oz::kTN);
-  static bool attr = false;
-  if (!attr) {
-    BST_CUDA(cudaFuncSetAttribute(oz::ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(smem_bytes())));
-    attr = true;
-  }
+  P->mapB = make_map(P->SB, P->kpitch, int(rb), TN);
+  if (P->ab_same) P->mapBA = make_map(P->SA, P->kpitch, int(ra), TN);
   return P;
 }
 
@@ -789,21 +826,52 @@ static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, d
     if (ga + gb > 0) {
       const oz::SplitJob ja{P->d_sa, P->nsa, P->rowsA, A, P->SA, P->eA};
       const oz::SplitJob jb{P->d_sb, P->nsb, P->rowsB, B, P->SB, P->eB};
-      oz::ozaki_split_kernel<<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
+      if (P->S == 5) oz::ozaki_split_kernel<5><<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
+      else oz::ozaki_split_kernel<3><<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
     }
     BST_CUDA(cudaGetLastError());
     count_launch(ctx, (wa + wb) > 0 ? 1 : 0);
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
   const int grid = std::min(P->ntiles, num_sms());
-  oz::ozaki_gemm_kernel<<<grid, oz::kThreads, smem_bytes(), s>>>(
-      P->mapA, b_from_a ? P->mapBA : P->mapB, P->d_probs, P->d_tiles, P->ntiles, P->eA, b_from_a ? P->eA : P->eB,
-      P->rowsA, P->rowsB, C, sc, ctx->d_err, ctx->spin_limit > 0 ? ctx->spin_limit : oz::kSpinLimit);
+  const long long spin = ctx->spin_limit > 0 ? ctx->spin_limit : oz::kSpinLimit;
+  const CUtensorMap& mB = b_from_a ? P->mapBA : P->mapB;
+  const int* eB = b_from_a ? P->eA : P->eB;
+  auto launch = [&](auto kern, size_t smem) {
+    kern<<<grid, oz::kThreads, smem, s>>>(P->mapA, mB, P->d_probs, P->d_tiles, P->ntiles, P->eA, eB, P->rowsA,
+                                           P->rowsB, C, sc, ctx->d_err, spin);
+  };
+  if (P->S == 5 && P->TN == 64) {
+    set_kernel_attrs<5, 64>();
+    launch(oz::ozaki_gemm_kernel<5, 64>, smem_bytes<5, 64>());
+  } else if (P->S == 5) {
+    set_kernel_attrs<5, 32>();
+    launch(oz::ozaki_gemm_kernel<5, 32>, smem_bytes<5, 32>());
+  } else if (P->TN == 64) {
+    set_kernel_attrs<3, 64>();
+    launch(oz::ozaki_gemm_kernel<3, 64>, smem_bytes<3, 64>());
+  } else {
+    set_kernel_attrs<3, 32>();
+    launch(oz::ozaki_gemm_kernel<3, 32>, smem_bytes<3, 32>());
+  }
   BST_CUDA(cudaGetLastError());
   count_launch(ctx);
 }
 
-void ozaki_prepare(Ctx* ctx, ContractPlan* p) { p->oz = build_plan(ctx, p->probs); }
+int ozaki_slices(bst_prec prec) { return prec == BST_BF16X3 ? 3 : 5; }
+
+int ozaki_pick_tn(const std::vector<GemmProb>& probs) {
+  int64_t tiles64 = 0;
+  double cols = 0, cols64 = 0;
+  for (auto& g : probs) {
+    if (g.K == 0) continue;
+    tiles64 += int64_t((g.M + oz::kTM - 1) / oz::kTM) * ((g.N + 63) / 64);
+    cols += double(g.N);
+    cols64 += double((g.N + 63) / 64 * 64);
+  }
+  if (tiles64 == 0) return 64;
+  return (tiles64 < num_sms() || cols < 0.5 * cols64) ? 32 : 64;
+}
 
 // Plan whose epilogue writes every product element into the output
 // tensor's canonical block (Sec. 2: the reduced pair products land in the
@@ -811,7 +879,7 @@ void ozaki_prepare(Ctx* ctx, ContractPlan* p) { p->oz = build_plan(ctx, p->probs
 // legs then B's, so the block of (row config r, column config c) is a
 // row-major [rows of r x columns of c] matrix: element (m, n) of a sector
 // goes to offset(r, c) + mi * width(c) + ni.
-void ozaki_prepare_scatter(Ctx* ctx, ContractPlan* p) {
+static OzakiPlan* prepare_scatter(Ctx* ctx, ContractPlan* p, int S) {
   ScatterSpec sc;
   const Layout* C = p->C;
   std::vector<int32_t> tup(C->rank);
@@ -847,26 +915,32 @@ void ozaki_prepare_scatter(Ctx* ctx, ContractPlan* p) {
   BST_REQUIRE(pi == p->probs.size(), BST_E_SHAPE, "scatter plan: problem count mismatch");
   BST_REQUIRE(sc.rowtab.size() < (size_t(1) << 31) && sc.coltab.size() < (size_t(1) << 31), BST_E_UNSUPPORTED,
               "scatter plan: too many rows");
-  p->ozs = build_plan(ctx, p->probs, 0, &sc);
+  return build_plan(ctx, p->probs, 0, &sc, S, ozaki_pick_tn(p->probs));
 }
 
-void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* c,
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* c,
                             double alpha, double beta, cudaStream_t s) {
-  run_plan(ctx, p->ozs, Amat, Bmat, c, s, true, alpha, beta);
+  OzakiPlan*& P = p->oz[S == 3 ? 1 : 0][1];
+  if (!P) P = prepare_scatter(ctx, p, S);
+  run_plan(ctx, P, Amat, Bmat, c, s, true, alpha, beta);
 }
 
-void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, const double* Amat, const double* Bmat, double* Cmat,
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* Cmat,
                     cudaStream_t s) {
-  run_plan(ctx, p->oz, Amat, Bmat, Cmat, s);
+  OzakiPlan*& P = p->oz[S == 3 ? 1 : 0][0];
+  if (!P) P = build_plan(ctx, p->probs, 0, nullptr, S, ozaki_pick_tn(p->probs));
+  run_plan(ctx, P, Amat, Bmat, Cmat, s);
 }
 
 void ozaki_free(OzakiPlan* oz) { delete oz; }
 
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
-                          const double* B, double* C, cudaStream_t s, int order, bool split_a) {
+                          const double* B, double* C, cudaStream_t s, int order, bool split_a, int S, int TN) {
+  if (TN == 0) TN = ozaki_pick_tn(probs);
   // plans live in the context (freed with it), keyed by caller tag, problem
-  // list and tile schedule
-  const std::string key = tag + "/" + std::to_string(probs_hash(probs)) + "/" + std::to_string(order);
+  // list, tile schedule, digit count and tile width
+  const std::string key = tag + "/" + std::to_string(probs_hash(probs)) + "/" + std::to_string(order) + "/" +
+                          std::to_string(S) + "x" + std::to_string(TN);
   OzakiPlan* P;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -874,7 +948,7 @@ void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<Ge
     P = it == ctx->ozplans.end() ? nullptr : it->second.get();
   }
   if (!P) {
-    std::shared_ptr<OzakiPlan> np(build_plan(ctx, probs, order));
+    std::shared_ptr<OzakiPlan> np(build_plan(ctx, probs, order, nullptr, S, TN));
     P = np.get();
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->ozplans[key] = std::move(np);

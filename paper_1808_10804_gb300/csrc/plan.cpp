@@ -111,8 +111,9 @@ ContractPlan::~ContractPlan() {
   rb.free_all();
   rc.free_all();
   g.free_all();
-  if (oz) ozaki_free(oz);
-  if (ozs) ozaki_free(ozs);
+  for (auto& row : oz)
+    for (OzakiPlan* q : row)
+      if (q) ozaki_free(q);
   release(A);
   release(B);
   release(C);
@@ -208,8 +209,7 @@ void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, b
   launch_relayout(ctx, p->rb, b, Bm, 0, 1.0, 0.0, s);
   if (prec != BST_FP64 && scatter && !cmat_out) {
     // the tensor-core GEMM's epilogue writes C's blocks directly
-    if (!p->ozs) ozaki_prepare_scatter(ctx, p);
-    run_gemm_ozaki_scatter(ctx, p, Am, Bm, c, alpha, beta, s);
+    run_gemm_ozaki_scatter(ctx, p, ozaki_slices(prec), Am, Bm, c, alpha, beta, s);
     return;
   }
   double* Cm = (double*)ctx->buf(cmat_out ? "contract.Ckeep" : "contract.C",
@@ -217,8 +217,7 @@ void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, b
   if (prec == BST_FP64) {
     launch_gemm_f64(ctx, p->g, Am, Bm, Cm, s);
   } else {
-    if (!p->oz) ozaki_prepare(ctx, p);
-    run_gemm_ozaki(ctx, p, Am, Bm, Cm, s);
+    run_gemm_ozaki(ctx, p, ozaki_slices(prec), Am, Bm, Cm, s);
   }
   if (scatter) launch_relayout(ctx, p->rc, c, Cm, 1, alpha, beta, s);
   if (cmat_out) *cmat_out = Cm;

@@ -116,7 +116,7 @@ struct ResProb {
   int64_t y_off, v_off, val_off, ld;
 };
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
-__global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double);
+__global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double, double);
 __global__ void add_inplace(double*, const double*, long long);
 __global__ void cholinv_f32(const SmallProb*, const double*, double*, int*, const float*, int);
 struct GramProb {
@@ -239,18 +239,21 @@ struct PSec {
   int b;           // small problem size
   int64_t q_off, z_off, sm_off, val_off;
   int64_t kmax;    // most states the truncation can keep from this sector (0: chi)
+  int64_t u_off;   // left vectors, row-major M x c, from the full SVD (-1: none)
 };
 
-// The small eigensolver resolves a sector's eigenvalues of N^T N below
-// 1e-6 of its largest only to ~1e-9 of the largest (one unresolved
-// cluster): singular values below sqrt(1e-5) of the sector's largest (a
-// tenfold margin) cannot decide the truncation.  True when the smallest
-// kept value kmin falls in that range of a sector that has values above
-// it: the candidates are then recomputed by the full FP64 SVD.
+// The small eigensolver of an iterated sector resolves its eigenvalues of
+// N^T N below 1e-6 of its largest only to ~1e-9 of the largest (one
+// unresolved cluster): singular values below sqrt(1e-5) of the sector's
+// largest (a tenfold margin) cannot decide the truncation.  A direct
+// sector's graded solve resolves eigenvalues down to ~1e-12 of its largest
+// (margin: 1e-11).  True when the smallest kept value kmin falls in that
+// range of a sector that has values above it: the candidates are then
+// recomputed by the full FP64 SVD.
 static bool cut_unresolved(const PSec& x, const std::vector<double>& hSig, double kmin) {
   if (x.c <= 0) return false;
   const double top = hSig[x.s_off];  // candidates are sorted descending
-  return top > kmin && kmin * kmin < 1e-5 * top * top;
+  return top > kmin && kmin * kmin < (x.direct ? 1e-11 : 1e-5) * top * top;
 }
 
 static void setup_attrs() {
@@ -277,9 +280,25 @@ static void setup_attrs() {
 // the singular values they converge to, so only close pairs still mix); the
 // first, absolute Jacobi pass and the rotation into its basis are skipped
 // and the relative pass starts from H itself.
+// Graded solves (`gr` set): H_i = N_i^T N_i of a sector matrix N_i
+// (M_i x b_i, row-major at noff_i of Nm).  An eigenvector of a small
+// eigenvalue lambda computed from H itself carries the rounding of H,
+// eps lambda_max, over the gap: with lambda = sigma^2 the singular vectors
+// at the truncation of a fast-decaying spectrum lose about as many digits
+// as sigma_1^2 / sigma^2 has.  Here only the first, absolute FP32 pass uses
+// H; the matrices of the second pass and of the refinement are formed as
+// W^T W with W = N X, whose entries are accurate to eps sigma_1 (sigma_i +
+// sigma_j), i.e. relative to the singular values themselves (the accuracy
+// of an SVD of N), and that pass rotates pairs relative to their own size.
+struct Graded {
+  const double* Nm;
+  std::vector<int> M;
+  std::vector<int64_t> noff;
+};
+
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
                       int64_t smtot, int64_t valtot, cudaStream_t s, const std::string& pre = "",
-                      bool near_diag = false) {
+                      bool near_diag = false, const Graded* gr = nullptr) {
   if (sp.empty()) return;
   setup_attrs();
   SmallProb* dsp = upload_cached(ctx, pre + "eig.sp", sp, s);
@@ -302,13 +321,48 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     g_s.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));       // X^T T
     g_xe.push_back(gp(b, b, b, o, b, 1, o, 1, b, o, b, 1));      // X E
   }
+  // graded: W = N X and W^T W per problem
+  std::vector<GemmProb> g_w, g_ww;
+  double* Wg = nullptr;
+  if (gr) {
+    BST_REQUIRE(gr->M.size() == sp.size() && gr->noff.size() == sp.size(), BST_E_ARG, "graded solve tables");
+    int64_t wtot = 0;
+    for (size_t i = 0; i < sp.size(); ++i) {
+      const int b = sp[i].b;
+      const int64_t o = sp[i].in_off;
+      g_w.push_back(gp(gr->M[i], b, b, gr->noff[i], b, 1, o, 1, b, wtot, b, 1));  // W = N X
+      g_ww.push_back(gp(b, b, gr->M[i], wtot, 1, b, wtot, 1, b, o, b, 1));        // W^T W
+      wtot += int64_t(gr->M[i]) * b;
+    }
+    Wg = (double*)ctx->buf(pre + "eig.w", sizeof(double) * std::max<int64_t>(wtot, 1), s);
+  }
   // nominal work of one Jacobi launch at its sweep limit: per sweep b-1
   // rounds of b/2 rotations, each touching 2 rows and 2 columns of A and V
   double jac_flops = 0;
   for (auto& p : sp) jac_flops += 7.0 * double(p.b) * p.b * 18.0 * p.b / 2.0;
-  if (near_diag) {
+  if (gr && !near_diag) {
+    {
+      ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
+      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
+    gemm_any(ctx, pre + "oa.w", prec, g_w, gr->Nm, X1, Wg, s, false, ws);
+    gemm_any(ctx, pre + "oa.ww", prec, g_ww, Wg, Wg, H1, s, false, ws);
+    {
+      ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
+      // pairs below 1e-14 of the largest (beyond the accuracy of H1) are
+      // left out of the convergence test
+      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 10, 1e-20f, 1e-14f);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
+    gemm_any(ctx, pre + "oa.xe", prec, g_xe, X1, T, X, s, false, ws);  // X = X1 X2
+  } else if (near_diag) {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 10, 1e-5f, 0.f);
+    // values below 1e-6 of the largest are not resolved by this FP32 pass
+    // (nor refined below): their pairs are left out of the convergence test
+    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 10, 1e-5f, 1e-6f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   } else {
@@ -330,11 +384,21 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   }
   for (int it = 0; it < 2; ++it) {
     gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
-    gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
-    gemm_any(ctx, pre + "oa.s", prec, g_s, X, T, S, s, false, ws);
+    if (gr) {
+      // S = (N X)^T (N X): accurate relative to the singular values, so
+      // every pair above eps sigma_1 is refined
+      gemm_any(ctx, pre + "oa.w", prec, g_w, gr->Nm, X, Wg, s, false, ws);
+      gemm_any(ctx, pre + "oa.ww", prec, g_ww, Wg, Wg, S, s, false, ws);
+    } else {
+      gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
+      gemm_any(ctx, pre + "oa.s", prec, g_s, X, T, S, s, false, ws);
+    }
     // about two CTAs per SM over all problems
     const int slices = std::max(1, std::min(64, 304 / int(sp.size())));
-    oa_update<<<dim3(unsigned(sp.size()), unsigned(slices)), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9, 1e-6);
+    // graded: the FP32 passes resolve eigenvalues down to ~1e-12 of the
+    // largest; S is accurate to ~eps sigma_1 (sigma_i + sigma_j)
+    oa_update<<<dim3(unsigned(sp.size()), unsigned(slices)), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9,
+                                                                          gr ? 1e-12 : 1e-6, gr ? 1e-13 : 0.0);
     gemm_any(ctx, pre + "oa.xe", prec, g_xe, X, E, T, s, false, ws);
     add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
     BST_CUDA(cudaGetLastError());
@@ -383,6 +447,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     return int(std::min<int64_t>(kEigMax, std::max<int64_t>(64, (k + k / 2 + 16 + 31) / 32 * 32)));
   };
   for (auto& x : secs) {
+    x.u_off = -1;
     x.direct = x.N <= kEigMax;
     x.b = x.direct ? x.N : block_of(x);
     x.c = x.b;
@@ -565,8 +630,13 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   bool forked = false;
   if (!g_direct.empty() && !defer) {
     std::vector<SmallProb> sp_dir;
+    Graded gdir{Nm, {}, {}};
     for (auto& x : secs)
-      if (x.direct) sp_dir.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
+      if (x.direct) {
+        sp_dir.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
+        gdir.M.push_back(x.M);
+        gdir.noff.push_back(x.cs->off);
+      }
     if (!ctx->side) {
       BST_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
       BST_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -578,7 +648,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     BST_CUDA(cudaEventRecord(ctx->ev_fork, s));
     BST_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     gemm_any(ctx, "side.ss.direct", rr, g_direct, Nm, Nm, Msm, ctx->side, false, "side.gemm_f64.splitk");
-    small_eig(ctx, rr, sp_dir, Msm, Xv, lam, smtot, valtot, ctx->side, "side.");
+    small_eig(ctx, rr, sp_dir, Msm, Xv, lam, smtot, valtot, ctx->side, "side.", false, &gdir);
     BST_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     forked = true;
   }
@@ -643,6 +713,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       if (defer) {
         std::vector<GemmProb> g_rel;
         std::vector<SmallProb> sp_rel;
+        Graded grel{Nm, {}, {}};
         for (size_t t = 0; t < dir_idx.size(); ++t) {
           const PSec& x = secs[dir_idx[t]];
           if (below[t]) {
@@ -653,11 +724,13 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
             const int64_t no = x.cs->off;
             g_rel.push_back(gp(x.N, x.N, x.M, no, 1, x.N, no, 1, x.N, x.sm_off, x.N, 1));  // N^T N
             sp_rel.push_back(SmallProb{x.b, 0, x.sm_off, x.sm_off, x.val_off});
+            grel.M.push_back(x.M);
+            grel.noff.push_back(no);
           }
         }
         if (!sp_rel.empty()) {
           gemm_any(ctx, "ss.direct.late", rr, g_rel, Nm, Nm, Msm, s);
-          small_eig(ctx, rr, sp_rel, Msm, Xv, lam, smtot, valtot, s, "late.");
+          small_eig(ctx, rr, sp_rel, Msm, Xv, lam, smtot, valtot, s, "late.", false, &grel);
           for (size_t t = 0; t < dir_idx.size(); ++t)
             if (!below[t]) {
               const PSec& x = secs[dir_idx[t]];
@@ -763,7 +836,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
 // Full FP64 SVD of every sector with cuSOLVER (gesvd); used for sectors the
 // small eigensolver cannot hold.
 static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>& secs, double*& dV,
-                          std::vector<double>& hSig, cudaStream_t s) {
+                          double*& dUl, std::vector<double>& hSig, cudaStream_t s) {
   if (!ctx->cusolver) {
     cusolverDnHandle_t h;
     BST_CUSOLVER(cusolverDnCreate(&h));
@@ -771,7 +844,7 @@ static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>&
   }
   cusolverDnHandle_t h = (cusolverDnHandle_t)ctx->cusolver;
   BST_CUSOLVER(cusolverDnSetStream(h, s));
-  int64_t stot = 0, utot = 0, vtot = 0, vt2 = 0;
+  int64_t stot = 0, utot = 0, vtot = 0, vt2 = 0, ultot = 0;
   int lwork = 0, maxmn = 1;
   std::vector<int64_t> u_off(secs.size()), vt_off(secs.size());
   for (size_t i = 0; i < secs.size(); ++i) {
@@ -786,6 +859,8 @@ static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>&
     vt2 += int64_t(mn) * mn;
     x.v_off = vtot;
     vtot += int64_t(x.N) * mn;
+    x.u_off = ultot;
+    ultot += int64_t(x.M) * mn;
     const bool trans = x.N >= x.M;
     int m = trans ? x.N : x.M, n = trans ? x.M : x.N, lw = 0;
     BST_CUSOLVER(cusolverDnDgesvd_bufferSize(h, m, n, &lw));
@@ -799,6 +874,7 @@ static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>&
   double* dR = (double*)ctx->buf("proj.rwork", sizeof(double) * maxmn, s);
   double* dX = (double*)ctx->buf("proj.X", sizeof(double) * std::max<int64_t>(cmat, 1), s);
   dV = (double*)ctx->buf("proj.V2", sizeof(double) * std::max<int64_t>(vtot, 1), s);
+  dUl = (double*)ctx->buf("proj.Ul", sizeof(double) * std::max<int64_t>(ultot, 1), s);
   int* dInfo = (int*)ctx->buf("proj.info", sizeof(int) * secs.size(), s);
   BST_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int) * secs.size(), s));
   {
@@ -813,16 +889,22 @@ static void factors_gesvd(Ctx* ctx, double* Nm, int64_t cmat, std::vector<PSec>&
         BST_CUDA(cudaMemcpyAsync(Y, Nm + x.cs->off, sizeof(double) * int64_t(x.M) * x.N, cudaMemcpyDeviceToDevice, s));
         BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.N, x.M, Y, x.N, dS + x.s_off, dU + u_off[i], x.N,
                                       dVT + vt_off[i], mn, dW, lwork, dR, dInfo + i));
-        // V (row-major N x mn) from col-major Ux (N x mn): V[r][j] = Ux[r + j N]
+        // V (row-major N x mn) from col-major Ux (N x mn): V[r][j] = Ux[r + j N];
+        // the left vectors of N_s are the rows of VTx: U[r][j] = VTx[j + r mn],
+        // the same memory order as row-major M x mn
         launch_transpose(dU + u_off[i], dV + x.v_off, mn, x.N, s);
+        BST_CUDA(cudaMemcpyAsync(dUl + x.u_off, dVT + vt_off[i], sizeof(double) * int64_t(x.M) * mn,
+                                 cudaMemcpyDeviceToDevice, s));
       } else {
         // col-major Y = N_s [M x N]; Y = Uy S VTy, right vectors = rows of VTy
         launch_transpose(Nm + x.cs->off, Y, x.M, x.N, s);
         BST_CUSOLVER(cusolverDnDgesvd(h, 'S', 'S', x.M, x.N, Y, x.M, dS + x.s_off, dU + u_off[i], x.M,
                                       dVT + vt_off[i], mn, dW, lwork, dR, dInfo + i));
-        // V[r][j] = VTy[j + r mn]: the same memory order
+        // V[r][j] = VTy[j + r mn]: the same memory order; U (row-major
+        // M x mn) from col-major Uy (M x mn)
         BST_CUDA(cudaMemcpyAsync(dV + x.v_off, dVT + vt_off[i], sizeof(double) * int64_t(x.N) * mn,
                                  cudaMemcpyDeviceToDevice, s));
+        launch_transpose(dU + u_off[i], dUl + x.u_off, mn, x.M, s);
       }
       count_launch(ctx, 2);
     }
@@ -848,6 +930,10 @@ void sym_eig_batched(Ctx* ctx, int n, int batch, const double* H, double* X, dou
 ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, const double* rb, int ncut,
                          int64_t chi, double rel_cutoff, int new_flow, bst_prec prec, double* p, double* pt,
                          cudaStream_t s) {
+  // the subspace iterations and eigensolver resolve singular values far
+  // below the largest: the cheaper three-slice arithmetic does not reach
+  // them, so the projector runs in the five-slice one
+  if (prec == BST_BF16X3) prec = BST_OZAKI;
   BST_REQUIRE(ncut >= 1 && ncut < Rt->rank && ncut < Rb->rank, BST_E_ARG, "bad ncut");
   BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
   BST_REQUIRE(new_flow == 1 || new_flow == -1, BST_E_ARG, "new_flow must be +1 or -1");
@@ -884,6 +970,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   launch_sumsq(ctx, Nm, pn->cmat, dss, s);
   launch_scale(ctx, Nm, pn->cmat, dss, s);
   double* dV = nullptr;
+  double* dUl = nullptr;  // left vectors of the full SVD (gesvd path)
   std::vector<double> hSig;
   double nscale = 0;
   struct Cand { double sv; int q; int sec; int j; };
@@ -903,7 +990,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
       ProfScope ps(ctx, s, "proj_subspace", 0.0, 0.0);
       done = factors_subspace(ctx, Nm, secs, chi, prec, ctx->proj_iters, dV, hSig, s);
     }
-    if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, hSig, s);
+    if (!done) factors_gesvd(ctx, Nm, pn->cmat, secs, dV, dUl, hSig, s);
     from_subspace = done;
     if (attempt == 0) {
       double nss = 0;
@@ -939,6 +1026,19 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
         }
         BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
         count_launch(ctx, int(secs.size()));
+        if (!done) {
+          // the full SVD's left vectors follow
+          int64_t utot = 0;
+          for (auto& x : secs) utot = std::max(utot, x.u_off + int64_t(x.M) * x.c);
+          double* tmpu = (double*)ctx->buf("proj.Uperm", sizeof(double) * std::max<int64_t>(utot, 1), s);
+          po = 0;
+          for (auto& x : secs) {
+            permute_cols<<<x.M, 128, 0, s>>>(dUl + x.u_off, tmpu + x.u_off, x.c, dperm + po);
+            po += x.c;
+          }
+          BST_CUDA(cudaMemcpyAsync(dUl, tmpu, sizeof(double) * utot, cudaMemcpyDeviceToDevice, s));
+          count_launch(ctx, int(secs.size()));
+        }
         if (done) {
           // the Rayleigh-Ritz vectors W of the iterated sectors follow V
           // (V = Q W), so that N V = (N Q) W column by column below
@@ -1065,6 +1165,7 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     // factors_subspace); for an iterated sector N V = (N Q) W with N Q the
     // final Rayleigh-Ritz product, still in its buffer: M x k x b in place
     // of M x k x N
+    if (x.u_off >= 0) continue;  // the full SVD gave the left vectors
     if (from_subspace && !x.direct)
       guz.push_back(gp(x.M, k, x.b, x.z_off, x.b, 1, x.sm_off, 1, x.b, ur_off[i], k, 1));
     else
@@ -1078,8 +1179,14 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     const PSec& x = secs[i];
     const int k = kcount[i];
     if (k == 0) continue;
-    gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i], k,
-                                         Us + uo, Vs + vo, 1, nscale);
+    // left vectors: those of the full SVD (consistent with its right
+    // vectors to the SVD's own backward error), else u = N v / sigma
+    if (x.u_off >= 0)
+      gauge_scale_kernel<<<k, 256, 0, s>>>(dUl + x.u_off, x.c, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i],
+                                           k, Us + uo, Vs + vo, 0, nscale);
+    else
+      gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i],
+                                           k, Us + uo, Vs + vo, 1, nscale);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
     const int key = int(x.cs->key);
@@ -1129,6 +1236,7 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
                          int64_t chi_total, double rel_cutoff, bst_prec prec, double** p_out, double** pt_out,
                          cudaStream_t s) {
   BST_REQUIRE(Rt->group == BST_SU2 && Rb->group == BST_SU2, BST_E_ARG, "SU(2) projector needs SU(2) tensors");
+  if (prec == BST_BF16X3) prec = BST_OZAKI;  // as for U(1)
   BST_REQUIRE(ncut >= 1 && ncut < Rt->rank && ncut < Rb->rank, BST_E_ARG, "bad ncut");
   BST_REQUIRE(chi_total >= 1, BST_E_ARG, "chi must be positive");
   std::vector<int> cut(ncut);
@@ -1236,6 +1344,7 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   BST_REQUIRE(!secs.empty(), BST_E_NUMERIC, "projector: no non-empty sector");
   double* dV = nullptr;
   std::vector<double> hSig;
+  double* dUl = nullptr;
   double nscale = 0, smax = 0, kmin = 0;
   std::vector<int> kcount;
   int64_t kept_dim = 0, kept = 0;
@@ -1248,7 +1357,7 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
       // chi-th largest may still be kept: no sector is skipped
       done = factors_subspace(ctx, Nm, secs, chi_total, prec, ctx->proj_iters, dV, hSig, s, false);
     }
-    if (!done) factors_gesvd(ctx, Nm, ntot, secs, dV, hSig, s);
+    if (!done) factors_gesvd(ctx, Nm, ntot, secs, dV, dUl, hSig, s);
     if (attempt == 0) {
       double nss = 0;
       BST_CUDA(cudaMemcpy(&nss, dss, sizeof(double), cudaMemcpyDeviceToHost));
@@ -1278,6 +1387,18 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
       }
       BST_CUDA(cudaMemcpyAsync(dV, tmpv, sizeof(double) * vtot, cudaMemcpyDeviceToDevice, s));
       count_launch(ctx, int(secs.size()));
+      if (!done) {
+        int64_t utot = 0;
+        for (auto& x : secs) utot = std::max(utot, x.u_off + int64_t(x.M) * x.c);
+        double* tmpu = (double*)ctx->buf("proj.Uperm", sizeof(double) * std::max<int64_t>(utot, 1), s);
+        po = 0;
+        for (auto& x : secs) {
+          permute_cols<<<x.M, 128, 0, s>>>(dUl + x.u_off, tmpu + x.u_off, x.c, dperm + po);
+          po += x.c;
+        }
+        BST_CUDA(cudaMemcpyAsync(dUl, tmpu, sizeof(double) * utot, cudaMemcpyDeviceToDevice, s));
+        count_launch(ctx, int(secs.size()));
+      }
     }
     struct Cand { double sv; int tJ; int sec; int j; };
     std::vector<Cand> cand;
@@ -1355,6 +1476,7 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     const int k = kcount[i];
     if (k == 0) continue;
     const PSec& x = secs[i];
+    if (x.u_off >= 0) continue;  // the full SVD gave the left vectors
     gu.push_back(gp(x.M, k, x.N, x.cs->off, x.N, 1, x.v_off, 1, x.c, ur_off[i], k, 1));
   }
   gemm_any(ctx, "proj.u", BST_FP64, gu, Nm, dV, Ur, s);
@@ -1362,8 +1484,12 @@ ProjResult su2_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
     const PSec& x = secs[i];
     const int k = kcount[i];
     if (k == 0) continue;
-    gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i], k,
-                                         Us + ur_off[i], Vs + vs_off[i], 1, nscale);
+    if (x.u_off >= 0)
+      gauge_scale_kernel<<<k, 256, 0, s>>>(dUl + x.u_off, x.c, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i],
+                                           k, Us + ur_off[i], Vs + vs_off[i], 0, nscale);
+    else
+      gauge_scale_kernel<<<k, 256, 0, s>>>(Ur + ur_off[i], k, 1, x.M, dV + x.v_off, x.c, 1, x.N, dSk + sk_off[i],
+                                           k, Us + ur_off[i], Vs + vs_off[i], 1, nscale);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }

@@ -700,7 +700,8 @@ void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double*
     if (prec == BST_FP64) {
       launch_gemm_f64(ctx, p->g, p->Am, p->Bm, p->P, s);
     } else {
-      run_gemm_ozaki_probs(ctx, "su2/" + std::to_string(uintptr_t(p)), p->probs, p->Am, p->Bm, p->P, s);
+      run_gemm_ozaki_probs(ctx, "su2/" + std::to_string(uintptr_t(p)), p->probs, p->Am, p->Bm, p->P, s, 0, true,
+                           ozaki_slices(prec));
     }
   }
   if (p->nchunks) {

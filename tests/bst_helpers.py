@@ -94,3 +94,18 @@ def matched_pair_flops(a_legs, la, b_legs, lb):
                 n = int(np.prod([sb[j] for j in range(len(sb)) if j not in lb]))
                 tot += 2 * m * k * n
     return tot
+
+
+def bf16x3_bound(Am, Bm):
+    """Elementwise error bound of the three-slice tensor-core product
+    C = Am Bm (Am: rows x K, Bm: K x cols, dense, zeros outside the
+    allowed blocks).  Each operand row (column) is scaled by 2^e with
+    max|x| < 2^e <= 2 max|x| and rounded to 26 bits, |x - x^| <= 2^(e-27);
+    the six kept slice products are summed exactly and the three dropped
+    ones (weights 2^-27, 2^-27, 2^-36 of the leading one, digits <= 2^8 in
+    magnitude) add at most 2^(ea+eb-26) per k, so every k contributes at
+    most 2^(ea+eb-25) <= 2^-23 max|a_i.| max|b_.j|."""
+    K = Am.shape[1]
+    amax = np.abs(Am).max(axis=1)
+    bmax = np.abs(Bm).max(axis=0)
+    return 2.0 ** -23 * K * np.outer(amax, bmax)

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import u1  # noqa: E402
 from workloads import batched_site_legs, batched_u1_configs, values  # noqa: E402
-from bst_helpers import rel_err  # noqa: E402
+from bst_helpers import bf16x3_bound, rel_err  # noqa: E402
 
 LEGS_X2 = (0, 2)   # X2[k_u, x_r, k_l, x_d]: k_u, k_l
 LEGS_A = (1, 0)    # a[k_l, k_u, k_r, k_d]:  k_u, k_l
@@ -91,6 +91,25 @@ def test_batched_matches_oracle(bst, ctx, prec, tol):
         assert not np.any(ref[~u1.allowed_mask(q_legs)])
         err = rel_err(c.cpu().numpy(), u1.from_dense(q_legs, ref))
         assert err <= tol, (cfg["name"], prec, err)
+
+
+def test_batched_bf16x3_within_bound(bst, ctx):
+    """The batch in the cheaper three-slice arithmetic: every element of
+    every entry within the bound of its rounding (bf16x3_bound)."""
+    cfgs = small_configs(6)
+    inst = [gpu_instance(bst, ctx, c) for c in cfgs]
+    Cls, cs = run_batch(ctx, inst, "bf16x3")
+    torch.cuda.synchronize()
+    for cfg, L, c in zip(cfgs, Cls, cs):
+        x2_legs, x2, a_legs, a, q_legs = oracle_instance(cfg)
+        ref = np.einsum("uxly,luzw->xyzw", x2, a)
+        assert same_legs(L.legs, q_legs)
+        nu, nx, nl, ny = x2.shape
+        Am = np.transpose(x2, (1, 3, 0, 2)).reshape(nx * ny, nu * nl)
+        Bm = np.transpose(a, (1, 0, 2, 3)).reshape(nu * nl, -1)
+        bound = bf16x3_bound(Am, Bm)
+        got = u1.to_dense(q_legs, c.cpu().numpy()).reshape(nx * ny, -1)
+        assert np.all(np.abs(got - ref.reshape(nx * ny, -1)) <= bound + 1e-300), cfg["name"]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "ozaki"])

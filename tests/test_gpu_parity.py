@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 from oracle import ctm as octm  # noqa: E402
 from oracle import u1  # noqa: E402
 from workloads import u1_config, values  # noqa: E402
-from bst_helpers import check_blocks, gpu_network, matched_pair_flops, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
+from bst_helpers import bf16x3_bound, check_blocks, gpu_network, matched_pair_flops, rel_err, to_bst_leg, to_oracle_leg  # noqa: E402
 
 TOL64 = 1e-12
 
@@ -157,6 +157,43 @@ def test_contract_ozaki_matches_oracle(bst, ctx, seed, maxdeg):
     want2 = u1.from_dense(c_legs, ref2)
     # compare row by row (rows of C follow rows of A)
     assert rel_err(got, want2) < TOL_OZ
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("maxdeg", [3, 40, 90])
+def test_contract_bf16x3_within_bound(bst, ctx, seed, maxdeg):
+    """The cheaper three-slice arithmetic: every element within the bound
+    of its rounding (bf16x3_bound), through the plain and the alpha/beta
+    epilogue, with both output tile widths in play (narrow sectors take
+    128 x 32 tiles); the error is above FP64 level, so the three-slice
+    kernel is the one that ran."""
+    rng = np.random.default_rng(700 + seed)
+    shared = rand_legs(rng, 2, maxdeg)
+    ao = rand_legs(rng, 1, maxdeg)
+    bo = rand_legs(rng, 1, maxdeg)
+    a_legs = [ao[0], shared[0], shared[1]]
+    b_legs = [shared[1].dual(), bo[0], shared[0].dual()]
+    A = u1.to_dense(a_legs, rng.standard_normal(u1.nnz(a_legs)))
+    B = u1.to_dense(b_legs, rng.standard_normal(u1.nnz(b_legs)))
+    la, lb = [1, 2], [2, 0]
+    ref = np.tensordot(A, B, axes=(la, lb))
+    Am = A.reshape(A.shape[0], -1)
+    Bm = np.transpose(B, (2, 0, 1)).reshape(-1, B.shape[1])
+    bound = bf16x3_bound(Am, Bm)
+    AL, ad = upload(bst, ctx, a_legs, A)
+    BL, bd = upload(bst, ctx, b_legs, B)
+    CL, cd = ctx.contract(AL, ad, BL, bd, la, lb, prec="bf16x3")
+    ctx.sync()
+    c_legs = [a_legs[0], b_legs[1]]
+    got = u1.to_dense(c_legs, cd.cpu().numpy())
+    assert np.all(np.abs(got - ref) <= bound + 1e-300)
+    if np.abs(ref).max() > 0 and Am.shape[1] > 8:
+        assert rel_err(got, ref) > 1e-13
+    c2 = cd.clone()
+    ctx.contract(AL, ad, BL, bd, la, lb, prec="bf16x3", alpha=2.0, beta=-0.5, Cl=CL, c=c2)
+    ctx.sync()
+    got2 = u1.to_dense(c_legs, c2.cpu().numpy())
+    assert np.all(np.abs(got2 - (2.0 * ref - 0.5 * got)) <= 2.0 * bound + 1e-12 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("seed", range(4))
