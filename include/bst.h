@@ -331,16 +331,20 @@ BST_API bst_status bst_contract_noalloc(bst_ctx ctx, bst_layout A, const double*
  * bst_contract would compute it.  A, a, B, b, C, c are HOST arrays of
  * nbatch entries: layouts (A[i], B[i] any structure; C[i] the layout
  * bst_contract_layout returns for A[i], B[i]) and device data pointers.
- * All sector matrices of all contractions go through one gather launch per
- * operand, one grouped GEMM (FP64 or the mixed-precision tensor-core GEMM,
- * per `prec`) and one scatter, whatever nbatch is.  The first call with a
- * given list of layouts builds and caches the plan, and the first call with
- * a given list of data pointers uploads a pointer table (both allocate and
- * synchronise); a repeated call launches four kernels (six for BST_OZAKI:
- * the two operand splits come in addition) and nothing else, so it may be
- * captured into a CUDA graph and replayed.
+ * Whatever nbatch is, the tensor-core arithmetics (BST_OZAKI, BST_BF16X3)
+ * take two launches when every operand's last contracted leg (in pair
+ * order) is its innermost leg: one gathers every operand row of every
+ * contraction from its blocks and splits it into digits, one grouped GEMM
+ * writes every output block in its epilogue (alpha, beta applied there);
+ * otherwise three: one gather of both operands' sector matrices, one split,
+ * the GEMM.  BST_FP64 takes one gather, one grouped DMMA GEMM and one
+ * scatter.  The first call with a given list of layouts builds and
+ * caches the plan, and the first call with a given list of data pointers
+ * uploads a pointer table (both allocate and synchronise); a repeated call
+ * launches those kernels and nothing else, so it may be captured into a
+ * CUDA graph and replayed.
  * The c[i] must not overlap one another or any input (they are written
- * concurrently).  Errors: BST_E_ARG (NULL entries, nbatch < 1),
+ * concurrently), and must be 8-byte aligned.  Errors: BST_E_ARG (NULL entries, nbatch < 1),
  * BST_E_SYMMETRY (a leg pair does not match), BST_E_SHAPE (C[i] wrong). */
 BST_API bst_status bst_contract_batched(bst_ctx ctx, int32_t nbatch, const bst_layout* A, const double* const* a,
                                         const bst_layout* B, const double* const* b, int32_t npairs,

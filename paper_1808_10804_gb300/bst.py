@@ -378,7 +378,8 @@ class Context:
     def contract_batched(self, As, as_, Bs, bs, legsA, legsB, prec="fp64", alpha=1.0, beta=0.0, Cls=None,
                          cs=None, stream=None):
         """Independent contractions cs[i] = alpha*As[i]·Bs[i] + beta*cs[i] in
-        one launch per stage (gather A, gather B, grouped GEMM, scatter)."""
+        one launch per stage (tensor cores: pack, GEMM with the output
+        scatter in its epilogue; FP64: gather A, gather B, GEMM, scatter)."""
         n = len(As)
         if Cls is None:
             Cls = [self.contract_layout(A, B, legsA, legsB) for A, B in zip(As, Bs)]

@@ -1,17 +1,23 @@
 // Batched contractions: many independent contractions (uneven sector sizes)
-// in one launch per stage -- one gather of every A, one of every B, one
-// grouped GEMM over the sector matrices of all of them, one scatter of every
-// C.  The matched block pairs of all contractions form one task list, so the
-// GPU is filled even when each contraction alone is small (Sec. 2: the
-// block pairs are independent, "straightforward to parallelise over").
+// in a few launches for all of them.  The matched block pairs of every
+// contraction form one problem list, so the GPU is filled even when each
+// contraction alone is small (Sec. 2: the block pairs of a contraction are
+// independent of one another, and so are separate contractions).
 //
-// The per-contraction plans are the cached single-contraction plans; the
-// batch plan concatenates their sector matrices into three combined buffers
-// and tags every relayout task with the index of its tensor, whose device
-// address comes from a small pointer table.  Each distinct set of data
-// pointers gets its own table, uploaded once and kept with the plan, so a
-// repeated call uploads nothing and a captured CUDA graph of it stays valid
-// while other pointer sets are used in between.
+// Tensor-core arithmetic: two launches.  One pack launch gathers the rows
+// of every contraction's operand sector matrices straight from the operand
+// tensors and splits them into digits (each segment carries the index of
+// its tensor in a device pointer table); one GEMM launch over all problems
+// writes every product into its contraction's output blocks (the scatter
+// tables address each output relative to the first output's pointer).
+// FP64: one gather per operand into combined sector-matrix buffers, one
+// grouped DMMA GEMM, one scatter.
+//
+// The per-contraction plans are the cached single-contraction plans.  Each
+// distinct set of data pointers gets its own pointer table (and output
+// offsets), uploaded once and kept with the plan, so a repeated call
+// uploads nothing and a captured CUDA graph of it stays valid while other
+// pointer sets are used in between.
 #include <algorithm>
 #include <cstring>
 
@@ -44,7 +50,10 @@ struct BatchRel {
 struct BatchPlan {
   std::vector<ContractPlan*> plans;
   int64_t amat = 0, bmat = 0, cmat = 0;
-  BatchRel ra, rb, rc;
+  // one gather of both operands (B's tasks point past A's matrices and at
+  // the second half of the pointer table), the FP64 path's scatter
+  BatchRel rab, rc;
+  bool packed = false;  // every contraction ozaki_packable
   std::vector<GemmProb> probs;
   DevGemm g;
   // schedule chosen by the autotuner (defaults until tuned)
@@ -55,18 +64,32 @@ struct BatchPlan {
   int order[3] = {0, 0, 0};
   int tn[3] = {0, 0, 0};
   // data pointers (a[0..n), b[0..n), c[0..n)) -> device copy of that table
-  std::map<std::vector<const void*>, double**> tables;
-  // the plan's own sector-matrix buffers: a captured graph of this batch
-  // keeps valid addresses for as long as the plan (the context) lives
+  // and, once a tensor-core call has used it, the output block offsets
+  // relative to c[0]
+  struct PtrSet {
+    double** bases = nullptr;
+    long long* bbase = nullptr;
+  };
+  std::map<std::vector<const void*>, PtrSet> tables;
+  // tensor-core plans by digit count, tile width and tile order, and the
+  // scatter offsets they share (inside each output, and its contraction)
+  std::map<std::string, OzakiPlan*> ozp;
+  std::vector<long long> bb_rel;
+  std::vector<int32_t> bb_src;
+  // the plan's own sector-matrix buffers (Bm = Am + amat): a captured graph
+  // of this batch keeps valid addresses for as long as the plan (the
+  // context) lives
   double *Am = nullptr, *Bm = nullptr, *Cm = nullptr;
   ~BatchPlan() {
     cudaFree(Am);
-    cudaFree(Bm);
     cudaFree(Cm);
-    ra.free_all();
-    rb.free_all();
+    rab.free_all();
     rc.free_all();
-    for (auto& kv : tables) cudaFree(kv.second);
+    for (auto& kv : tables) {
+      cudaFree(kv.second.bases);
+      cudaFree(kv.second.bbase);
+    }
+    for (auto& kv : ozp) ozaki_free(kv.second);
     g.free_all();
   }
 };
@@ -116,6 +139,15 @@ static void launch_rel(Ctx* ctx, const BatchRel& r, double* const* bases, double
   count_launch(ctx);
 }
 
+static OzakiPlan* batch_oz(Ctx* ctx, BatchPlan* bp, int order, int S, int TN) {
+  const std::string key = std::to_string(S) + "/" + std::to_string(TN) + "/" + std::to_string(order);
+  auto it = bp->ozp.find(key);
+  if (it != bp->ozp.end()) return it->second;
+  OzakiPlan* P = ozaki_batch_plan(ctx, bp->plans, bp->probs, order, S, TN, bp->packed, &bp->bb_rel, &bp->bb_src);
+  bp->ozp[key] = P;
+  return P;
+}
+
 // Median over `reps` timed runs of f (after one untimed run), in ms.
 template <class F>
 static float time_ms(cudaStream_t s, int reps, F&& f) {
@@ -148,26 +180,23 @@ static float time_ms(cudaStream_t s, int reps, F&& f) {
 //   and, for the tensor-core GEMM, the output tile shape (128 x 64, or
 //   128 x 32: twice the tiles, half the padding of narrow sectors).
 static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bst_prec prec, const std::string& tag,
-                     cudaStream_t s) {
+                     cudaStream_t s, const std::vector<Layout*>& C) {
   const bool prof = ctx->prof;
   ctx->prof = false;
   char line[256];
-  if (!bp->tuned_rel) {
+  if (!bp->tuned_rel && !(prec != BST_FP64 && bp->packed)) {
     float best = 1e30f;
     int bc = 2048;
     for (int c : kChunkChoices) {
-      upload_rel(bp->ra, c);
-      upload_rel(bp->rb, c);
+      upload_rel(bp->rab, c);
       const float t = time_ms(s, 3, [&] {
-        launch_rel(ctx, bp->ra, bases, bp->Am, 0, 1.0, 0.0, s);
-        launch_rel(ctx, bp->rb, bases + n, bp->Bm, 0, 1.0, 0.0, s);
+        launch_rel(ctx, bp->rab, bases, bp->Am, 0, 1.0, 0.0, s);
       });
       snprintf(line, sizeof(line), "batch %p relayout chunk %d: %.4f ms\n", (void*)bp, c, t);
       ctx->tune_log += line;
       if (t < best) best = t, bc = c;
     }
-    upload_rel(bp->ra, bc);
-    upload_rel(bp->rb, bc);
+    upload_rel(bp->rab, bc);
     upload_rel(bp->rc, bc);
     snprintf(line, sizeof(line), "batch %p relayout chunk chosen %d\n", (void*)bp, bc);
     ctx->tune_log += line;
@@ -175,8 +204,22 @@ static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bs
   }
   const int pi = int(prec);
   if (!bp->tuned[pi]) {
-    launch_rel(ctx, bp->ra, bases, bp->Am, 0, 1.0, 0.0, s);
-    launch_rel(ctx, bp->rb, bases + n, bp->Bm, 0, 1.0, 0.0, s);
+    if (!(prec != BST_FP64 && bp->packed)) launch_rel(ctx, bp->rab, bases, bp->Am, 0, 1.0, 0.0, s);
+    // the tensor-core candidates write every output through the scatter
+    // epilogue: while tuning they write a scratch copy of the outputs
+    double* scratch = nullptr;
+    long long* sbb = nullptr;
+    if (prec != BST_FP64) {
+      batch_oz(ctx, bp, 0, ozaki_slices(prec), 64);  // the shared scatter offsets
+      int64_t tot = 0;
+      std::vector<int64_t> coff(n);
+      for (size_t i = 0; i < n; ++i) coff[i] = tot, tot += C[i]->nnz;
+      std::vector<long long> abs(bp->bb_rel.size());
+      for (size_t j = 0; j < abs.size(); ++j) abs[j] = bp->bb_rel[j] + coff[bp->bb_src[j]];
+      BST_CUDA(cudaMalloc(&scratch, sizeof(double) * std::max<int64_t>(tot, 1)));
+      BST_CUDA(cudaMalloc(&sbb, sizeof(long long) * std::max<size_t>(abs.size(), 1)));
+      BST_CUDA(cudaMemcpy(sbb, abs.data(), sizeof(long long) * abs.size(), cudaMemcpyHostToDevice));
+    }
     const int norders = prec == BST_FP64 ? 2 : 3;
     const int S = ozaki_slices(prec);
     const char* kname = prec == BST_FP64 ? "gemm_f64" : "gemm_ozaki";
@@ -190,9 +233,8 @@ static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bs
           bp->g.upload(bp->probs, kF64TileM, kF64TileN, o);
           t = time_ms(s, 3, [&] { launch_gemm_f64(ctx, bp->g, bp->Am, bp->Bm, bp->Cm, s); });
         } else {
-          t = time_ms(s, 3, [&] {
-            run_gemm_ozaki_probs(ctx, tag, bp->probs, bp->Am, bp->Bm, bp->Cm, s, o, true, S, tn);
-          });
+          OzakiPlan* P = batch_oz(ctx, bp, o, S, tn);
+          t = time_ms(s, 3, [&] { run_ozaki_batch(ctx, P, bases, int(n), bp->Am, bp->Bm, scratch, sbb, 1.0, 0.0, s); });
         }
         snprintf(line, sizeof(line), "batch %p %s tile 128x%d order %d: %.4f ms\n", (void*)bp, kname,
                  prec == BST_FP64 ? kF64TileN : tn, o, t);
@@ -201,6 +243,11 @@ static void autotune(Ctx* ctx, BatchPlan* bp, double* const* bases, size_t n, bs
       }
     }
     if (prec == BST_FP64) bp->g.upload(bp->probs, kF64TileM, kF64TileN, bo);
+    if (scratch) {
+      BST_CUDA(cudaStreamSynchronize(s));
+      cudaFree(scratch);
+      cudaFree(sbb);
+    }
     bp->order[pi] = bo;
     bp->tn[pi] = btn;
     bp->tuned[pi] = true;
@@ -227,15 +274,19 @@ static BatchPlan* get_batch_plan(Ctx* ctx, const std::vector<Layout*>& A, const 
   }
   auto bp = std::make_shared<BatchPlan>();
   bp->plans = plans;
+  const int32_t n = int32_t(plans.size());
+  std::vector<BatchTask> btasks;
+  bp->packed = true;
   for (size_t i = 0; i < plans.size(); ++i) {
     ContractPlan* p = plans[i];
+    bp->packed = bp->packed && ozaki_packable(p);
     for (auto t : p->va.tasks) {
       t.mat_base += bp->amat;
-      bp->ra.host.push_back({t, int32_t(i), 0});
+      bp->rab.host.push_back({t, int32_t(i), 0});
     }
     for (auto t : p->vb.tasks) {
-      t.mat_base += bp->bmat;
-      bp->rb.host.push_back({t, int32_t(i), 0});
+      t.mat_base += bp->bmat;  // shifted past A's matrices below
+      btasks.push_back({t, n + int32_t(i), 0});
     }
     for (auto t : p->vc.tasks) {
       t.mat_base += bp->cmat;
@@ -251,12 +302,15 @@ static BatchPlan* get_batch_plan(Ctx* ctx, const std::vector<Layout*>& A, const 
     bp->bmat += p->bmat;
     bp->cmat += p->cmat;
   }
-  upload_rel(bp->ra, 2048);
-  upload_rel(bp->rb, 2048);
+  for (auto& t : btasks) {
+    t.t.mat_base += bp->amat;
+    bp->rab.host.push_back(t);
+  }
+  upload_rel(bp->rab, 2048);
   upload_rel(bp->rc, 2048);
   bp->g.upload(bp->probs, kF64TileM, kF64TileN);
-  BST_CUDA(cudaMalloc(&bp->Am, sizeof(double) * std::max<int64_t>(bp->amat, 1)));
-  BST_CUDA(cudaMalloc(&bp->Bm, sizeof(double) * std::max<int64_t>(bp->bmat, 1)));
+  BST_CUDA(cudaMalloc(&bp->Am, sizeof(double) * std::max<int64_t>(bp->amat + bp->bmat, 1)));
+  bp->Bm = bp->Am + bp->amat;
   BST_CUDA(cudaMalloc(&bp->Cm, sizeof(double) * std::max<int64_t>(bp->cmat, 1)));
   BatchPlan* raw = bp.get();
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -281,32 +335,38 @@ void contract_batched(Ctx* ctx, const std::vector<Layout*>& A, const std::vector
   for (size_t i = 0; i < n; ++i) ptrs.push_back(a[i]);
   for (size_t i = 0; i < n; ++i) ptrs.push_back(b[i]);
   for (size_t i = 0; i < n; ++i) ptrs.push_back(c[i]);
-  double** bases = nullptr;
   auto it = bp->tables.find(ptrs);
-  if (it != bp->tables.end()) {
-    bases = it->second;
-  } else {
+  if (it == bp->tables.end()) {
     // first call with this pointer set: allocate and fill its table (not
     // capturable; later calls with the same pointers only launch)
-    BST_CUDA(cudaMalloc(&bases, sizeof(void*) * ptrs.size()));
-    BST_CUDA(cudaMemcpy(bases, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice));
-    bp->tables[ptrs] = bases;
+    BatchPlan::PtrSet ps;
+    BST_CUDA(cudaMalloc(&ps.bases, sizeof(void*) * ptrs.size()));
+    BST_CUDA(cudaMemcpy(ps.bases, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice));
+    it = bp->tables.emplace(ptrs, ps).first;
   }
+  double** bases = it->second.bases;
   const std::string tag = "batch/" + std::to_string(uintptr_t(bp));
-  if (ctx->autotune) autotune(ctx, bp, bases, n, prec, tag, s);
-  double *Am = bp->Am, *Bm = bp->Bm, *Cm = bp->Cm;
+  if (ctx->autotune) autotune(ctx, bp, bases, n, prec, tag, s, C);
   ctx->work_flops += bp->g.flops;
-  launch_rel(ctx, bp->ra, bases, Am, 0, 1.0, 0.0, s);
-  launch_rel(ctx, bp->rb, bases + n, Bm, 0, 1.0, 0.0, s);
   if (prec == BST_FP64) {
-    launch_gemm_f64(ctx, bp->g, Am, Bm, Cm, s);
-  } else {
-    // the same grouped tensor-core GEMM as a single contraction, over the
-    // problems of all contractions
-    run_gemm_ozaki_probs(ctx, tag, bp->probs, Am, Bm, Cm, s, bp->order[int(prec)], true, ozaki_slices(prec),
-                         bp->tn[int(prec)]);
+    launch_rel(ctx, bp->rab, bases, bp->Am, 0, 1.0, 0.0, s);
+    launch_gemm_f64(ctx, bp->g, bp->Am, bp->Bm, bp->Cm, s);
+    launch_rel(ctx, bp->rc, bases + 2 * n, bp->Cm, 1, alpha, beta, s);
+    return;
   }
-  launch_rel(ctx, bp->rc, bases + 2 * n, Cm, 1, alpha, beta, s);
+  // packed: one pack launch over every operand; else one gather of both
+  // operands and one split; then one GEMM whose epilogue writes every
+  // output block (alpha, beta applied there)
+  if (!bp->packed) launch_rel(ctx, bp->rab, bases, bp->Am, 0, 1.0, 0.0, s);
+  const int pi = int(prec);
+  OzakiPlan* P = batch_oz(ctx, bp, bp->order[pi], ozaki_slices(prec), bp->tn[pi] ? bp->tn[pi] : ozaki_pick_tn(bp->probs));
+  if (!it->second.bbase) {
+    std::vector<long long> abs;
+    ozaki_batch_bbase(bp->bb_rel, bp->bb_src, c, &abs);
+    BST_CUDA(cudaMalloc(&it->second.bbase, sizeof(long long) * std::max<size_t>(abs.size(), 1)));
+    BST_CUDA(cudaMemcpy(it->second.bbase, abs.data(), sizeof(long long) * abs.size(), cudaMemcpyHostToDevice));
+  }
+  run_ozaki_batch(ctx, P, bases, int(n), bp->Am, bp->Bm, c[0], it->second.bbase, alpha, beta, s);
 }
 
 }  // namespace bst

@@ -312,15 +312,33 @@ int ozaki_slices(bst_prec prec);
 // output tile width for a problem list: 64, or 32 when 128 x 64 tiles
 // would leave SMs idle or pad narrow problems by more than half
 int ozaki_pick_tn(const std::vector<GemmProb>& probs);
+// The contraction plan's operands a, b (tensor data) are read by the pack
+// kernel, which gathers each sector-matrix row from the blocks and splits it
+// into digits in one pass.
 // plain variant: the epilogue writes the sector matrices Cmat
-void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* Cmat,
-                    cudaStream_t s);
+// (Am, Bm: the operands' sector matrices when the caller has gathered them)
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* a, const double* b, double* Cmat,
+                    cudaStream_t s, const double* Am = nullptr, const double* Bm = nullptr);
 // scatter variant: the epilogue writes c = alpha * A B + beta * c straight
 // into the output tensor's canonical blocks (no sector matrix, no scatter
 // launch)
-void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* c,
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* a, const double* b, double* c,
                             double alpha, double beta, cudaStream_t s);
 void ozaki_free(OzakiPlan* oz);
+// batched contractions (batch.cu): one packed plan whose epilogue scatters
+// into every contraction's output (see gemm_ozaki.cu)
+// pack: operands gathered and split by the pack kernel (every plan
+// ozaki_packable), else split from the gathered sector matrices
+bool ozaki_packable(const ContractPlan* p);
+OzakiPlan* ozaki_batch_plan(Ctx* ctx, const std::vector<ContractPlan*>& plans, const std::vector<GemmProb>& probs,
+                            int order, int S, int TN, bool pack, std::vector<long long>* bbase_rel,
+                            std::vector<int32_t>* bbase_src);
+void ozaki_batch_bbase(const std::vector<long long>& rel, const std::vector<int32_t>& src,
+                       const std::vector<double*>& c, std::vector<long long>* out);
+// bases: device table a[0..n), b[0..n) (packed plans) or Am, Bm: the
+// gathered sector matrices; c0 = c[0]; bbase from ozaki_batch_bbase
+void run_ozaki_batch(Ctx* ctx, OzakiPlan* P, double* const* bases, int n, const double* Am, const double* Bm,
+                     double* c0, const long long* bbase, double alpha, double beta, cudaStream_t s);
 // generic Ozaki GEMM over a problem list (used by the projector)
 // `order` selects the tile schedule (0 problem order, 1 longest K first,
 // 2 column tiles outer); each schedule is its own cached plan

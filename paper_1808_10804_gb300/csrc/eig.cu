@@ -219,6 +219,265 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
   for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]) * hscale;
 }
 
+// Block Jacobi: the same problem, interface and tests as jacobi_eig_f32,
+// with the indices in blocks of 16.  A sweep is nb - 1 rounds (nb blocks,
+// round-robin pairing of blocks); in a round every block pair P = I u J is
+// one 32 x 32 subproblem: a warp runs one cyclic sweep of 2 x 2 rotations
+// on A[P, P] (in its own shared buffer), accumulating Q^T in registers
+// (lane i holds row i), then all threads apply A[P, :] <- Q^T A[P, :],
+// A[:, P] <- A[:, P] Q and V[:, P] <- V[:, P] Q.  Per sweep this moves
+// the matrix through shared memory nb - 1 times instead of b - 1 (the
+// scalar kernel's rounds are bound by those passes), at the same
+// arithmetic.  bp = b rounded up to 32 (zero padding, decoupled).
+constexpr int kBjThreads = 512;
+
+__global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* __restrict__ probs,
+                                                               const double* __restrict__ in,
+                                                               double* __restrict__ out, double* __restrict__ vals,
+                                                               int max_sweeps, float tfloor, float junk) {
+  extern __shared__ float sh[];
+  const SmallProb pr = probs[blockIdx.x];
+  const int b = pr.b;
+  const int bp = (b + 31) & ~31;
+  const int ld = bp + 1;
+  const int nb = bp >> 4;       // blocks of 16 (even)
+  const int npair = nb >> 1;    // <= 5
+  float* A = sh;
+  float* V = A + bp * ld;
+  float* Sub = V + bp * ld;     // npair x 32 x 33: subproblem, then Q^T
+  float* red = Sub + npair * 32 * 33;
+  int* order = reinterpret_cast<int*>(red + kBjThreads);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const double* H = in + pr.in_off;
+  __shared__ double dmax[32];
+  {
+    double m = 0;
+    for (int i = tid; i < b; i += nt) m = fmax(m, fabs(H[(long long)i * b + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) dmax[warp] = m;
+  }
+  __syncthreads();
+  __shared__ double hscale;
+  if (tid == 0) {
+    double m = 0;
+    for (int w = 0; w < nt / 32; ++w) m = fmax(m, dmax[w]);
+    hscale = m > 0 ? m : 1.0;
+  }
+  __syncthreads();
+  const double inv = 1.0 / hscale;
+  for (int q = tid; q < bp * bp; q += nt) {
+    const int i = q / bp, j = q - i * bp;
+    A[i * ld + j] = (i < b && j < b) ? float(H[(long long)i * b + j] * inv) : 0.0f;
+    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const float kTau = fminf(1e-5f, fmaxf(tfloor, 1e-30f));
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence: the scalar kernel's test (relative with floor, or the
+    // remaining rotation below 1e-6 rad; pairs both below junk left out)
+    float worst = 0.f;
+    for (int i = tid; i < b; i += nt) {
+      const float aii = A[i * ld + i];
+      const float ai = fabsf(aii);
+      const float di = fmaxf(ai, tfloor);
+      for (int j = i + 1; j < b; ++j) {
+        const float a = A[i * ld + j];
+        const float ajj = A[j * ld + j];
+        const float aj = fabsf(ajj);
+        if (fmaxf(ai, aj) >= junk) {
+          const float rel = a * a / (di * fmaxf(aj, tfloor));
+          const float gap = aii - ajj;
+          const float ang = 0.1f * (a * a) / fmaxf(gap * gap, 1e-37f);
+          worst = fmaxf(worst, fminf(rel, ang));
+        }
+      }
+    }
+    red[tid] = worst;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] = fmaxf(red[tid], red[tid + w]);
+      __syncthreads();
+    }
+    const float wmax = red[0];
+    __syncthreads();
+    if (wmax <= 1e-13f) break;
+    for (int r = 0; r < nb - 1; ++r) {
+      // ---- the subproblems: warp p < npair takes block pair p ----
+      if (warp < npair) {
+        int bi, bj;
+        if (warp == 0) {
+          bi = nb - 1;
+          bj = r;
+        } else {
+          bi = r + warp;
+          if (bi >= nb - 1) bi -= nb - 1;
+          bj = r - warp;
+          if (bj < 0) bj += nb - 1;
+        }
+        // index map of the pair: local 0..15 -> block bi, 16..31 -> block bj
+        float* S = Sub + warp * 32 * 33;
+        const int gl = (lane < 16 ? bi * 16 + lane : bj * 16 + lane - 16);
+        for (int k = 0; k < 32; ++k) {
+          const int gk = (k < 16 ? bi * 16 + k : bj * 16 + k - 16);
+          S[lane * 33 + k] = A[gl * ld + gk];
+        }
+        float qt[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) qt[k] = (k == lane) ? 1.f : 0.f;
+        __syncwarp();
+        // one cyclic sweep: 31 rounds of 16 disjoint rotations
+        for (int rr = 0; rr < 31; ++rr) {
+          // lane's partner in round rr (index 31 fixed, others rotate)
+          int mate;
+          if (lane == 31) mate = rr;
+          else if (lane == rr) mate = 31;
+          else {
+            mate = 2 * rr - lane;
+            mate %= 31;
+            if (mate < 0) mate += 31;
+          }
+          const int p = min(lane, mate), q = max(lane, mate);
+          const float apq = S[p * 33 + q], app = S[p * 33 + p], aqq = S[q * 33 + q];
+          float c = 1.f, sn = 0.f;
+          const float dd = fmaxf(fabsf(app), kTau) * fmaxf(fabsf(aqq), kTau);
+          if (fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            sn = t * c;
+          }
+          // row of this lane: S'[lane] = c S[lane] -/+ s S[mate], then the
+          // columns likewise (S' is no longer symmetric); in halves of 16
+          // (reads of a half before anyone writes it)
+          const bool lo = lane == p;
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            float rl[16], rm[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              rl[k] = S[lane * 33 + h + k];
+              rm[k] = S[mate * 33 + h + k];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) S[lane * 33 + h + k] = lo ? (c * rl[k] - sn * rm[k]) : (sn * rm[k] + c * rl[k]);
+            __syncwarp();
+          }
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            float rl[16], rm[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              rl[k] = S[(h + k) * 33 + lane];
+              rm[k] = S[(h + k) * 33 + mate];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) S[(h + k) * 33 + lane] = lo ? (c * rl[k] - sn * rm[k]) : (sn * rm[k] + c * rl[k]);
+            __syncwarp();
+          }
+          // Q^T rows: row lane of Q^T = column lane of Q
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float m = __shfl_sync(0xffffffffu, qt[k], mate);
+            qt[k] = lo ? (c * qt[k] - sn * m) : (sn * m + c * qt[k]);
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) S[lane * 33 + k] = qt[k];
+      }
+      __syncthreads();
+      // ---- A[P, :] <- Q^T A[P, :]: task (pair, column) ----
+      for (int t = tid; t < npair * bp; t += nt) {
+        const int pp = t / bp, col = t - pp * bp;
+        int bi, bj;
+        if (pp == 0) {
+          bi = nb - 1;
+          bj = r;
+        } else {
+          bi = r + pp;
+          if (bi >= nb - 1) bi -= nb - 1;
+          bj = r - pp;
+          if (bj < 0) bj += nb - 1;
+        }
+        const float* QT = Sub + pp * 32 * 33;
+        float a[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[k] = A[(k < 16 ? bi * 16 + k : bj * 16 + k - 16) * ld + col];
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 32; k += 2) {
+            acc0 = fmaf(QT[i * 33 + k], a[k], acc0);
+            acc1 = fmaf(QT[i * 33 + k + 1], a[k + 1], acc1);
+          }
+          A[(i < 16 ? bi * 16 + i : bj * 16 + i - 16) * ld + col] = acc0 + acc1;
+        }
+      }
+      __syncthreads();
+      // ---- A[:, P] <- A[:, P] Q and V[:, P] <- V[:, P] Q: task (matrix, pair, row) ----
+      for (int t = tid; t < 2 * npair * bp; t += nt) {
+        const int which = t / (npair * bp);
+        const int rem = t - which * npair * bp;
+        const int pp = rem / bp, row = rem - pp * bp;
+        int bi, bj;
+        if (pp == 0) {
+          bi = nb - 1;
+          bj = r;
+        } else {
+          bi = r + pp;
+          if (bi >= nb - 1) bi -= nb - 1;
+          bj = r - pp;
+          if (bj < 0) bj += nb - 1;
+        }
+        float* M = which ? V : A;
+        const float* QT = Sub + pp * 32 * 33;
+        float a[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[k] = M[row * ld + (k < 16 ? bi * 16 + k : bj * 16 + k - 16)];
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 32; k += 2) {
+            acc0 = fmaf(a[k], QT[j * 33 + k], acc0);
+            acc1 = fmaf(a[k + 1], QT[j * 33 + k + 1], acc1);
+          }
+          M[row * ld + (j < 16 ? bi * 16 + j : bj * 16 + j - 16)] = acc0 + acc1;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < b; i += nt) {
+    float ai = A[i * ld + i];
+    if (ai != ai) ai = -INFINITY;
+    int rank = 0;
+    for (int j = 0; j < b; ++j) {
+      float aj = A[j * ld + j];
+      if (aj != aj) aj = -INFINITY;
+      rank += (aj > ai) || (aj == ai && j < i);
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+  double* X = out + pr.out_off;
+  for (int q = tid; q < b * b; q += nt) {
+    const int i = q / b, jn = q - i * b;
+    X[q] = double(V[i * ld + order[jn]]);
+  }
+  for (int jn = tid; jn < b; jn += nt) vals[pr.val_off + jn] = double(A[order[jn] * ld + order[jn]]) * hscale;
+}
+
+size_t jacobi_block_smem(int b) {
+  const int bp = (b + 31) & ~31;
+  const int npair = bp / 32;
+  return sizeof(float) * (2 * bp * (bp + 1) + npair * 32 * 33 + kBjThreads) + sizeof(int) * bp;
+}
+
 size_t jacobi_smem(int b) {
   const int bp = b + (b & 1);
   return sizeof(float) * (2 * bp * (bp + 1) + bp + 1024) + sizeof(int) * (bp + bp);

@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "bst_internal.h"
+#include "relayout_dev.cuh"
 
 namespace bst {
 
@@ -477,6 +478,43 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// The outputs of problems with no matched block pair (K == 0), written by
+// the last CTAs of the split or pack launch (kZeroCtas per problem): beta * C
+// through the scatter tables, or zeros into the sector matrices of a plain
+// plan.
+constexpr int kZeroCtas = 8;
+struct ZeroJob {
+  int nz;
+  const Prob* probs;      // scatter form: problems listed by zidx
+  const int* zidx;
+  Scatter sc;
+  const GemmProb* zp;     // plain form (probs == nullptr)
+  double* C;
+};
+
+__device__ __forceinline__ void zero_part(const ZeroJob& z, int cta) {
+  const int pi = cta / kZeroCtas, part = cta - pi * kZeroCtas;
+  const long long stride = (long long)kZeroCtas * blockDim.x;
+  if (z.probs) {
+    const Prob p = z.probs[z.zidx[pi]];
+    const long long n = (long long)p.M * p.N;
+    for (long long e = part * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
+      const int m = int(e / p.N), c = int(e - (long long)m * p.N);
+      const int2 ri = z.sc.rowtab[p.rt_off + m];
+      const int4 ci = z.sc.coltab[p.ct_off + c];
+      const long long dst = z.sc.bbase[p.bb_off + (long long)ri.x * p.ncc + ci.x] + (long long)ri.y * ci.z + ci.y;
+      z.C[dst] = z.sc.beta == 0.0 ? 0.0 : z.sc.beta * z.C[dst];
+    }
+  } else {
+    const GemmProb p = z.zp[pi];
+    const long long n = (long long)p.M * p.N;
+    for (long long e = part * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
+      const long long m = e / p.N, c = e - m * p.N;
+      z.C[p.c_off + m * p.c_m + c * p.c_n] = 0.0;
+    }
+  }
+}
+
 // Split FP64 rows into S BF16 digit slices (integer arithmetic on the bit
 // pattern).  One warp per row; digits for k in [K, roundup(K, 32)) are 0.
 // One launch splits both operands: CTAs [0, ga) take the rows of A, the
@@ -491,7 +529,11 @@ struct SplitJob {
 };
 
 template <int S>
-__global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch) {
+__global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int gab, int kpitch, ZeroJob zj) {
+  if (int(blockIdx.x) >= gab) {
+    zero_part(zj, int(blockIdx.x) - gab);
+    return;
+  }
   const bool is_a = int(blockIdx.x) < ga;
   const SplitJob& J = is_a ? ja : jb;
   const SplitTask* __restrict__ tasks = J.tasks;
@@ -563,6 +605,176 @@ __global__ void ozaki_split_kernel(SplitJob ja, SplitJob jb, int ga, int kpitch)
   }
 }
 
+// Gather and split in one pass (the operand's sector matrix is never
+// formed): one warp per row of a sector matrix reads the row's K elements
+// straight from the operand tensor's canonical blocks, takes the row's
+// exponent and writes its S digit slices.  A row of sector s and row
+// configuration r meets one block per column configuration c (a segment
+// [k0, k0 + w) of the row); inside block (r, c) the element of row mi and
+// column kk sits at  off + sum_rowlegs idx * str + sum_collegs idx * str,
+// the indices from mi and kk row-major over the legs in matrix order.
+// One warp per row, lanes along k: the reads are coalesced when the operand
+// block's innermost leg is a contracted leg (consecutive k are consecutive
+// in memory); plans whose operands are not laid out so gather and split in
+// two passes instead (ozaki_packable).
+struct PackGroup {
+  int32_t pw0;    // first warp of this group
+  int32_t row0;   // its first row in the split buffer
+  int32_t h, K;   // rows of this (sector, row configuration), columns
+  int64_t seg0;   // its segments (one per column configuration), k0 ascending
+  int32_t nseg, pad;
+};
+
+struct PackSeg {
+  int64_t off;          // block offset in its tensor (elements)
+  int32_t k0, w;        // columns [k0, k0 + w) of the row
+  int32_t nr, nc;       // row legs, column legs
+  int32_t src, pad;     // index of the tensor in the job's pointer table
+  int32_t dim[kMaxRank];  // row legs then column legs, matrix order
+  int32_t str[kMaxRank];  // their strides inside the block
+  uint32_t fm[kMaxRank], fl[kMaxRank];  // FastDiv of dim
+};
+
+struct PackJob {
+  const PackGroup* groups;
+  const PackSeg* segs;
+  int ngroups, nwarps;         // groups, warps
+  int rows_total;              // rows of the split buffer (slice stride)
+  const double* src;           // the operand tensor (tab == nullptr)
+  const double* const* tab;    // per-segment tensors (batched contractions)
+  __nv_bfloat16* S;
+  int* ex;
+};
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t m, uint32_t l) { return (__umulhi(n, m) + n) >> l; }
+
+
+template <int S>
+__global__ void __launch_bounds__(256) pack_split_kernel(PackJob ja, PackJob jb, int ga, int gab, int kpitch,
+                                                         ZeroJob zj) {
+  if (int(blockIdx.x) >= gab) {
+    zero_part(zj, int(blockIdx.x) - gab);
+    return;
+  }
+  const bool is_a = int(blockIdx.x) < ga;
+  const PackJob& J = is_a ? ja : jb;
+  const int w = ((int(blockIdx.x) - (is_a ? 0 : ga)) * int(blockDim.x) + int(threadIdx.x)) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= J.nwarps || J.ngroups == 0) return;
+  int lo = 0, hi = J.ngroups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (J.groups[mid].pw0 <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  const PackGroup G = J.groups[lo];
+  const PackSeg* segs = J.segs + G.seg0;
+  const int mi = w - G.pw0;
+  if (mi < 0 || mi >= G.h) return;
+  const int grow = G.row0 + mi;
+  // row-leg indices of mi (the row legs' extents are those of every
+  // segment of the group)
+  int ridx[kMaxRank];
+  {
+    const PackSeg& s0 = segs[0];
+    uint32_t rem = uint32_t(mi);
+#pragma unroll
+    for (int j = kMaxRank - 1; j >= 0; --j) {
+      ridx[j] = 0;
+      if (j < s0.nr) {
+        const uint32_t q = fdiv(rem, s0.fm[j], s0.fl[j]);
+        ridx[j] = int(rem - q * uint32_t(s0.dim[j]));
+        rem = q;
+      }
+    }
+  }
+  // element k of the row (k < K), walking the segments forward
+  int si = 0;
+  long long rp = 0;
+  const double* base = nullptr;
+  auto enter = [&](int i) {
+    const PackSeg& sg = segs[i];
+    long long o = sg.off;
+#pragma unroll
+    for (int j = 0; j < kMaxRank; ++j)
+      if (j < sg.nr) o += (long long)ridx[j] * sg.str[j];
+    rp = o;
+    base = J.tab ? J.tab[sg.src] : J.src;
+  };
+  auto load = [&](int k) -> double {
+    while (k >= segs[si].k0 + segs[si].w) {
+      ++si;
+      enter(si);
+    }
+    const PackSeg& sg = segs[si];
+    uint32_t rem = uint32_t(k - sg.k0);
+    long long o = rp;
+#pragma unroll
+    for (int j = kMaxRank - 1; j >= 0; --j) {
+      if (j < sg.nc) {
+        const int jj = sg.nr + j;
+        const uint32_t q = fdiv(rem, sg.fm[jj], sg.fl[jj]);
+        o += (long long)(rem - q * uint32_t(sg.dim[jj])) * sg.str[jj];
+        rem = q;
+      }
+    }
+    return base[o];
+  };
+  // the digits of x against the row exponent e (the same integer
+  // arithmetic as ozaki_split_kernel<S>)
+  auto digits = [&](double x, int e, int (&dig)[S]) {
+    long long Xi = 0;
+    const unsigned long long b = __double_as_longlong(x);
+    const int E = int((b >> 52) & 0x7FF);
+    if (E != 0) {
+      const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+      const int sh = E - 1075 - e + 9 * S - 1;
+      if (sh >= 0) {
+        Xi = m << sh;
+      } else if (sh > -64) {
+        const int rs = -sh;
+        Xi = (m + (1ll << (rs - 1))) >> rs;
+      }
+      if (b >> 63) Xi = -Xi;
+    }
+#pragma unroll
+    for (int i = S - 1; i >= 1; --i) {
+      const long long lo9 = ((Xi + 256) & 511) - 256;
+      dig[i] = int(lo9);
+      Xi = (Xi - lo9) >> 9;
+    }
+    dig[0] = int(Xi);
+  };
+  const int kend = (G.K + 31) & ~31;
+  enter(0);
+  unsigned long long mx = 0;
+  for (int k = lane; k < G.K; k += 32) {
+    const unsigned long long b = __double_as_longlong(load(k)) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  const int e = int(mx >> 52) - 1022;
+  if (lane == 0) J.ex[grow] = e;
+  si = 0;
+  enter(0);
+  for (int k = lane; k < kend; k += 32) {
+    int dig[S];
+    if (k < G.K && mx != 0) {
+      digits(load(k), e, dig);
+    } else {
+#pragma unroll
+      for (int i = 0; i < S; ++i) dig[i] = 0;
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      J.S[((long long)i * J.rows_total + grow) * kpitch + k] = __int2bfloat16_rn(dig[i]);
+  }
+}
+
 }  // namespace oz
 
 // ---------------------------------------------------------------------------------
@@ -630,7 +842,17 @@ struct OzakiPlan {
   long long* d_bbase = nullptr;
   int* d_zidx = nullptr;
   bool scatter = false;
+  // packed operands (pack_split_kernel reads the tensors' blocks; no
+  // sector matrices, no separate split)
+  bool packed = false;
+  oz::PackGroup *d_pgA = nullptr, *d_pgB = nullptr;
+  oz::PackSeg *d_psA = nullptr, *d_psB = nullptr;
+  int ngA = 0, ngB = 0, nrA = 0, nrB = 0;  // groups and warps of each operand
   ~OzakiPlan() {
+    cudaFree(d_pgA);
+    cudaFree(d_pgB);
+    cudaFree(d_psA);
+    cudaFree(d_psB);
     cudaFree(d_rowtab);
     cudaFree(d_coltab);
     cudaFree(d_bbase);
@@ -646,16 +868,6 @@ struct OzakiPlan {
     cudaFree(d_zprobs);
   }
 };
-
-// C = 0 on the problems with K == 0 (one CTA row per problem)
-__global__ void zero_probs_kernel(const GemmProb* __restrict__ zp, double* __restrict__ C) {
-  const GemmProb p = zp[blockIdx.y];
-  const long long n = (long long)p.M * p.N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long m = e / p.N, c = e - m * p.N;
-    C[p.c_off + m * p.c_m + c * p.c_n] = 0.0;
-  }
-}
 
 template <int S, int TN>
 static size_t smem_bytes() { return sizeof(oz::Smem<S, TN>) + 1024; }
@@ -675,6 +887,84 @@ static int num_sms() {
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 152;
   return n > 0 ? n : 152;
+}
+
+struct PackTables {
+  std::vector<oz::PackGroup> g;
+  std::vector<oz::PackSeg> sg;
+  int nwarps = 0;
+};
+
+// Appends the pack groups and segments of one operand of one contraction:
+// v is the operand's sector-matrix view of layout L (rows: its open legs,
+// columns: its contracted legs), probs the contraction's problems in GEMM
+// order (their operand sectors at a_off / b_off), `row` the split-buffer
+// row of the first problem (advanced by M or N per problem), `src` the
+// operand's index in a pointer table (0 for a single contraction).
+static void append_pack(PackTables& T, const Layout* L, const MatView& v, const std::vector<GemmProb>& probs,
+                        bool b_side, int& row, int src) {
+  std::map<int64_t, const MatSector*> by_off;
+  for (auto& sec : v.secs)
+    if (sec.rows > 0 && sec.cols > 0) by_off[sec.off] = &sec;
+  const int r = L->rank;
+  const int nr = int(v.rowlegs.size()), nc = int(v.collegs.size());
+  BST_REQUIRE(nr + nc == r && r <= kMaxRank, BST_E_ARG, "pack: view does not cover the tensor");
+
+  std::vector<int32_t> tup(r);
+  for (auto& g : probs) {
+    const int rows = b_side ? g.N : g.M;
+    if (g.K > 0) {
+      auto it = by_off.find(b_side ? g.b_off : g.a_off);
+      BST_REQUIRE(it != by_off.end() && it->second->rows == rows && it->second->cols == g.K, BST_E_SHAPE,
+                  "pack: problem does not match its operand sector");
+      const MatSector& sec = *it->second;
+      for (size_t rc = 0; rc < sec.rcfg.size(); ++rc) {
+        const int64_t h = (rc + 1 < sec.rcfg.size() ? sec.roff[rc + 1] : sec.rows) - sec.roff[rc];
+        oz::PackGroup pg{};
+        pg.pw0 = T.nwarps;
+        pg.row0 = int32_t(row + sec.roff[rc]);
+        pg.h = int32_t(h);
+        pg.K = g.K;
+        pg.seg0 = int64_t(T.sg.size());
+        pg.nseg = int32_t(sec.ccfg.size());
+        int64_t kcov = 0;
+        for (size_t cc = 0; cc < sec.ccfg.size(); ++cc) {
+          for (int j = 0; j < nr; ++j) tup[v.rowlegs[j]] = sec.rcfg[rc][j];
+          for (int j = 0; j < nc; ++j) tup[v.collegs[j]] = sec.ccfg[cc][j];
+          const int64_t b = L->block_of(tup.data());
+          BST_REQUIRE(b >= 0, BST_E_SHAPE, "pack: missing operand block");
+          const int64_t* sh = &L->shape[b * r];
+          std::vector<int64_t> bst(r, 1);
+          for (int i = r - 2; i >= 0; --i) bst[i] = bst[i + 1] * sh[i + 1];
+          oz::PackSeg sg{};
+          sg.off = L->offset[b];
+          sg.k0 = int32_t(sec.coff[cc]);
+          sg.nr = nr;
+          sg.nc = nc;
+          sg.src = src;
+          int64_t hh = 1, w = 1;
+          for (int j = 0; j < nr + nc; ++j) {
+            const int leg = j < nr ? v.rowlegs[j] : v.collegs[j - nr];
+            sg.dim[j] = int32_t(sh[leg]);
+            sg.str[j] = int32_t(bst[leg]);
+            FastDiv f;
+            f.init(uint32_t(sh[leg]));
+            sg.fm[j] = f.m;
+            sg.fl[j] = f.l;
+            (j < nr ? hh : w) *= sh[leg];
+          }
+          sg.w = int32_t(w);
+          BST_REQUIRE(hh == h && sg.k0 == kcov, BST_E_SHAPE, "pack: segment does not tile the row");
+          kcov += w;
+          T.sg.push_back(sg);
+        }
+        BST_REQUIRE(kcov == g.K, BST_E_SHAPE, "pack: segments do not cover K");
+        T.g.push_back(pg);
+        T.nwarps += int32_t(h);
+      }
+    }
+    row += rows;
+  }
 }
 
 // Tile schedule of a plan (the order in which CTAs pick up output tiles):
@@ -790,47 +1080,48 @@ static OzakiPlan* build_plan(Ctx* ctx, const std::vector<GemmProb>& probs, int o
   return P;
 }
 
-// Scatter plans: the output blocks of K == 0 problems (no matched block
-// pair) become beta * C (0 for beta == 0), through the same tables as the
-// GEMM epilogue.
-__global__ void zero_scatter_kernel(const oz::Prob* __restrict__ probs, const int* __restrict__ zidx,
-                                    const oz::Scatter sc, double* __restrict__ C) {
-  const oz::Prob p = probs[zidx[blockIdx.y]];
-  const long long n = (long long)p.M * p.N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int m = int(e / p.N), c = int(e - (long long)m * p.N);
-    const int2 ri = sc.rowtab[p.rt_off + m];
-    const int4 ci = sc.coltab[p.ct_off + c];
-    const long long dst = sc.bbase[p.bb_off + (long long)ri.x * p.ncc + ci.x] + (long long)ri.y * ci.z + ci.y;
-    C[dst] = sc.beta == 0.0 ? 0.0 : sc.beta * C[dst];
-  }
-}
-
+// A, B: the operands' sector matrices, or for a packed plan the operand
+// tensors themselves (tabA / tabB: per-segment tensor tables of a batch)
 static void run_plan(Ctx* ctx, OzakiPlan* P, const double* A, const double* B, double* C, cudaStream_t s,
-                     bool split_a = true, double alpha = 1.0, double beta = 0.0) {
-  const oz::Scatter sc{P->d_rowtab, P->d_coltab, P->d_bbase, alpha, beta};
-  if (P->nzprobs) {
-    if (P->scatter)
-      zero_scatter_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_probs, P->d_zidx, sc, C);
-    else
-      zero_probs_kernel<<<dim3(64, unsigned(P->nzprobs)), 256, 0, s>>>(P->d_zprobs, C);
-    BST_CUDA(cudaGetLastError());
-    count_launch(ctx);
-  }
-  if (P->ntiles == 0) return;
+                     bool split_a = true, double alpha = 1.0, double beta = 0.0,
+                     const double* const* tabA = nullptr, const double* const* tabB = nullptr,
+                     const long long* bbase = nullptr) {
+  const oz::Scatter sc{P->d_rowtab, P->d_coltab, bbase ? bbase : P->d_bbase, alpha, beta};
   const bool b_from_a = P->ab_same && A == B && split_a;
-  {
+  if (P->packed) {
+    // gather + split: FP64 read once per element (and once more from cache),
+    // S digits written; the byte count is that of the split of gathered
+    // rows without the FP64 row write and read of a separate gather.  The
+    // K == 0 problems' outputs are written by the same launch.
+    ProfScope ps(ctx, s, "pack_bf16", 0.0, P->split_bytes);
+    const oz::PackJob ja{P->d_pgA, P->d_psA, P->ngA, P->nrA, P->rowsA, A, tabA, P->SA, P->eA};
+    const oz::PackJob jb{P->d_pgB, P->d_psB, P->ngB, P->nrB, P->rowsB, B, tabB, P->SB, P->eB};
+    const oz::ZeroJob zj{P->nzprobs, P->scatter ? P->d_probs : nullptr, P->d_zidx, sc, P->d_zprobs, C};
+    const int ga = (P->nrA + 7) / 8, gb = (P->nrB + 7) / 8, gz = P->nzprobs * oz::kZeroCtas;
+    if (ga + gb + gz > 0) {
+      if (P->S == 5) oz::pack_split_kernel<5><<<ga + gb + gz, 256, 0, s>>>(ja, jb, ga, ga + gb, P->kpitch, zj);
+      else oz::pack_split_kernel<3><<<ga + gb + gz, 256, 0, s>>>(ja, jb, ga, ga + gb, P->kpitch, zj);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
+    }
+    if (P->ntiles == 0) return;
+  } else {
+    // the split of both operands; the K == 0 problems' outputs are written
+    // by the same launch
     ProfScope ps(ctx, s, "split_bf16", 0.0, b_from_a ? 0.5 * P->split_bytes : P->split_bytes);
-    const int wa = split_a ? P->rowsA : 0, wb = b_from_a ? 0 : P->rowsB;
+    const int wa = (split_a && P->ntiles) ? P->rowsA : 0, wb = (b_from_a || !P->ntiles) ? 0 : P->rowsB;
     const int ga = (wa + 7) / 8, gb = (wb + 7) / 8;  // 8 rows (warps) per CTA
-    if (ga + gb > 0) {
+    const int gz = P->nzprobs * oz::kZeroCtas;
+    const oz::ZeroJob zj{P->nzprobs, P->scatter ? P->d_probs : nullptr, P->d_zidx, sc, P->d_zprobs, C};
+    if (ga + gb + gz > 0) {
       const oz::SplitJob ja{P->d_sa, P->nsa, P->rowsA, A, P->SA, P->eA};
       const oz::SplitJob jb{P->d_sb, P->nsb, P->rowsB, B, P->SB, P->eB};
-      if (P->S == 5) oz::ozaki_split_kernel<5><<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
-      else oz::ozaki_split_kernel<3><<<ga + gb, 256, 0, s>>>(ja, jb, ga, P->kpitch);
+      if (P->S == 5) oz::ozaki_split_kernel<5><<<ga + gb + gz, 256, 0, s>>>(ja, jb, ga, ga + gb, P->kpitch, zj);
+      else oz::ozaki_split_kernel<3><<<ga + gb + gz, 256, 0, s>>>(ja, jb, ga, ga + gb, P->kpitch, zj);
+      BST_CUDA(cudaGetLastError());
+      count_launch(ctx);
     }
-    BST_CUDA(cudaGetLastError());
-    count_launch(ctx, (wa + wb) > 0 ? 1 : 0);
+    if (P->ntiles == 0) return;
   }
   ProfScope ps(ctx, s, "gemm_ozaki", P->flops, 0.0);
   const int grid = std::min(P->ntiles, num_sms());
@@ -879,8 +1170,10 @@ int ozaki_pick_tn(const std::vector<GemmProb>& probs) {
 // legs then B's, so the block of (row config r, column config c) is a
 // row-major [rows of r x columns of c] matrix: element (m, n) of a sector
 // goes to offset(r, c) + mi * width(c) + ni.
-static OzakiPlan* prepare_scatter(Ctx* ctx, ContractPlan* p, int S) {
-  ScatterSpec sc;
+// Appends the scatter tables of one contraction's problems (block offsets
+// relative to its own output; bsrc, when given, records the contraction
+// index `src` of every entry of bbase).
+static void append_scatter(ScatterSpec& sc, ContractPlan* p, std::vector<int32_t>* bsrc, int src) {
   const Layout* C = p->C;
   std::vector<int32_t> tup(C->rank);
   size_t pi = 0;
@@ -908,6 +1201,7 @@ static OzakiPlan* prepare_scatter(Ctx* ctx, ContractPlan* p, int S) {
         const int64_t b = C->block_of(tup.data());
         BST_REQUIRE(b >= 0, BST_E_SHAPE, "scatter plan: missing output block");
         sc.bbase.push_back((long long)C->offset[b]);
+        if (bsrc) bsrc->push_back(src);
       }
     }
     ++pi;
@@ -915,24 +1209,138 @@ static OzakiPlan* prepare_scatter(Ctx* ctx, ContractPlan* p, int S) {
   BST_REQUIRE(pi == p->probs.size(), BST_E_SHAPE, "scatter plan: problem count mismatch");
   BST_REQUIRE(sc.rowtab.size() < (size_t(1) << 31) && sc.coltab.size() < (size_t(1) << 31), BST_E_UNSUPPORTED,
               "scatter plan: too many rows");
+}
+
+static OzakiPlan* prepare_scatter(Ctx* ctx, ContractPlan* p, int S) {
+  ScatterSpec sc;
+  append_scatter(sc, p, nullptr, 0);
   return build_plan(ctx, p->probs, 0, &sc, S, ozaki_pick_tn(p->probs));
 }
 
-void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* c,
-                            double alpha, double beta, cudaStream_t s) {
-  OzakiPlan*& P = p->oz[S == 3 ? 1 : 0][1];
-  if (!P) P = prepare_scatter(ctx, p, S);
-  run_plan(ctx, P, Amat, Bmat, c, s, true, alpha, beta);
+// Device tables of the packed operands of a contraction plan.
+static void attach_pack(OzakiPlan* P, const PackTables& ta, const PackTables& tb) {
+  auto up = [](auto** dst, const auto& v) {
+    using T = typename std::remove_reference<decltype(v)>::type::value_type;
+    if (v.empty()) return;
+    BST_CUDA(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+    BST_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  };
+  up(&P->d_pgA, ta.g);
+  up(&P->d_psA, ta.sg);
+  up(&P->d_pgB, tb.g);
+  up(&P->d_psB, tb.sg);
+  P->ngA = int(ta.g.size());
+  P->ngB = int(tb.g.size());
+  P->nrA = ta.nwarps;
+  P->nrB = tb.nwarps;
+  P->packed = true;
+  P->ab_same = false;
 }
 
-void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* Amat, const double* Bmat, double* Cmat,
-                    cudaStream_t s) {
+static void attach_pack(OzakiPlan* P, ContractPlan* p) {
+  PackTables ta, tb;
+  int ra = 0, rb = 0;
+  append_pack(ta, p->A, p->va, p->probs, false, ra, 0);
+  append_pack(tb, p->B, p->vb, p->probs, true, rb, 0);
+  BST_REQUIRE(ra == P->rowsA && rb == P->rowsB, BST_E_SHAPE, "pack: row count mismatch");
+  attach_pack(P, ta, tb);
+}
+
+// The pack kernel reads a row's K elements with its lanes: coalesced when
+// the last contracted leg (in pair order) is the operand tensor's innermost
+// leg.  Plans whose operands are laid out otherwise gather (block-contiguous
+// reads) and split in two passes.
+bool ozaki_packable(const ContractPlan* p) {
+  return !p->va.collegs.empty() && p->va.collegs.back() == p->A->rank - 1 && !p->vb.collegs.empty() &&
+         p->vb.collegs.back() == p->B->rank - 1;
+}
+
+// Operands of a plan that is not packed: the gathered sector matrices.
+static void gather_operands(Ctx* ctx, ContractPlan* p, const double* a, const double* b, const double** Am,
+                            const double** Bm, cudaStream_t s) {
+  double* am = (double*)ctx->buf("contract.A", sizeof(double) * std::max<int64_t>(p->amat, 1), s);
+  double* bm = (double*)ctx->buf("contract.B", sizeof(double) * std::max<int64_t>(p->bmat, 1), s);
+  launch_relayout(ctx, p->ra, a, am, 0, 1.0, 0.0, s);
+  launch_relayout(ctx, p->rb, b, bm, 0, 1.0, 0.0, s);
+  *Am = am;
+  *Bm = bm;
+}
+
+void run_gemm_ozaki_scatter(Ctx* ctx, ContractPlan* p, int S, const double* a, const double* b, double* c,
+                            double alpha, double beta, cudaStream_t s) {
+  OzakiPlan*& P = p->oz[S == 3 ? 1 : 0][1];
+  if (!P) {
+    P = prepare_scatter(ctx, p, S);
+    if (ozaki_packable(p)) attach_pack(P, p);
+  }
+  if (!P->packed) gather_operands(ctx, p, a, b, &a, &b, s);
+  run_plan(ctx, P, a, b, c, s, true, alpha, beta);
+}
+
+void run_gemm_ozaki(Ctx* ctx, ContractPlan* p, int S, const double* a, const double* b, double* Cmat,
+                    cudaStream_t s, const double* Am, const double* Bm) {
   OzakiPlan*& P = p->oz[S == 3 ? 1 : 0][0];
-  if (!P) P = build_plan(ctx, p->probs, 0, nullptr, S, ozaki_pick_tn(p->probs));
-  run_plan(ctx, P, Amat, Bmat, Cmat, s);
+  if (!P) {
+    P = build_plan(ctx, p->probs, 0, nullptr, S, ozaki_pick_tn(p->probs));
+    if (ozaki_packable(p)) attach_pack(P, p);
+  }
+  if (!P->packed) {
+    if (Am && Bm) a = Am, b = Bm;
+    else gather_operands(ctx, p, a, b, &a, &b, s);
+  }
+  run_plan(ctx, P, a, b, Cmat, s);
 }
 
 void ozaki_free(OzakiPlan* oz) { delete oz; }
+
+// Batched contractions: one packed, scattering plan over the problems of
+// every contraction (probs: their concatenation, in plan order).  The
+// output blocks of contraction i are addressed relative to the first
+// output's pointer: bbase_rel holds each entry's offset inside its own
+// output and bbase_src its contraction, and ozaki_batch_bbase turns them
+// into element offsets from c[0] for one set of output pointers.
+OzakiPlan* ozaki_batch_plan(Ctx* ctx, const std::vector<ContractPlan*>& plans, const std::vector<GemmProb>& probs,
+                            int order, int S, int TN, bool pack, std::vector<long long>* bbase_rel,
+                            std::vector<int32_t>* bbase_src) {
+  ScatterSpec sc;
+  bbase_src->clear();
+  PackTables ta, tb;
+  int ra = 0, rb = 0;
+  for (size_t i = 0; i < plans.size(); ++i) {
+    append_scatter(sc, plans[i], bbase_src, int(i));
+    if (pack) {
+      append_pack(ta, plans[i]->A, plans[i]->va, plans[i]->probs, false, ra, int(i));
+      append_pack(tb, plans[i]->B, plans[i]->vb, plans[i]->probs, true, rb, int(i));
+    }
+  }
+  BST_REQUIRE(sc.rt_off.size() == probs.size(), BST_E_SHAPE, "batch plan: problem count mismatch");
+  *bbase_rel = sc.bbase;
+  OzakiPlan* P = build_plan(ctx, probs, order, &sc, S, TN == 0 ? ozaki_pick_tn(probs) : TN);
+  if (pack) {
+    BST_REQUIRE(ra == P->rowsA && rb == P->rowsB, BST_E_SHAPE, "batch plan: row count mismatch");
+    attach_pack(P, ta, tb);
+  }
+  return P;
+}
+
+void ozaki_batch_bbase(const std::vector<long long>& rel, const std::vector<int32_t>& src,
+                       const std::vector<double*>& c, std::vector<long long>* out) {
+  std::vector<long long> delta(c.size());
+  const uintptr_t c0 = uintptr_t(c[0]);
+  for (size_t i = 0; i < c.size(); ++i) {
+    const long long d = (long long)(uintptr_t(c[i]) - c0);
+    BST_REQUIRE(d % (long long)sizeof(double) == 0, BST_E_ARG, "output pointers must be 8-byte aligned");
+    delta[i] = d / (long long)sizeof(double);
+  }
+  out->resize(rel.size());
+  for (size_t j = 0; j < rel.size(); ++j) (*out)[j] = rel[j] + delta[src[j]];
+}
+
+void run_ozaki_batch(Ctx* ctx, OzakiPlan* P, double* const* bases, int n, const double* Am, const double* Bm,
+                     double* c0, const long long* bbase, double alpha, double beta, cudaStream_t s) {
+  if (P->packed) run_plan(ctx, P, nullptr, nullptr, c0, s, true, alpha, beta, bases, bases + n, bbase);
+  else run_plan(ctx, P, Am, Bm, c0, s, true, alpha, beta, nullptr, nullptr, bbase);
+}
 
 void run_gemm_ozaki_probs(Ctx* ctx, const std::string& tag, const std::vector<GemmProb>& probs, const double* A,
                           const double* B, double* C, cudaStream_t s, int order, bool split_a, int S, int TN) {

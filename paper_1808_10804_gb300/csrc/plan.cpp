@@ -202,22 +202,23 @@ ContractPlan* get_contract_plan(Ctx* ctx, Layout* A, Layout* B, const std::vecto
 
 void run_contract(Ctx* ctx, ContractPlan* p, const double* a, const double* b, bst_prec prec, double alpha,
                   double beta, double* c, cudaStream_t s, bool scatter, double** cmat_out) {
-  double* Am = (double*)ctx->buf("contract.A", sizeof(double) * std::max<int64_t>(p->amat, 1), s);
-  double* Bm = (double*)ctx->buf("contract.B", sizeof(double) * std::max<int64_t>(p->bmat, 1), s);
   ctx->work_flops += p->g.flops;
-  launch_relayout(ctx, p->ra, a, Am, 0, 1.0, 0.0, s);
-  launch_relayout(ctx, p->rb, b, Bm, 0, 1.0, 0.0, s);
   if (prec != BST_FP64 && scatter && !cmat_out) {
-    // the tensor-core GEMM's epilogue writes C's blocks directly
-    run_gemm_ozaki_scatter(ctx, p, ozaki_slices(prec), Am, Bm, c, alpha, beta, s);
+    // the tensor-core path reads A's and B's blocks directly (gather and
+    // digit split in one kernel) and its epilogue writes C's blocks
+    run_gemm_ozaki_scatter(ctx, p, ozaki_slices(prec), a, b, c, alpha, beta, s);
     return;
   }
   double* Cm = (double*)ctx->buf(cmat_out ? "contract.Ckeep" : "contract.C",
                                  sizeof(double) * std::max<int64_t>(p->cmat, 1), s);
   if (prec == BST_FP64) {
+    double* Am = (double*)ctx->buf("contract.A", sizeof(double) * std::max<int64_t>(p->amat, 1), s);
+    double* Bm = (double*)ctx->buf("contract.B", sizeof(double) * std::max<int64_t>(p->bmat, 1), s);
+    launch_relayout(ctx, p->ra, a, Am, 0, 1.0, 0.0, s);
+    launch_relayout(ctx, p->rb, b, Bm, 0, 1.0, 0.0, s);
     launch_gemm_f64(ctx, p->g, Am, Bm, Cm, s);
   } else {
-    run_gemm_ozaki(ctx, p, ozaki_slices(prec), Am, Bm, Cm, s);
+    run_gemm_ozaki(ctx, p, ozaki_slices(prec), a, b, Cm, s);
   }
   if (scatter) launch_relayout(ctx, p->rc, c, Cm, 1, alpha, beta, s);
   if (cmat_out) *cmat_out = Cm;

@@ -116,6 +116,8 @@ struct ResProb {
   int64_t y_off, v_off, val_off, ld;
 };
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
+__global__ void jacobi_block_f32(const SmallProb*, const double*, double*, double*, int, float, float);
+size_t jacobi_block_smem(int b);
 __global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double, double);
 __global__ void add_inplace(double*, const double*, long long);
 __global__ void cholinv_f32(const SmallProb*, const double*, double*, int*, const float*, int);
@@ -260,6 +262,8 @@ static void setup_attrs() {
   static bool done = false;
   if (done) return;
   BST_CUDA(cudaFuncSetAttribute(jacobi_eig_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jacobi_smem(kEigMax))));
+  BST_CUDA(cudaFuncSetAttribute(jacobi_block_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(jacobi_block_smem(kEigMax))));
   BST_CUDA(cudaFuncSetAttribute(cholinv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cholinv_smem(kEigMax))));
   done = true;
 }
@@ -304,6 +308,10 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   SmallProb* dsp = upload_cached(ctx, pre + "eig.sp", sp, s);
   int bmax = 0;
   for (auto& p : sp) bmax = std::max(bmax, p.b);
+  // FP32 Jacobi stage: the block kernel (32 x 32 subproblems per round)
+  auto jacobi = [&](const SmallProb* pp, const double* in, double* o, double* l, int sweeps, float tf, float jk) {
+    jacobi_block_f32<<<int(sp.size()), 512, jacobi_block_smem(bmax), s>>>(pp, in, o, l, sweeps, tf, jk);
+  };
   double* X1 = (double*)ctx->buf(pre + "eig.x1", sizeof(double) * smtot, s);
   double* H1 = (double*)ctx->buf(pre + "eig.h1", sizeof(double) * smtot, s);
   double* XtX = (double*)ctx->buf(pre + "eig.xtx", sizeof(double) * smtot, s);
@@ -343,7 +351,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   if (gr && !near_diag) {
     {
       ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
+      jacobi(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
       BST_CUDA(cudaGetLastError());
       count_launch(ctx);
     }
@@ -353,7 +361,7 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
       ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
       // pairs below 1e-14 of the largest (beyond the accuracy of H1) are
       // left out of the convergence test
-      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 10, 1e-20f, 1e-14f);
+      jacobi(dsp, H1, T, lam, 10, 1e-20f, 1e-14f);
       BST_CUDA(cudaGetLastError());
       count_launch(ctx);
     }
@@ -362,13 +370,13 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
     // values below 1e-6 of the largest are not resolved by this FP32 pass
     // (nor refined below): their pairs are left out of the convergence test
-    jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X, lam, 10, 1e-5f, 1e-6f);
+    jacobi(dsp, H, X, lam, 10, 1e-5f, 1e-6f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   } else {
     {
       ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
+      jacobi(dsp, H, X1, lam, 7, 1.0f, 1e-5f);
       BST_CUDA(cudaGetLastError());
       count_launch(ctx);
     }
@@ -376,13 +384,16 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     gemm_any(ctx, pre + "oa.s", prec, g_s, X1, T, H1, s, false, ws);
     {
       ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
-      jacobi_eig_f32<<<int(sp.size()), 1024, jacobi_smem(bmax), s>>>(dsp, H1, T, lam, 7, 1e-5f, 0.f);
+      jacobi(dsp, H1, T, lam, 7, 1e-5f, 0.f);
       BST_CUDA(cudaGetLastError());
       count_launch(ctx);
     }
     gemm_any(ctx, pre + "oa.xe", prec, g_xe, X1, T, X, s, false, ws);  // X = X1 X2
   }
-  for (int it = 0; it < 2; ++it) {
+  // three refinement steps: quadratic from the FP32 stage's angles, which
+  // for a pair of values closer than ~1e-6 relative are limited by FP32
+  // rounding to ~1e-2 (two steps reach 1e-8 there, three the FP64 floor)
+  for (int it = 0; it < 3; ++it) {
     gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
     if (gr) {
       // S = (N X)^T (N X): accurate relative to the singular values, so
@@ -940,15 +951,17 @@ ProjResult svd_projector(Ctx* ctx, Layout* Rt, const double* rt, Layout* Rb, con
   std::vector<int> cut(ncut);
   std::iota(cut.begin(), cut.end(), 0);
   ContractPlan* pn = get_contract_plan(ctx, Rt, Rb, cut, cut);
-  double* Nm = nullptr;
-  // N = Rt^T Rb as sector matrices (rows: right cut of Rt, cols: right cut of Rb)
-  run_contract(ctx, pn, rt, rb, prec, 1.0, 0.0, nullptr, s, /*scatter=*/false, &Nm);
-  const double* Am = (const double*)ctx->bufs["contract.A"].p;  // Rt as [beta x alpha]
-  const double* Bm = (const double*)ctx->bufs["contract.B"].p;  // Rb as [beta' x alpha']
-  double* At = (double*)ctx->buf("proj.A", sizeof(double) * std::max<int64_t>(pn->amat, 1), s);
-  double* Bt = (double*)ctx->buf("proj.B", sizeof(double) * std::max<int64_t>(pn->bmat, 1), s);
-  BST_CUDA(cudaMemcpyAsync(At, Am, sizeof(double) * pn->amat, cudaMemcpyDeviceToDevice, s));
-  BST_CUDA(cudaMemcpyAsync(Bt, Bm, sizeof(double) * pn->bmat, cudaMemcpyDeviceToDevice, s));
+  // Rt and Rb as sector matrices (kept for P and Pt below), and
+  // N = Rt^T Rb (rows: right cut of Rt, cols: right cut of Rb); the
+  // tensor-core product reads Rt's and Rb's blocks itself
+  double* At = (double*)ctx->buf("proj.A", sizeof(double) * std::max<int64_t>(pn->amat, 1), s);  // [beta x alpha]
+  double* Bt = (double*)ctx->buf("proj.B", sizeof(double) * std::max<int64_t>(pn->bmat, 1), s);  // [beta' x alpha']
+  launch_relayout(ctx, pn->ra, rt, At, 0, 1.0, 0.0, s);
+  launch_relayout(ctx, pn->rb, rb, Bt, 0, 1.0, 0.0, s);
+  double* Nm = (double*)ctx->buf("contract.Ckeep", sizeof(double) * std::max<int64_t>(pn->cmat, 1), s);
+  ctx->work_flops += pn->g.flops;
+  if (prec == BST_FP64) launch_gemm_f64(ctx, pn->g, At, Bt, Nm, s);
+  else run_gemm_ozaki(ctx, pn, ozaki_slices(prec), rt, rb, Nm, s, At, Bt);
 
   std::vector<PSec> secs;
   for (auto& cs : pn->vc.secs) {

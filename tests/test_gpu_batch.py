@@ -93,6 +93,53 @@ def test_batched_matches_oracle(bst, ctx, prec, tol):
         assert err <= tol, (cfg["name"], prec, err)
 
 
+@pytest.mark.parametrize("prec", ["ozaki", "bf16x3"])
+def test_tensor_core_batch_launches(bst, ctx, prec):
+    """A repeated tensor-core batch: operands whose last contracted leg is
+    their innermost leg are packed (gathered and split by one kernel), the
+    others gathered by one launch and split by one; one GEMM writes every
+    output block in its epilogue.  The corner workload (open innermost
+    legs) takes 3 launches, a batch contracted over innermost legs 2; the
+    results equal the first call's bit for bit and the oracle's."""
+    cfgs = small_configs(8)
+    inst = [gpu_instance(bst, ctx, c) for c in cfgs]
+    Cls, cs = run_batch(ctx, inst, prec)
+    torch.cuda.synchronize()
+    first = [c.clone() for c in cs]
+    l0 = ctx.launches
+    run_batch(ctx, inst, prec, Cls=Cls, cs=cs)
+    torch.cuda.synchronize()
+    assert ctx.launches - l0 == 3
+    for a, b in zip(cs, first):
+        assert torch.equal(a, b)
+    # contracted over both operands' last legs: packed
+    rng = np.random.default_rng(11)
+    As, as_, Bs, bs, refs = [], [], [], [], []
+    for i in range(6):
+        x = u1.Leg(1, (-1, 0, 1), tuple(int(v) for v in rng.integers(1, 30, 3)))
+        y = u1.Leg(1, (-1, 0, 1), tuple(int(v) for v in rng.integers(1, 30, 3)))
+        k = u1.Leg(-1, (-2, -1, 0, 1, 2), tuple(int(v) for v in rng.integers(1, 40, 5)))
+        al, bl = [x, k], [y, k.dual()]
+        A = u1.to_dense(al, rng.standard_normal(u1.nnz(al)))
+        B = u1.to_dense(bl, rng.standard_normal(u1.nnz(bl)))
+        AL = ctx.layout([bst.Leg(l.flow, l.charges, l.degs) for l in al])
+        BL = ctx.layout([bst.Leg(l.flow, l.charges, l.degs) for l in bl])
+        As.append(AL)
+        Bs.append(BL)
+        as_.append(dev(u1.from_dense(al, A)))
+        bs.append(dev(u1.from_dense(bl, B)))
+        refs.append(([x, y], np.tensordot(A, B, axes=([1], [1]))))
+    Cls2, cs2 = ctx.contract_batched(As, as_, Bs, bs, [1], [1], prec=prec)
+    torch.cuda.synchronize()
+    l0 = ctx.launches
+    ctx.contract_batched(As, as_, Bs, bs, [1], [1], prec=prec, Cls=Cls2, cs=cs2)
+    torch.cuda.synchronize()
+    assert ctx.launches - l0 == 2
+    tol = 1e-11 if prec == "ozaki" else 1e-6
+    for (cl, ref), c in zip(refs, cs2):
+        assert rel_err(c.cpu().numpy(), u1.from_dense(cl, ref)) < tol
+
+
 def test_batched_bf16x3_within_bound(bst, ctx):
     """The batch in the cheaper three-slice arithmetic: every element of
     every entry within the bound of its rounding (bf16x3_bound)."""
