@@ -73,25 +73,34 @@ def sector_keys(legs, sign):
     return reduce(sign * tot, modulus(legs)).reshape(-1)
 
 
+def cell_quarters(ul, ur, ll, lr):
+    """The four enlarged corners and the two half systems of the left cut of
+    a 2 x 2 plaquette: Q1 from the upper-left site's C1, T1, T4, a, Q2 from
+    the upper-right site's T1, C2, T2, a, Q4 from the lower-left site's T4,
+    C4, T3, a, Q3 from the lower-right site's T2, C3, T3, a (each site's
+    net holds its own environment)."""
+    e = lambda s, *x: np.einsum(s, *x, optimize=True)
+    g = lambda net, r: net[r][1]
+    X1 = e("rd,rkx->dkx", g(ul, "C1"), g(ul, "T1"))       # [C1.D, T1.D, T1.R]
+    X2 = e("dkx,dme->kxme", X1, g(ul, "T4"))              # [T1.D, T1.R, T4.R, T4.D]
+    Q1 = e("kxme,mkrd->xerd", X2, g(ul, "a"))             # [T1.R, T4.D, a.R, a.D]
+    Y1 = e("xkc,cd->xkd", g(ur, "T1"), g(ur, "C2"))       # [T1.L, T1.D, C2.D]
+    Y2 = e("xkd,dme->xkme", Y1, g(ur, "T2"))              # [T1.L, T1.D, T2.L, T2.D]
+    Q2 = e("xkme,lkmd->xeld", Y2, g(ur, "a"))             # [T1.L, T2.D, a.L, a.D]
+    Rt = e("xerd,xfrg->edfg", Q1, Q2)                     # [T4.D, a.D | T2.D, a.D]
+    Z1 = e("ukd,dr->ukr", g(ll, "T4"), g(ll, "C4"))       # [T4.U, T4.R, C4.R]
+    Z2 = e("ukr,rmx->ukmx", Z1, g(ll, "T3"))              # [T4.U, T4.R, T3.U, T3.R]
+    Q4 = e("ukmx,kwrm->uwxr", Z2, g(ll, "a"))             # [T4.U, a.U, T3.R, a.R]
+    W1 = e("ukd,dl->ukl", g(lr, "T2"), g(lr, "C3"))       # [T2.U, T2.L, C3.L]
+    W2 = e("ukl,xml->ukxm", W1, g(lr, "T3"))              # [T2.U, T2.L, T3.L, T3.U]
+    Q3 = e("ukxm,lwkm->uwxl", W2, g(lr, "a"))             # [T2.U, a.U, T3.L, a.L]
+    Rb = e("uwxr,vyxr->uwvy", Q4, Q3)                     # [T4.U, a.U | T2.U, a.U]
+    return {"X1": X1, "Q1": Q1, "Q2": Q2, "Q3": Q3, "Q4": Q4, "Rt": Rt, "Rb": Rb}
+
+
 def quarters(net):
     """The four enlarged corners and the two half systems of the left cut."""
-    C1, T1, C2, T2, C3, T3, C4, T4, a = (net[r][1] for r in ROLES)
-    e = lambda s, *x: np.einsum(s, *x, optimize=True)
-    X1 = e("rd,rkx->dkx", C1, T1)            # [C1.D, T1.D, T1.R]
-    X2 = e("dkx,dme->kxme", X1, T4)         # [T1.D, T1.R, T4.R, T4.D]
-    Q1 = e("kxme,mkrd->xerd", X2, a)        # [T1.R, T4.D, a.R, a.D]
-    Y1 = e("xkc,cd->xkd", T1, C2)           # [T1.L, T1.D, C2.D]
-    Y2 = e("xkd,dme->xkme", Y1, T2)         # [T1.L, T1.D, T2.L, T2.D]
-    Q2 = e("xkme,lkmd->xeld", Y2, a)        # [T1.L, T2.D, a.L, a.D]
-    Rt = e("xerd,xfrg->edfg", Q1, Q2)       # [T4.D, a.D | T2.D, a.D]
-    Z1 = e("ukd,dr->ukr", T4, C4)           # [T4.U, T4.R, C4.R]
-    Z2 = e("ukr,rmx->ukmx", Z1, T3)         # [T4.U, T4.R, T3.U, T3.R]
-    Q4 = e("ukmx,kwrm->uwxr", Z2, a)        # [T4.U, a.U, T3.R, a.R]
-    W1 = e("ukd,dl->ukl", T2, C3)           # [T2.U, T2.L, C3.L]
-    W2 = e("ukl,xml->ukxm", W1, T3)         # [T2.U, T2.L, T3.L, T3.U]
-    Q3 = e("ukxm,lwkm->uwxl", W2, a)        # [T2.U, a.U, T3.L, a.L]
-    Rb = e("uwxr,vyxr->uwvy", Q4, Q3)       # [T4.U, a.U | T2.U, a.U]
-    return {"X1": X1, "Q1": Q1, "Q2": Q2, "Q3": Q3, "Q4": Q4, "Rt": Rt, "Rb": Rb}
+    return cell_quarters(net, net, net, net)
 
 
 def truncate(cands, chi, rel_cutoff):
@@ -105,22 +114,25 @@ def truncate(cands, chi, rel_cutoff):
     return [c for c in order[:chi] if c[0] > rel_cutoff * smax]
 
 
-def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
-    """One LEFT move; returns the updated network (C1, T4, C4 replaced)."""
-    L = {r: net[r][0] for r in ROLES}
-    q = quarters(net)
+def plaquette_projector(ul, ur, ll, lr, chi, rel_cutoff=1e-14):
+    """Projectors of the left cut of a 2 x 2 plaquette (upper-left,
+    upper-right, lower-left, lower-right site nets): the N = R_top^T R_bot
+    of Sec. 3 per sector, global top-chi truncation, gauge, P and P~.
+    Returns (q, P3 [T4.U, a.U, new] of the lower-left site, Pt3 [new, T4.D,
+    a.D] of the upper-left site, new_leg, info)."""
+    q = cell_quarters(ul, ur, ll, lr)
     Rt, Rb = q["Rt"], q["Rb"]
-    beta_legs = [L["T2"][2], L["a"][3]]        # T2.D, a.D  (top half, right cut)
-    betap_legs = [L["T2"][0], L["a"][1]]       # T2.U, a.U  (bottom half, right cut)
-    alpha_dims = (L["T4"][2].dim, L["a"][3].dim)
-    alphap_dims = (L["T4"][0].dim, L["a"][1].dim)
+    beta_legs = [ur["T2"][0][2], ur["a"][0][3]]    # T2.D, a.D  (top half, right cut)
+    betap_legs = [lr["T2"][0][0], lr["a"][0][1]]   # T2.U, a.U  (bottom half, right cut)
+    alpha_dims = (ul["T4"][0][2].dim, ul["a"][0][3].dim)
+    alphap_dims = (ll["T4"][0][0].dim, ll["a"][0][1].dim)
     na, nap = int(np.prod(alpha_dims)), int(np.prod(alphap_dims))
     Rt_m = Rt.reshape(na, -1)                 # [alpha, beta]
     Rb_m = Rb.reshape(nap, -1)                # [alpha', beta']
     N = Rt_m.T @ Rb_m                         # [beta, beta']
     kb = sector_keys(beta_legs, -1)
     kbp = sector_keys(betap_legs, +1)
-    f_new = L["C1"][1].flow                   # the new bond keeps C1.D's flow
+    f_new = ll["C1"][0][1].flow               # the new bond keeps C1.D's flow
     mod = modulus(beta_legs)
     secs = {}
     cands = []
@@ -158,29 +170,43 @@ def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
             svals[col] = s
             col += 1
     new_leg = Leg(f_new, new_charges, new_degs, mod)
-    C1, T1, C2, T2, C3, T3, C4, T4, a = (net[r][1] for r in ROLES)
-    e = lambda s, *x: np.einsum(s, *x, optimize=True)
-    X1 = q["X1"]                                            # [C1.D, T1.D, T1.R]
     P3 = P.reshape(alphap_dims + (n_new,))
     Pt3 = Pt.reshape((n_new,) + alpha_dims)
-    C1n = e("dkx,dkc->xc", X1, P3)
-    W = e("cuk,umd->ckmd", Pt3, T4)                         # [chi, a.U, T4.R, T4.D]
+    info = {"svals": svals, "P": P, "Pt": Pt, "N": N, "kept": len(kept), "new_leg": new_leg,
+            "sectors": secs, "kb": kb, "kbp": kbp}
+    return q, P3, Pt3, new_leg, info
+
+
+def renormalise(net, X1, P3_above, Pt3_above, leg_above, P3_below, Pt3_below, leg_below):
+    """Column absorption of one site (Sec. 3): C1' = (C1 T1) P (the
+    projector of the cut above the site), T4' = P~ (T4 a) P (above, below),
+    C4' = P~ (C4 T3) (below); each divided by its Frobenius norm.  Returns
+    the three (legs, dense) pairs and the norms."""
+    L = {r: net[r][0] for r in ROLES}
+    C1, T1, C2, T2, C3, T3, C4, T4, a = (net[r][1] for r in ROLES)
+    e = lambda s, *x: np.einsum(s, *x, optimize=True)
+    C1n = e("dkx,dkc->xc", X1, P3_above)
+    W = e("cuk,umd->ckmd", Pt3_above, T4)                   # [chi, a.U, T4.R, T4.D]
     Z = e("ckmd,mkre->cdre", W, a)                          # [chi, T4.D, a.R, a.D]
-    T4n = e("cdre,dex->crx", Z, P3)                         # [chi, a.R, chi]
+    T4n = e("cdre,dex->crx", Z, P3_below)                   # [chi, a.R, chi]
     Y = e("ur,rkx->ukx", C4, T3)                            # [C4.U, T3.U, T3.R]
-    C4n = e("cuk,ukx->cx", Pt3, Y)
+    C4n = e("cuk,ukx->cx", Pt3_below, Y)
     norms = []
     for t in (C1n, T4n, C4n):
         norms.append(float(np.linalg.norm(t)))
     C1n, T4n, C4n = C1n / norms[0], T4n / norms[1], C4n / norms[2]
+    return (([L["T1"][2], leg_above], C1n), ([leg_above.dual(), L["a"][2], leg_below], T4n),
+            ([leg_below.dual(), L["T3"][2]], C4n), norms)
+
+
+def left_move(net, chi, rel_cutoff=1e-14, return_info=False):
+    """One LEFT move; returns the updated network (C1, T4, C4 replaced)."""
+    q, P3, Pt3, new_leg, info = plaquette_projector(net, net, net, net, chi, rel_cutoff)
+    C1n, T4n, C4n, norms = renormalise(net, q["X1"], P3, Pt3, new_leg, P3, Pt3, new_leg)
     out = dict(net)
-    out["C1"] = ([L["T1"][2], new_leg], C1n)
-    out["T4"] = ([new_leg.dual(), L["a"][2], new_leg], T4n)
-    out["C4"] = ([new_leg.dual(), L["T3"][2]], C4n)
+    out["C1"], out["T4"], out["C4"] = C1n, T4n, C4n
     if return_info:
-        info = {"svals": svals, "P": P, "Pt": Pt, "N": N, "kept": len(kept),
-                "norms": norms, "new_leg": new_leg, "sectors": secs,
-                "kb": kb, "kbp": kbp}
+        info["norms"] = norms
         return out, info
     return out
 
@@ -203,6 +229,83 @@ def full_move(net, chi, rel_cutoff=1e-14):
     for d in "LRUD":
         net = move(net, d, chi, rel_cutoff)
     return net
+
+
+# ---------------------------------------------------------------------------
+# Unit cells (Sec. 3.1 and Sec. 4.1: the 2 x 2 cell of the timings): an
+# Lx x Ly cell holds a site tensor per position (x right, y down), each with
+# its own environment; cell["site"][(x, y)] is that site's net (its C1..C4,
+# T1..T4 and a).  The LEFT move absorbs the cell column by column: for
+# column x every plaquette (x, y), (x+1, y), (x, y+1), (x+1, y+1) gives the
+# projectors of the cut between rows y and y+1, and column x is absorbed
+# into the left environment of column x+1 (C1' with the cut above the row,
+# T4' between the cuts above and below, C4' with the cut below), as the
+# directional scheme the paper cites for its CTM (Sec. 3) does.  A 1 x 1
+# cell is the one-site move.
+
+def cell_left_move(cell, chi, rel_cutoff=1e-14, return_info=False):
+    Lx, Ly = cell["Lx"], cell["Ly"]
+    S = {k: dict(v) for k, v in cell["site"].items()}
+    infos = []
+    for x in range(Lx):
+        xr = (x + 1) % Lx
+        proj = {}
+        for y in range(Ly):
+            yd = (y + 1) % Ly
+            proj[y] = plaquette_projector(S[(x, y)], S[(xr, y)], S[(x, yd)], S[(xr, yd)], chi, rel_cutoff)
+        new = {}
+        for y in range(Ly):
+            qa, P3a, Pt3a, la, _ = proj[(y - 1) % Ly]
+            qb, P3b, Pt3b, lb, _ = proj[y]
+            new[y] = renormalise(S[(x, y)], qb["X1"], P3a, Pt3a, la, P3b, Pt3b, lb)
+        for y in range(Ly):
+            C1n, T4n, C4n, norms = new[y]
+            tgt = S[(xr, y)]
+            tgt["C1"], tgt["T4"], tgt["C4"] = C1n, T4n, C4n
+            infos.append({"x": x, "y": y, "norms": norms, "info": proj[y][4]})
+    out = {"Lx": Lx, "Ly": Ly, "site": S}
+    return (out, infos) if return_info else out
+
+
+def rotate_cell(cell, k):
+    """The cell seen after k counter-clockwise quarter turns: the site at
+    (x, y) moves to (y, -x mod Lx) (right becomes up, down becomes right)
+    and every net is rotated as the one-site network is."""
+    for _ in range(k % 4):
+        Lx, Ly = cell["Lx"], cell["Ly"]
+        cell = {"Lx": Ly, "Ly": Lx,
+                "site": {(y, (-x) % Lx): rotate_ccw(net) for (x, y), net in cell["site"].items()}}
+    return cell
+
+
+def cell_move(cell, direction, chi, rel_cutoff=1e-14):
+    k = DIR_ROTATIONS[direction]
+    out = cell_left_move(rotate_cell(cell, k), chi, rel_cutoff)
+    return rotate_cell(out, (4 - k) % 4)
+
+
+def cell_full_move(cell, chi, rel_cutoff=1e-14):
+    """L, R, U, D cell moves in sequence."""
+    for d in "LRUD":
+        cell = cell_move(cell, d, chi, rel_cutoff)
+    return cell
+
+
+def row_value(cell, x, y):
+    """The 3 x 4 network of row y across columns x and x+1:
+    C1 T1 T1' C2' / T4 a a' T2' / C4 T3 T3' C3' (primes: column x+1)."""
+    Lx = cell["Lx"]
+    return _row_value(cell["site"][(x, y)], cell["site"][((x + 1) % Lx, y)])
+
+
+def _row_value(s0, s1):
+    C1, T1, C2, T2, C3, T3, C4, T4, a = (s0[r][1] for r in ROLES)
+    T1b, C2b, T2b, C3b, T3b, ab = (s1[r][1] for r in ("T1", "C2", "T2", "C3", "T3", "a"))
+    e = lambda s, *x: np.einsum(s, *x, optimize=True)
+    top = e("ab,akc,clf,fd->bkld", C1, T1, T1b, C2b)        # [C1.D, T1.D, T1'.D, C2'.D]
+    mid = e("bmh,mkrn,rlgs,dge->bkldhnse", T4, a, ab, T2b)  # [T4.U, a.U, a'.U, T2'.U, T4.D, a.D, a'.D, T2'.D]
+    bot = e("hi,inj,jso,eo->hnse", C4, T3, T3b, C3b)        # [C4.U, T3.U, T3'.U, C3'.U]
+    return float(e("bkld,bkldhnse,hnse->", top, mid, bot))
 
 
 def network_value(net):
