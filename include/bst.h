@@ -449,6 +449,28 @@ BST_API bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, c
                         bst_env* env, int64_t chi, double rel_cutoff, bst_prec prec,
                         bst_ctm_stats* stats, bst_stream stream);
 
+/* CTMRG move of an Lx x Ly unit cell (Sec. 3.1's unit cells; Sec. 4.1 times
+ * a 2 x 2 cell): site i = x + Lx y (x right, y down) has the double layer
+ * a[i] (rank 4, layout a_layouts[i]; BST_U1 or BST_Z2) and its own
+ * environment envs[i] (its C1..C4, T1..T4 around it).  The LEFT move
+ * absorbs the cell column by column: for column x, the plaquette of sites
+ * (x, y), (x+1, y), (x, y+1), (x+1, y+1) (positions periodic) gives the
+ * projectors of the cut between rows y and y+1 (as bst_svd_projector); then
+ * every site (x, y) is absorbed into the left environment of (x+1, y):
+ * C1 <- (C1 T1) P_above, T4 <- P~_above (T4 a) P_below, C4 <- P~_below
+ * (C4 T3), each normalised; later columns see the renewed tensors.  The
+ * other directions turn the cell by quarter turns (the site at (x, y) goes
+ * to (y, -x mod Lx)) and every tensor as in bst_ctm_move; dir 4 runs LEFT,
+ * RIGHT, UP, DOWN.  A 1 x 1 cell is bst_ctm_move.  a_layouts, a and envs
+ * are HOST arrays of Lx Ly entries; renewed tensors are written into the
+ * envs' buffers (capacities as for bst_ctm_move) and their layouts
+ * replaced.  Errors: BST_E_ARG (NULL entries, Lx Ly outside 1..64, a site
+ * not of rank 4, mixed groups), BST_E_UNSUPPORTED (SU(2)), BST_E_SYMMETRY
+ * (legs of neighbouring sites do not match), BST_E_SHAPE (capacity). */
+BST_API bst_status bst_ctm_move_cell(bst_ctx ctx, int32_t dir, int32_t Lx, int32_t Ly, const bst_layout* a_layouts,
+                                     const double* const* a, bst_env* envs, int64_t chi, double rel_cutoff,
+                                     bst_prec prec, bst_stream stream);
+
 /* ---- observables and the CTM error procedure ------------------------------ */
 
 /* Open double layer of a site A[p,l,u,r,d] (Sec. 3.2 with the physical legs

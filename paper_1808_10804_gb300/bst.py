@@ -105,6 +105,7 @@ def lib():
         "bst_svd_projector": [vp, vp, vp, vp, vp, i32, i64, dbl, i32, C.c_int, P(vp), vp, P(vp), vp,
                               P(dbl), P(i64), vp],
         "bst_ctm_move": [vp, i32, vp, vp, P(_Env), i64, dbl, C.c_int, P(_Stats), vp],
+        "bst_ctm_move_cell": [vp, i32, i32, i32, P(vp), P(vp), P(_Env), i64, dbl, C.c_int, vp],
         "bst_sym_eig": [vp, i32, i32, vp, vp, vp, C.c_int, vp],
         "bst_double_layer_open": [vp, vp, vp, vp, vp, P(vp), vp, vp],
         "bst_ctm_bond_rdm": [vp, i32, vp, vp, P(_Env), C.c_int, P(vp), vp, i64, vp],
@@ -494,6 +495,21 @@ class Context:
         env.from_c(e)
         return {"kept": list(st.kept), "smin_over_smax": list(st.smin_over_smax),
                 "trunc_weight": list(st.trunc_weight)}
+
+
+    def ctm_move_cell(self, envs, a_layouts, a, Lx, Ly, direction, chi, rel_cutoff=1e-14, prec="fp64",
+                      stream=None):
+        """Unit-cell move: envs, a_layouts, a are lists over sites x + Lx*y;
+        renewed tensors are rewritten in place."""
+        n = Lx * Ly
+        assert len(envs) == n and len(a_layouts) == n and len(a) == n
+        earr = (_Env * n)(*[e.to_c() for e in envs])
+        larr = (C.c_void_p * n)(*[L.h.value for L in a_layouts])
+        darr = (C.c_void_p * n)(*[_ptr(x) for x in a])
+        _check(lib().bst_ctm_move_cell(self.h, direction, Lx, Ly, larr, darr, earr, chi, rel_cutoff, PREC[prec],
+                                       _stream(stream)))
+        for e, ce in zip(envs, earr):
+            e.from_c(ce)
 
 
 class Env:

@@ -568,6 +568,25 @@ bst_status bst_sym_eig(bst_ctx ctx, int32_t n, int32_t batch, const double* H, d
   });
 }
 
+bst_status bst_ctm_move_cell(bst_ctx ctx, int32_t dir, int32_t Lx, int32_t Ly, const bst_layout* a_layouts,
+                             const double* const* a, bst_env* envs, int64_t chi, double rel_cutoff, bst_prec prec,
+                             bst_stream stream) {
+  return guarded([&] {
+    require_prec(prec);
+    BST_REQUIRE(ctx && a_layouts && a && envs, BST_E_ARG, "null argument");
+    BST_REQUIRE(Lx >= 1 && Ly >= 1 && int64_t(Lx) * Ly <= 64, BST_E_ARG, "cell must be 1..64 sites");
+    BST_REQUIRE(chi >= 1, BST_E_ARG, "chi must be positive");
+    Ctx* c = C_(ctx);
+    set_dev(c);
+    std::vector<Layout*> L(size_t(Lx) * Ly);
+    for (size_t i = 0; i < L.size(); ++i) {
+      BST_REQUIRE(a_layouts[i], BST_E_ARG, "site layout is NULL");
+      L[i] = L_(a_layouts[i]);
+    }
+    ctm_move_cell(c, dir, Lx, Ly, L.data(), a, envs, chi, rel_cutoff, prec, (cudaStream_t)stream);
+  });
+}
+
 bst_status bst_ctm_move(bst_ctx ctx, int32_t dir, bst_layout a_layout, const double* a, bst_env* env, int64_t chi,
                         double rel_cutoff, bst_prec prec, bst_ctm_stats* stats, bst_stream stream) {
   return guarded([&] {

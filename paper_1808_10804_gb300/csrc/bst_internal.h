@@ -400,6 +400,10 @@ inline void require_u1(const Layout* L) {
 }
 
 // ctm.cpp
+// Unit cell Lx x Ly (sites and environments in row-major position order
+// x + Lx y); abelian double layers (ctm.cpp)
+void ctm_move_cell(Ctx* ctx, int dir, int Lx, int Ly, Layout* const* a, const double* const* ad, bst_env* envs,
+                   int64_t chi, double cutoff, bst_prec prec, cudaStream_t s);
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double rel_cutoff,
               bst_prec prec, bst_ctm_stats* stats, cudaStream_t s);
 

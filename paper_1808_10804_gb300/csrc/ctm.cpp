@@ -11,8 +11,10 @@
 // Leg directions of the roles: C1[R,D] C2[L,D] C3[U,L] C4[U,R]
 // T1[L,D,R] T2[U,L,D] T3[L,U,R] T4[U,R,D], a[L,U,R,D].
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <numeric>
+#include <string>
 
 #include "bst_internal.h"
 
@@ -236,6 +238,188 @@ static void left_move(Ctx* ctx, T* r, Layout* site_dual, int64_t chi, double cut
   T Y = contract(ctx, "ctm.Y", r[C4], r[T3], {1}, {0}, prec, s);           // [C4.U, T3.U, T3.R]
   out[2] = contract(ctx, "ctm.C4n", tPt, Y, {1, 2}, {0, 1}, prec, s);    // [new^, T3.R]
   for (int i = 0; i < 3; ++i) normalise(ctx, out[i].L, const_cast<double*>(out[i].d), s);
+}
+
+// ---------------------------------------------------------------------------
+// Unit cells (Sec. 3.1; Sec. 4.1 times a 2 x 2 cell).  An Lx x Ly cell (x
+// right, y down) holds a site per position, each with its own environment.
+// The LEFT move absorbs column by column: for column x, plaquette (x, y)
+// (sites (x, y), (x+1, y), (x, y+1), (x+1, y+1)) gives the projectors of
+// the cut between rows y and y+1; then every row y of column x is absorbed
+// into the left environment of site (x+1, y): C1' = (C1 T1) P[y-1],
+// T4' = Pt[y-1] (T4 a) P[y], C4' = Pt[y] (C4 T3).  Other directions turn
+// the cell: the site at (x, y) moves to (y, -x mod Lx) and every tensor is
+// rotated as in the one-site move.
+
+// Projectors of the left cut of plaquette (ul, ur, ll, lr); P into pbuf,
+// Pt into ptbuf (named context buffers), layouts in the result.
+static ProjResult plaquette_projector(Ctx* ctx, T* ul, T* ur, T* ll, T* lr, int64_t chi, double cutoff, bst_prec prec,
+                               const std::string& pname, double** P, double** Pt, cudaStream_t s) {
+  // the one-site move's contraction sequence, each quarter from its own site
+  T X1 = contract(ctx, "ctm.X1", ul[C1], ul[T1], {0}, {0}, prec, s);                  // [C1.D, T1.D, T1.R]
+  T X2 = contract(ctx, "ctm.X2", X1, ul[T4], {0}, {0}, prec, s);                     // [T1.D, T1.R, T4.R, T4.D]
+  T Q1 = absorb(ctx, "ctm.Q1", X2, {0, 2}, {1, 0}, ul[SITE], nullptr, prec, s);      // [T1.R, T4.D, a.R, a.D]
+  T Y1 = contract(ctx, "ctm.Y1", ur[T1], ur[C2], {2}, {0}, prec, s);                  // [T1.L, T1.D, C2.D]
+  T Y2 = contract(ctx, "ctm.Y2", Y1, ur[T2], {2}, {0}, prec, s);                     // [T1.L, T1.D, T2.L, T2.D]
+  T Q2 = absorb(ctx, "ctm.Q2", Y2, {1, 2}, {1, 2}, ur[SITE], nullptr, prec, s);      // [T1.L, T2.D, a.L, a.D]
+  T Rt = contract(ctx, "ctm.Rt", Q1, Q2, {0, 2}, {0, 2}, prec, s);                   // [T4.D, a.D | T2.D, a.D]
+  T Z1 = contract(ctx, "ctm.Z1", ll[T4], ll[C4], {2}, {0}, prec, s);                  // [T4.U, T4.R, C4.R]
+  T Z2 = contract(ctx, "ctm.Z2", Z1, ll[T3], {2}, {0}, prec, s);                     // [T4.U, T4.R, T3.U, T3.R]
+  T Q4 = absorb(ctx, "ctm.Q4", Z2, {1, 2}, {0, 3}, ll[SITE], nullptr, prec, s);      // [T4.U, T3.R, a.U, a.R]
+  T W1 = contract(ctx, "ctm.W1", lr[T2], lr[C3], {2}, {0}, prec, s);                  // [T2.U, T2.L, C3.L]
+  T W2 = contract(ctx, "ctm.W2", W1, lr[T3], {2}, {2}, prec, s);                     // [T2.U, T2.L, T3.L, T3.U]
+  T Q3 = absorb(ctx, "ctm.Q3", W2, {1, 3}, {2, 3}, lr[SITE], nullptr, prec, s);      // [T2.U, T3.L, a.L, a.U]
+  T Rb = contract(ctx, "ctm.Rb", Q4, Q3, {1, 3}, {1, 2}, prec, s);                   // [T4.U, a.U | T2.U, a.U]
+  const int new_flow = ll[C1].L->legs[1].flow;
+  const int64_t pcap = Rb.L->legs[0].dim * Rb.L->legs[1].dim * chi;
+  const int64_t ptcap = Rt.L->legs[0].dim * Rt.L->legs[1].dim * chi;
+  *P = (double*)ctx->buf(pname + ".P", sizeof(double) * pcap, s);
+  *Pt = (double*)ctx->buf(pname + ".Pt", sizeof(double) * ptcap, s);
+  return svd_projector(ctx, Rt.L, Rt.d, Rb.L, Rb.d, 2, chi, cutoff, new_flow, prec, *P, *Pt, s);
+}
+
+// Column absorption of one site: C1' = (C1 T1) Pa, T4' = Pta (T4 a) Pb,
+// C4' = Ptb (C4 T3), each normalised, into buffers named by `tag`.
+static void renormalise_site(Ctx* ctx, T* r, T tPa, T tPta, T tPb, T tPtb, bst_prec prec, const std::string& tag, T out[3],
+                      cudaStream_t s) {
+  T X1 = contract(ctx, "ctm.X1", r[C1], r[T1], {0}, {0}, prec, s);                    // [C1.D, T1.D, T1.R]
+  out[0] = contract(ctx, (tag + ".C1n").c_str(), X1, tPa, {0, 1}, {0, 1}, prec, s);   // [T1.R, new_a]
+  T W = contract(ctx, "ctm.W", tPta, r[T4], {1}, {0}, prec, s);                        // [new_a^, a.D, T4.R, T4.D]
+  T Z = absorb(ctx, "ctm.Z", W, {2, 1}, {0, 1}, r[SITE], nullptr, prec, s);           // [new_a^, T4.D, a.R, a.D]
+  out[1] = contract(ctx, (tag + ".T4n").c_str(), Z, tPb, {1, 3}, {0, 1}, prec, s);     // [new_a^, a.R, new_b]
+  T Y = contract(ctx, "ctm.Y", r[C4], r[T3], {1}, {0}, prec, s);                       // [C4.U, T3.U, T3.R]
+  out[2] = contract(ctx, (tag + ".C4n").c_str(), tPtb, Y, {1, 2}, {0, 1}, prec, s);    // [new_b^, T3.R]
+  for (int i = 0; i < 3; ++i) normalise(ctx, out[i].L, const_cast<double*>(out[i].d), s);
+}
+
+void ctm_move_cell(Ctx* ctx, int dir, int Lx, int Ly, Layout* const* a, const double* const* ad, bst_env* envs,
+                   int64_t chi, double cutoff, bst_prec prec, cudaStream_t s) {
+  BST_REQUIRE(dir >= 0 && dir <= 4, BST_E_ARG, "dir must be 0..4");
+  BST_REQUIRE(Lx >= 1 && Ly >= 1 && Lx * Ly <= 64, BST_E_ARG, "cell must be 1..64 sites");
+  const int nsite = Lx * Ly;
+  for (int i = 0; i < nsite; ++i) {
+    BST_REQUIRE(a[i] && ad[i], BST_E_ARG, "site is NULL");
+    BST_REQUIRE(a[i]->rank == 4, BST_E_ARG, "cell sites must be double layers a[L,U,R,D]");
+    BST_REQUIRE(a[i]->group != BST_SU2, BST_E_UNSUPPORTED, "unit cells: abelian groups only");
+    for (int j = 0; j < 4; ++j) {
+      bst_env* e = &envs[i];
+      BST_REQUIRE(e->C[j] && e->T[j] && e->c[j] && e->t[j], BST_E_ARG, "env has a null entry");
+      BST_REQUIRE(L_(e->C[j])->rank == 2 && L_(e->T[j])->rank == 3, BST_E_ARG, "env ranks must be 2 (C) and 3 (T)");
+      BST_REQUIRE(L_(e->C[j])->group == a[i]->group && L_(e->T[j])->group == a[i]->group, BST_E_ARG,
+                  "environment and site belong to different symmetry groups");
+    }
+  }
+  std::vector<int> seq;
+  if (dir == 4) seq = {0, 2, 1, 3};  // LEFT, RIGHT, UP, DOWN
+  else seq = {dir};
+  for (int d : seq) {
+    const int k = d;  // quarter turns (LEFT 0, UP 1, RIGHT 2, DOWN 3)
+    std::vector<Src> rot = rotation(k);
+    // rotated cell: position of every original site after k turns
+    int lx = Lx, ly = Ly;
+    std::vector<int> px(nsite), py(nsite);
+    for (int i = 0; i < nsite; ++i) px[i] = i % Lx, py[i] = i / Lx;
+    for (int t = 0; t < k; ++t) {
+      for (int i = 0; i < nsite; ++i) {
+        const int x = px[i], y = py[i];
+        px[i] = y;
+        py[i] = ((-x) % lx + lx) % lx;
+      }
+      std::swap(lx, ly);
+    }
+    std::vector<int> at(nsite);  // rotated position -> original site index
+    for (int i = 0; i < nsite; ++i) at[px[i] + lx * py[i]] = i;
+    // the rotated tensors of every site (role n of rotated site j)
+    std::vector<std::vector<T>> R(nsite, std::vector<T>(NROLE));
+    for (int j = 0; j < nsite; ++j) {
+      const int i = at[j];
+      T orig[NROLE];
+      for (int q = 0; q < 4; ++q) {
+        orig[C1 + q] = {L_(envs[i].C[q]), envs[i].c[q]};
+        orig[T1 + q] = {L_(envs[i].T[q]), envs[i].t[q]};
+      }
+      orig[SITE] = {a[i], ad[i]};
+      for (int n = 0; n < NROLE; ++n) {
+        const Src& src = rot[n];
+        if (is_identity(src.perm)) {
+          R[j][n] = orig[src.role];
+        } else {
+          Layout* dst = nullptr;
+          DevRelayout* rp = get_permute_plan(ctx, orig[src.role].L, src.perm, &dst);
+          const std::string nm = "cell.rot." + std::to_string(j) + "." + std::to_string(n);
+          double* buf = (double*)ctx->buf(nm, sizeof(double) * std::max<int64_t>(dst->nnz, 1), s);
+          launch_relayout(ctx, *rp, orig[src.role].d, buf, 0, 1.0, 0.0, s);
+          release(dst);  // interned
+          R[j][n] = {dst, buf};
+        }
+      }
+    }
+    // LEFT move of the rotated cell, column by column
+    for (int x = 0; x < lx; ++x) {
+      const int xr = (x + 1) % lx;
+      std::vector<ProjResult> pr(ly);
+      std::vector<double*> P(ly), Pt(ly);
+      for (int y = 0; y < ly; ++y) {
+        const int yd = (y + 1) % ly;
+        pr[y] = plaquette_projector(ctx, R[x + lx * y].data(), R[xr + lx * y].data(), R[x + lx * yd].data(),
+                                    R[xr + lx * yd].data(), chi, cutoff, prec, "cell.p" + std::to_string(y), &P[y],
+                                    &Pt[y], s);
+      }
+      std::vector<std::array<T, 3>> out(ly);
+      for (int y = 0; y < ly; ++y) {
+        const int ya = (y - 1 + ly) % ly;
+        T o[3];
+        renormalise_site(ctx, R[x + lx * y].data(), {pr[ya].P, P[ya]}, {pr[ya].Pt, Pt[ya]}, {pr[y].P, P[y]},
+                         {pr[y].Pt, Pt[y]}, prec, "cell.n" + std::to_string(xr + lx * y), o, s);
+        out[y] = {o[0], o[1], o[2]};
+      }
+      for (int y = 0; y < ly; ++y) {
+        R[xr + lx * y][C1] = out[y][0];
+        R[xr + lx * y][T4] = out[y][1];
+        R[xr + lx * y][C4] = out[y][2];
+      }
+      for (auto& q : pr) {
+        release(q.P);
+        release(q.Pt);
+      }
+    }
+    // renewed C1, T4, C4 of every rotated site back to the original frame
+    const int renewed[3] = {C1, T4, C4};
+    for (int j = 0; j < nsite; ++j) {
+      bst_env* env = &envs[at[j]];
+      for (int q = 0; q < 3; ++q) {
+        const Src& src = rot[renewed[q]];
+        const T& o = R[j][renewed[q]];
+        std::vector<int> inv(src.perm.size());
+        for (size_t m = 0; m < src.perm.size(); ++m) inv[src.perm[m]] = int(m);
+        double* dst;
+        int64_t cap;
+        bst_layout* slot;
+        if (src.role < T1) {
+          dst = env->c[src.role - C1];
+          cap = env->c_cap[src.role - C1];
+          slot = &env->C[src.role - C1];
+        } else {
+          dst = env->t[src.role - T1];
+          cap = env->t_cap[src.role - T1];
+          slot = &env->T[src.role - T1];
+        }
+        Layout* nl = nullptr;
+        if (is_identity(inv)) {
+          nl = o.L;
+          retain(nl);
+          BST_REQUIRE(nl->nnz <= cap, BST_E_SHAPE, "env buffer capacity too small for the renewed tensor");
+          BST_CUDA(cudaMemcpyAsync(dst, o.d, sizeof(double) * nl->nnz, cudaMemcpyDeviceToDevice, s));
+        } else {
+          DevRelayout* rp = get_permute_plan(ctx, o.L, inv, &nl);
+          BST_REQUIRE(nl->nnz <= cap, BST_E_SHAPE, "env buffer capacity too small for the renewed tensor");
+          launch_relayout(ctx, *rp, o.d, dst, 0, 1.0, 0.0, s);
+        }
+        release(L_(*slot));
+        *slot = reinterpret_cast<bst_layout>(nl);
+      }
+    }
+  }
 }
 
 void ctm_move(Ctx* ctx, int dir, Layout* a, const double* ad, bst_env* env, int64_t chi, double cutoff,
