@@ -719,10 +719,15 @@ def run_ours(args):
                     "digit_product_tflops": (15.0 if prec == "ozaki" else 6.0) * fl / sec / 1e12}
         if name == "gemm_f64":
             peak = pk["bf16_tflops"] * 1.25 / 2250.0   # FP64 tensor peak from the nominal ratio
-            a = algo_flops / sec / 1e12
+            if prec == "fp64":
+                a, work = algo_flops / sec / 1e12, "method flops of the step, counted once"
+            else:
+                # the mixed path runs only the projector's small FP64
+                # products here: their own flops
+                a, work = fl / sec / 1e12, "flops of the FP64 products of the class"
             return {"kernel": name, "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s",
-                    "frac": a / peak, "work": "method flops of the step, counted once"}
-        if name in ("cholinv_f32", "jacobi_f32"):
+                    "frac": a / peak, "work": work}
+        if name in ("cholinv_f32", "jacobi_f32", "gram_f32"):
             a = fl / sec / 1e12
             return {"kernel": name, "bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": a / fp32_peak}

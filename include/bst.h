@@ -232,7 +232,12 @@ BST_API bst_status bst_layout_dual(bst_layout l, bst_layout* out);
 
 /* dst = src with legs permuted: dst leg j is src leg perm[j].  Returns the
  * canonical layout of the permuted legs in *dst (new reference) and writes
- * nnz(src) doubles to dst_data (must not alias src_data). */
+ * nnz(src) doubles to dst_data (must not alias src_data).  SU(2): the trees
+ * of the permuted legs are recoupled: reduced block t' of dst is
+ * sum_t R[t', t] (block t of the same sector tuple, legs permuted) with
+ * R[t', t] = <c'_t', c_t permuted> / (2J'+1) from the Clebsch-Gordan
+ * tensors (Sec. 2, Eq. tensor-cgc), so the dense tensor is permuted
+ * exactly. */
 BST_API bst_status bst_permute(bst_ctx ctx, bst_layout src, const double* src_data,
                        const int32_t* perm, bst_layout* dst, double* dst_data,
                        bst_stream stream);

@@ -49,6 +49,7 @@ Ctx::~Ctx() {
   if (ev_join) cudaEventDestroy(ev_join);
   projviews.clear();
   su2plans.clear();
+  su2perm.clear();
   bplans.clear();
   ozplans.clear();
   cplans.clear();
@@ -313,11 +314,19 @@ bst_status bst_permute(bst_ctx ctx, bst_layout src, const double* src_data, cons
                        double* dst_data, bst_stream stream) {
   return guarded([&] {
     BST_REQUIRE(ctx && src && perm && dst, BST_E_ARG, "null argument");
-    require_u1(L_(src));
     Ctx* c = C_(ctx);
     set_dev(c);
     Layout* S = L_(src);
     std::vector<int> p(perm, perm + S->rank);
+    if (S->group == BST_SU2) {
+      // trees recoupled to the permuted leg order
+      BST_REQUIRE(S->nnz == 0 || (src_data && dst_data), BST_E_ARG, "data pointer is NULL");
+      Layout* D = su2_permute(c, S, src_data, p, dst_data, (cudaStream_t)stream);
+      retain(D);
+      *dst = H_(D);
+      return;
+    }
+    require_u1(S);
     Layout* D = nullptr;
     DevRelayout* rp = get_permute_plan(c, S, p, &D);
     if (S->nnz) {

@@ -174,6 +174,7 @@ struct DevGemm {
 struct OzakiPlan;  // mixed-precision GEMM plan (gemm_ozaki.cu)
 struct BatchPlan;  // batched-contraction plan (batch.cu)
 struct Su2Plan;    // SU(2) contraction plan (su2.cu)
+struct Su2PermPlan;  // SU(2) permutation with recoupling (su2.cu)
 struct ProjView;   // projector layout view (projector.cu)
 
 // Contraction plan (cached per (A, B, pairs)).
@@ -221,6 +222,7 @@ struct Ctx {
   std::map<std::string, std::shared_ptr<BatchPlan>> bplans;  // deleter bound in batch.cu
   std::map<std::string, std::shared_ptr<OzakiPlan>> ozplans;  // deleter bound in gemm_ozaki.cu
   std::map<std::string, std::shared_ptr<Su2Plan>> su2plans;   // deleter bound in su2.cu
+  std::map<std::string, std::shared_ptr<Su2PermPlan>> su2perm; // deleter bound in su2.cu
   std::map<std::string, std::shared_ptr<ProjView>> projviews; // deleter bound in projector.cu
   std::map<uint64_t, DevBuf> su2_weights;  // SU(2) layout id -> per-element 2J+1 (norms)
   int* d_err = nullptr;                     // device error word
@@ -387,6 +389,10 @@ double su2_cg(int tj1, int tm1, int tj2, int tm2, int tJ, int tM);  // doubled s
 int su2_ntree(const std::vector<Leg>& legs);
 void su2_enum_blocks(const std::vector<Leg>& legs, std::vector<int32_t>& sect, std::vector<int32_t>& tree);
 Layout* su2_contract_layout(Ctx* ctx, Layout* A, Layout* B, const std::vector<int>& la, const std::vector<int>& lb);
+// dst = src with legs permuted (dst leg j = src leg perm[j]), trees recoupled;
+// returns the (interned) dst layout; src/dst may be null when nnz is 0
+Layout* su2_permute(Ctx* ctx, Layout* S, const double* src, const std::vector<int>& perm, double* dst,
+                    cudaStream_t s);
 void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double* b, const std::vector<int>& la,
                   const std::vector<int>& lb, bst_prec prec, double alpha, double beta, Layout* C, double* c,
                   cudaStream_t s);

@@ -35,6 +35,7 @@
 #include <unordered_map>
 
 #include "bst_internal.h"
+#include "relayout_dev.cuh"
 
 namespace bst {
 
@@ -711,6 +712,217 @@ void su2_contract(Ctx* ctx, Layout* A, const double* a, Layout* B, const double*
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Permutation with recoupling.  A block of S with sector tuple s and tree t
+// is m_t (x) c_t; permuting the legs gives m_t^P (x) c_t^P, and c_t^P is a
+// combination of the permuted layout's basis tensors of the same tuple,
+//     c_t^P = sum_t' R[t', t] c'_t',  R[t', t] = <c'_t', c_t^P> / (2 J' + 1)
+// (the bases are orthogonal with ||c||^2 = 2J+1), so the permuted tensor's
+// reduced block t' is sum_t R[t', t] m_t^P.  R comes from the dense CGC
+// tensors at plan time; the kernel forms every output element as that sum
+// over the source trees of its tuple, each read through the permutation.
+
+struct Su2PermTask {
+  int64_t out_off;
+  int32_t rank, n;
+  int32_t shape[kMaxRank];  // output block extents (permuted leg order)
+  int64_t istr[kMaxRank];   // stride in the source block of each output leg
+  int64_t term0;
+  int32_t nterm, pad;
+};
+
+struct Su2PermTerm {
+  int64_t in_off;
+  double coef;
+};
+
+struct Su2PermPlan {
+  Layout* dst = nullptr;
+  Su2PermTask* tasks = nullptr;
+  Su2PermTerm* terms = nullptr;
+  int2* chunks = nullptr;
+  int ntasks = 0, nchunks = 0;
+  double elems = 0;
+  ~Su2PermPlan() {
+    cudaFree(tasks);
+    cudaFree(terms);
+    cudaFree(chunks);
+    if (dst) release(dst);
+  }
+};
+
+constexpr int kPermChunk = 1024;
+constexpr int kPermThreads = 256;
+
+__global__ void __launch_bounds__(kPermThreads) su2_permute_kernel(const Su2PermTask* __restrict__ tasks,
+                                                                   const Su2PermTerm* __restrict__ terms,
+                                                                   const int2* __restrict__ chunks,
+                                                                   const double* __restrict__ src,
+                                                                   double* __restrict__ dst) {
+  const int2 c = chunks[blockIdx.x];
+  const Su2PermTask& t = tasks[c.x];
+  FastDiv fd[kMaxRank];
+#pragma unroll
+  for (int i = 0; i < kMaxRank; ++i) fd[i].init(i < t.rank ? uint32_t(t.shape[i]) : 1u);
+  const int end = min(t.n, c.y + kPermChunk);
+  for (int e = c.y + int(threadIdx.x); e < end; e += kPermThreads) {
+    uint32_t rem = uint32_t(e);
+    long long o = 0;
+#pragma unroll
+    for (int i = kMaxRank - 1; i >= 0; --i) {
+      if (i < t.rank) {
+        const uint32_t q = fd[i].div(rem);
+        o += (long long)(rem - q * fd[i].d) * t.istr[i];
+        rem = q;
+      }
+    }
+    double v = 0.0;
+    for (int k = 0; k < t.nterm; ++k) {
+      const Su2PermTerm tm = terms[t.term0 + k];
+      v = fma(tm.coef, src[tm.in_off + o], v);
+    }
+    dst[t.out_off + e] = v;
+  }
+}
+
+static Su2PermPlan* build_su2_perm(Ctx* ctx, Layout* S, const std::vector<int>& perm) {
+  const int r = S->rank;
+  std::vector<Leg> dl(r);
+  for (int j = 0; j < r; ++j) dl[j] = S->legs[perm[j]];
+  auto* P = new Su2PermPlan();
+  P->dst = make_layout(ctx, BST_SU2, dl);
+  Layout* D = P->dst;
+  const std::vector<int> fs = flows_of(S), fd = flows_of(D);
+  // R per source sector tuple: R[t' * nsrc + t] over its trees
+  std::map<std::vector<int32_t>, std::vector<double>> rcache;
+  std::vector<Su2PermTask> tasks;
+  std::vector<Su2PermTerm> terms;
+  std::vector<int32_t> ts(r);
+  for (int64_t b = 0; b < D->nblocks; ++b) {
+    const int32_t* sd = &D->sect[b * r];
+    for (int j = 0; j < r; ++j) ts[perm[j]] = sd[j];
+    const int64_t b0 = S->block_of(ts.data());
+    BST_REQUIRE(b0 >= 0, BST_E_SHAPE, "SU(2) permute: source sector tuple missing");
+    int64_t nsrc = 0;
+    while (b0 + nsrc < S->nblocks && std::equal(ts.begin(), ts.end(), &S->sect[(b0 + nsrc) * r])) ++nsrc;
+    // the destination trees of this tuple: consecutive blocks
+    int64_t d0 = b;
+    while (d0 > 0 && std::equal(sd, sd + r, &D->sect[(d0 - 1) * r])) --d0;
+    int64_t ndst = 0;
+    while (d0 + ndst < D->nblocks && std::equal(sd, sd + r, &D->sect[(d0 + ndst) * r])) ++ndst;
+    auto it = rcache.find(ts);
+    if (it == rcache.end()) {
+      const std::vector<int> tjs = spins_of(S, b0), tjd = spins_of(D, d0);
+      std::vector<std::vector<double>> cs(nsrc), cd(ndst);
+      std::vector<int64_t> ext(r), sstr(r);
+      for (int i = 0; i < r; ++i) ext[i] = tjs[i] + 1;
+      int64_t st = 1;
+      for (int i = r - 1; i >= 0; --i) sstr[i] = st, st *= ext[i];
+      for (int64_t t = 0; t < nsrc; ++t) {
+        const std::vector<double> c = basis_tensor(tjs, fs, &S->tree[(b0 + t) * S->ntree]);
+        // permuted: element m' (dst order) = c at m_{perm[j]} = m'_j
+        std::vector<double> cp(c.size());
+        std::vector<int> idx(r, 0);
+        for (size_t e = 0; e < cp.size(); ++e) {
+          int64_t so = 0;
+          for (int j = 0; j < r; ++j) so += idx[j] * sstr[perm[j]];
+          cp[e] = c[so];
+          for (int j = r - 1; j >= 0; --j) {
+            if (++idx[j] < int(ext[perm[j]])) break;
+            idx[j] = 0;
+          }
+        }
+        cs[t] = std::move(cp);
+      }
+      for (int64_t t = 0; t < ndst; ++t) cd[t] = basis_tensor(tjd, fd, &D->tree[(d0 + t) * D->ntree]);
+      int nin = 0;
+      for (int f : fd) nin += f == 1;
+      const int jpos = std::max(nin - 2, 0);
+      std::vector<double> R(size_t(ndst * nsrc), 0.0);
+      for (int64_t u = 0; u < ndst; ++u) {
+        const double w = double(D->tree[(d0 + u) * D->ntree + jpos] + 1);
+        for (int64_t t = 0; t < nsrc; ++t) {
+          double dot = 0.0;
+          for (size_t e = 0; e < cd[u].size(); ++e) dot += cd[u][e] * cs[t][e];
+          R[size_t(u * nsrc + t)] = dot / w;
+        }
+      }
+      it = rcache.emplace(ts, std::move(R)).first;
+    }
+    const std::vector<double>& R = it->second;
+    Su2PermTask tk{};
+    tk.out_off = D->offset[b];
+    tk.rank = r;
+    int64_t n = 1;
+    std::vector<int64_t> bstr(r);
+    int64_t st = 1;
+    for (int i = r - 1; i >= 0; --i) bstr[i] = st, st *= S->shape[b0 * r + i];
+    for (int j = 0; j < r; ++j) {
+      tk.shape[j] = int32_t(D->shape[b * r + j]);
+      tk.istr[j] = bstr[perm[j]];
+      n *= tk.shape[j];
+    }
+    tk.n = int32_t(n);
+    tk.term0 = int64_t(terms.size());
+    for (int64_t t = 0; t < nsrc; ++t) {
+      const double c = R[size_t((b - d0) * nsrc + t)];
+      if (std::fabs(c) > 1e-14) terms.push_back({S->offset[b0 + t], c});
+    }
+    tk.nterm = int32_t(int64_t(terms.size()) - tk.term0);
+    if (n > 0) tasks.push_back(tk);
+  }
+  std::vector<int2> ch;
+  for (int i = 0; i < int(tasks.size()); ++i) {
+    P->elems += tasks[i].n;
+    for (int e = 0; e < tasks[i].n; e += kPermChunk) ch.push_back(make_int2(i, e));
+  }
+  P->ntasks = int(tasks.size());
+  P->nchunks = int(ch.size());
+  auto up = [](auto** dst, const auto& v) {
+    using T = typename std::remove_reference<decltype(v)>::type::value_type;
+    if (v.empty()) return;
+    BST_CUDA(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+    BST_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  };
+  up(&P->tasks, tasks);
+  up(&P->terms, terms);
+  up(&P->chunks, ch);
+  return P;
+}
+
+Layout* su2_permute(Ctx* ctx, Layout* S, const double* src, const std::vector<int>& perm, double* dst,
+                    cudaStream_t s) {
+  BST_REQUIRE(S->group == BST_SU2, BST_E_ARG, "su2_permute: not an SU(2) layout");
+  BST_REQUIRE(int(perm.size()) == S->rank, BST_E_ARG, "perm must list every leg");
+  std::vector<bool> seen(S->rank, false);
+  for (int x : perm) {
+    BST_REQUIRE(x >= 0 && x < S->rank && !seen[x], BST_E_ARG, "perm is not a permutation");
+    seen[x] = true;
+  }
+  std::string key = "su2perm/" + std::to_string(S->id) + "/";
+  for (int x : perm) key += std::to_string(x) + ",";
+  Su2PermPlan* P = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->su2perm.find(key);
+    if (it != ctx->su2perm.end()) P = it->second.get();
+  }
+  if (!P) {
+    std::shared_ptr<Su2PermPlan> np(build_su2_perm(ctx, S, perm));
+    P = np.get();
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->su2perm[key] = std::move(np);
+  }
+  if (P->nchunks > 0) {
+    BST_REQUIRE(src && dst, BST_E_ARG, "data pointer is NULL");
+    ProfScope ps(ctx, s, "relayout", 0.0, 16.0 * P->elems);
+    su2_permute_kernel<<<P->nchunks, kPermThreads, 0, s>>>(P->tasks, P->terms, P->chunks, src, dst);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
+  }
+  return P->dst;
 }
 
 }  // namespace bst

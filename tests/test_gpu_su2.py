@@ -237,3 +237,22 @@ def test_su2_full_corner_sampled_oracle(full_corner, pick):
             checked += 1
         pos += n
     assert checked >= 1
+
+
+@pytest.mark.parametrize("flows", [(1, -1, -1), (1, 1, -1, -1), (-1, 1, -1, 1), (1, 1, 1, -1, -1), (-1, -1, -1, 1)])
+@pytest.mark.parametrize("seed", range(3))
+def test_su2_permute_matches_oracle(bst, ctx, flows, seed):
+    """Leg permutation with tree recoupling: the dense tensor of the result
+    is the dense tensor of the input with its axes permuted."""
+    rng = np.random.default_rng(900 + 31 * seed + len(flows))
+    legs = rand_legs(rng, flows, maxspin=3)
+    x = rng.standard_normal(su2.nnz(legs))
+    perm = [int(i) for i in rng.permutation(len(legs))]
+    L = ctx.layout(bst_legs(bst, legs), group="su2")
+    DL, out = ctx.permute(L, dev(x), perm)
+    ctx.sync()
+    dlegs = [legs[p] for p in perm]
+    assert [(l.flow, tuple(l.charges), tuple(l.degs)) for l in DL.legs] == \
+        [(l.flow, tuple(l.spins), tuple(l.degs)) for l in dlegs]
+    want = su2.from_dense(dlegs, np.transpose(su2.to_dense(legs, x), perm))
+    assert rel_err(out.cpu().numpy(), want) < 1e-13
