@@ -757,7 +757,11 @@ def run_ours(args):
     for name, rep in subs.items():
         if rep:
             print(json.dumps({"sub_workload": name, **rep}), file=sys.stderr, flush=True)
-    brief = {name: {k: (round(rep[k], 6) if isinstance(rep.get(k), float) else rep.get(k))
+    def short(k, v):
+        if not isinstance(v, float):
+            return v
+        return float(f"{v:.3e}") if k == "rel_err_vs_fp64_path" else round(v, 6)
+    brief = {name: {k: short(k, rep.get(k))
                     for k in ("value", "unit", "ms_per_step", "fp64_path_ms_per_step", "rel_err_vs_fp64_path")}
              for name, rep in subs.items() if rep}
     line = {

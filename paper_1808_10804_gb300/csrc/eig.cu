@@ -19,6 +19,7 @@ namespace bst {
 
 constexpr int kEigMax = 160;
 constexpr int kOaMax = 160;  // largest b of oa_update
+constexpr int kGramMaxParts = 16;  // most K slices of a partial Gram matrix
 
 struct SmallProb {
   int32_t b, pad;
@@ -234,7 +235,8 @@ constexpr int kBjThreads = 512;
 __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* __restrict__ probs,
                                                                const double* __restrict__ in,
                                                                double* __restrict__ out, double* __restrict__ vals,
-                                                               int max_sweeps, float tfloor, float junk) {
+                                                               int max_sweeps, float tfloor, float junk,
+                                                               int* __restrict__ sweeps_used) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
   const int b = pr.b;
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
   }
   __syncthreads();
   const float kTau = fminf(1e-5f, fmaxf(tfloor, 1e-30f));
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
     // convergence: the scalar kernel's test (relative with floor, or the
     // remaining rotation below 1e-6 rad; pairs both below junk left out)
     float worst = 0.f;
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
       __syncthreads();
     }
   }
+  if (sweeps_used && tid == 0) sweeps_used[blockIdx.x] = sweep;  // sweeps run (max_sweeps: not converged)
   for (int i = tid; i < b; i += nt) {
     float ai = A[i * ld + i];
     if (ai != ai) ai = -INFINITY;
@@ -639,19 +643,72 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const float* G = nparts > 0 ? gin + pr.in_off : nullptr;
+  if (G) {
+    // FP32 partial sums, added in slice order.  Every thread keeps the
+    // loads of all slices of one 4-wide group in flight at once (the sums
+    // are latency bound otherwise); with b and the offset multiples of 4
+    // the groups are aligned 16-byte words of each partial.
+    const int b4 = ((b & 3) || (pr.in_off & 3)) ? 0 : b >> 2;
+    for (int q = tid; q < (b4 ? 0 : b * b); q += kCholThreads) {  // (b not a multiple of 4)
+      const int i = q / b, j = q - i * b;
+      float g = 0.f;
+      for (int s = 0; s < nparts; ++s) g += G[(long long)s * bb + q];
+      L[i * ld + j] = g;
+    }
+    for (int g4 = tid; g4 < b * b4; g4 += kCholThreads) {
+      const int i = g4 / b4, j = (g4 - i * b4) << 2;
+      const float4* src = reinterpret_cast<const float4*>(G + (long long)i * b + j);
+      float4 part[kGramMaxParts];
+#pragma unroll
+      for (int s = 0; s < kGramMaxParts; ++s)
+        part[s] = s < nparts ? __ldg(src + (long long)s * (bb >> 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < kGramMaxParts; ++s)
+        if (s < nparts) {
+          g.x += part[s].x;
+          g.y += part[s].y;
+          g.z += part[s].z;
+          g.w += part[s].w;
+        }
+      float* row = L + i * ld + j;
+      row[0] = g.x;
+      row[1] = g.y;
+      row[2] = g.z;
+      row[3] = g.w;
+    }
+    // padding: identity
+    for (int q = tid; q < bp * bp; q += kCholThreads) {
+      const int i = q / bp, j = q - i * bp;
+      if (i >= b || j >= b) L[i * ld + j] = (i == j) ? 1.f : 0.f;
+      Li[i * ld + j] = 0.f;
+    }
+    __syncthreads();
+    // unit-diagonal scaling: row i times 1 / sqrt(M_ii) = rsc[i] 2^ksc[i]
+    for (int i = tid; i < bp; i += kCholThreads) {
+      int k = 0;
+      float r = 1.f;
+      if (i < b) {
+        const double d = double(L[i * ld + i]);
+        if (d > 0) split_pow2(1.0 / sqrt(d), &k, &r);
+      }
+      ksc[i] = k;
+      rsc[i] = r;
+      drop[i] = 0;
+    }
+    __syncthreads();
+    // (the power of two exactly, the mantissas as two FP32 products)
+    for (int q = tid; q < b * b; q += kCholThreads) {
+      const int i = q / b, j = q - i * b;
+      L[i * ld + j] = ldexpf(L[i * ld + j], ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+    }
+  } else {
   // unit-diagonal scaling: row i times 1 / sqrt(M_ii) = rsc[i] 2^ksc[i]
   for (int i = tid; i < bp; i += kCholThreads) {
     int k = 0;
     float r = 1.f;
     if (i < b) {
-      double d;
-      if (G) {
-        float ds = 0.f;
-        for (int s = 0; s < nparts; ++s) ds += G[(long long)s * bb + (long long)i * b + i];
-        d = double(ds);
-      } else {
-        d = M[(long long)i * b + i];
-      }
+      const double d = M[(long long)i * b + i];
       if (d > 0) split_pow2(1.0 / sqrt(d), &k, &r);
     }
     ksc[i] = k;
@@ -659,23 +716,6 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
     drop[i] = 0;
   }
   __syncthreads();
-  if (G) {
-    // FP32 partial sums: added in slice order, then scaled (the power of two
-    // exactly, the mantissas as two FP32 products)
-    for (int q = tid; q < bp * bp; q += kCholThreads) {
-      const int i = q / bp, j = q - i * bp;
-      float a;
-      if (i < b && j < b) {
-        float g = 0.f;
-        for (int s = 0; s < nparts; ++s) g += G[(long long)s * bb + (long long)i * b + j];
-        a = ldexpf(g, ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
-      } else {
-        a = (i == j) ? 1.f : 0.f;
-      }
-      L[i * ld + j] = a;
-      Li[i * ld + j] = 0.f;
-    }
-  } else {
   for (int q0 = tid; q0 < bp * bp; q0 += 4 * kCholThreads) {
     double v[4];
 #pragma unroll

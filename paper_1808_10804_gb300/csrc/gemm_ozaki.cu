@@ -48,9 +48,9 @@ constexpr long long kDrainLimit = 1ll << 30;  // bound of the waits for issued c
 // Shape of one instantiation: S digit slices per operand (5: the FP64-
 // accurate split; 3: 26 bits, the cheaper arithmetic), output tiles of
 // 128 x TN (TN = 64, or 32 for narrow problems: twice the tiles).
-//   tensor memory: d0, d1, d2 double-buffered (6 TN columns), then for
-//   S = 5 the whole-K diagonals d3 and d4 (2 TN more); allocated as the
-//   next power of two.
+//   tensor memory: d0, d1, d2 side by side, double-buffered (buffer b at
+//   columns 3 TN b), then for S = 5 the whole-K diagonals d3 and d4 (2 TN
+//   more, from 6 TN); allocated as the next power of two.
 template <int S, int TN>
 struct Cfg {
   static_assert(S == 5 || S == 3, "digit slices");
@@ -162,12 +162,14 @@ __host__ __device__ constexpr uint32_t instr_desc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
 }
 
-template <int TN>
+// D[128 x N] (+)= A[128 x 16] B[N x 16]^T; N a multiple of 16, at most 256
+template <int N>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "tcgen05.mma kind::f16 with M = 128");
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(instr_desc<TN>()), "r"(acc));
+      "l"(a), "l"(b), "r"(instr_desc<N>()), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -335,23 +337,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t a0 = smem_u32(sm.stage[s]);
           const uint32_t b0 = a0 + S * kABytes;
+          // The slices of B are stacked in the stage (slice j: rows
+          // j TN .. j TN + TN - 1), so B slices j .. j + n - 1 form one
+          // operand of n TN rows; in tensor memory the diagonals of a
+          // buffer lie side by side (d at buf 3 TN + d TN; d3, d4 at
+          // kColD3).  A slice i times B slices j .. j + n - 1 thus adds into
+          // diagonals i + j .. i + j + n - 1 with one product: 8 products
+          // of width TN .. 3 TN per 16 K instead of 15 of width TN (S = 5),
+          // 3 instead of 6 (S = 3), each reading its A slice once.
+          const uint32_t cb = tmem + uint32_t(buf * 3 * TN);
+          const uint32_t c3 = tmem + uint32_t(kColD3);
           for (int ks = 0; ks < kTK / 16; ++ks) {
-            for (int d = 0; d < S; ++d) {
-              for (int i = 0; i <= d; ++i) {
-                const int j = d - i;
-                uint32_t col;
-                uint32_t acc;
-                if (d <= 2) {
-                  col = d * 2 * TN + buf * TN;
-                  acc = (!first || ks > 0 || i > 0) ? 1u : 0u;
-                } else {
-                  col = kColD3 + (d - 3) * TN;
-                  acc = (c > 0 || ks > 0 || i > 0) ? 1u : 0u;
-                }
-                const uint64_t ad = smem_desc(a0 + i * kABytes + ks * 32);
-                const uint64_t bd = smem_desc(b0 + j * kBBytes + ks * 32);
-                mma_bf16<TN>(tmem + col, ad, bd, acc);
-              }
+            const uint32_t acc_b = (!first || ks > 0) ? 1u : 0u;  // first writer of d0..d2 in this pair
+            const uint32_t acc_3 = (c > 0 || ks > 0) ? 1u : 0u;   // first writer of d3, d4 in this tile
+            auto ad = [&](int i) { return smem_desc(a0 + i * kABytes + ks * 32); };
+            auto bd = [&](int j) { return smem_desc(b0 + j * kBBytes + ks * 32); };
+            mma_bf16<3 * TN>(cb, ad(0), bd(0), acc_b);           // d0 d1 d2 += A0 [B0 B1 B2]
+            if constexpr (S == 5) mma_bf16<2 * TN>(c3, ad(0), bd(3), acc_3);  // d3 d4 += A0 [B3 B4]
+            mma_bf16<2 * TN>(cb + TN, ad(1), bd(0), 1u);         // d1 d2 += A1 [B0 B1]
+            if constexpr (S == 5) mma_bf16<2 * TN>(c3, ad(1), bd(2), 1u);     // d3 d4 += A1 [B2 B3]
+            mma_bf16<TN>(cb + 2 * TN, ad(2), bd(0), 1u);         // d2 += A2 B0
+            if constexpr (S == 5) {
+              mma_bf16<2 * TN>(c3, ad(2), bd(1), 1u);            // d3 d4 += A2 [B1 B2]
+              mma_bf16<2 * TN>(c3, ad(3), bd(0), 1u);            // d3 d4 += A3 [B0 B1]
+              mma_bf16<TN>(c3 + TN, ad(4), bd(0), 1u);           // d4 += A4 B0
             }
           }
           mma_commit(&sm.empty[s]);
@@ -394,15 +403,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         uint32_t v[kHalf];
         // exact FP32 integers below 2^24: one round-to-nearest conversion each
-        tmem_ld_cols(lane_base + 0 * 2 * TN + buf * TN + c0, v);
+        tmem_ld_cols(lane_base + buf * 3 * TN + 0 * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
-        tmem_ld_cols(lane_base + 1 * 2 * TN + buf * TN + c0, v);
+        tmem_ld_cols(lane_base + buf * 3 * TN + 1 * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
-        tmem_ld_cols(lane_base + 2 * 2 * TN + buf * TN + c0, v);
+        tmem_ld_cols(lane_base + buf * 3 * TN + 2 * TN + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));

@@ -116,7 +116,7 @@ struct ResProb {
   int64_t y_off, v_off, val_off, ld;
 };
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
-__global__ void jacobi_block_f32(const SmallProb*, const double*, double*, double*, int, float, float);
+__global__ void jacobi_block_f32(const SmallProb*, const double*, double*, double*, int, float, float, int*);
 size_t jacobi_block_smem(int b);
 __global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double, double);
 __global__ void add_inplace(double*, const double*, long long);
@@ -132,6 +132,7 @@ __global__ void ritz_residual(const ResProb*, const double*, const double*, cons
 size_t jacobi_smem(int b);
 size_t cholinv_smem(int b);
 constexpr int kEigMax = 160;
+constexpr int kGramMaxParts = 16;  // most K slices of a partial Gram matrix (cholinv_f32 holds them all)
 
 static GemmProb gp(int M, int N, int K, int64_t ao, int64_t am, int64_t ak, int64_t bo, int64_t bn, int64_t bk,
                    int64_t co, int64_t cm, int64_t cn) {
@@ -302,15 +303,16 @@ struct Graded {
 
 static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp, const double* H, double* X, double* lam,
                       int64_t smtot, int64_t valtot, cudaStream_t s, const std::string& pre = "",
-                      bool near_diag = false, const Graded* gr = nullptr) {
+                      bool near_diag = false, const Graded* gr = nullptr, int* dsweeps = nullptr) {
   if (sp.empty()) return;
   setup_attrs();
   SmallProb* dsp = upload_cached(ctx, pre + "eig.sp", sp, s);
   int bmax = 0;
   for (auto& p : sp) bmax = std::max(bmax, p.b);
   // FP32 Jacobi stage: the block kernel (32 x 32 subproblems per round)
+  // (dsweeps: the sweeps each problem ran, of the last Jacobi stage)
   auto jacobi = [&](const SmallProb* pp, const double* in, double* o, double* l, int sweeps, float tf, float jk) {
-    jacobi_block_f32<<<int(sp.size()), 512, jacobi_block_smem(bmax), s>>>(pp, in, o, l, sweeps, tf, jk);
+    jacobi_block_f32<<<int(sp.size()), 512, jacobi_block_smem(bmax), s>>>(pp, in, o, l, sweeps, tf, jk, dsweeps);
   };
   double* X1 = (double*)ctx->buf(pre + "eig.x1", sizeof(double) * smtot, s);
   double* H1 = (double*)ctx->buf(pre + "eig.h1", sizeof(double) * smtot, s);
@@ -518,7 +520,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   int64_t gtot = 0;
   int nparts = 1;
   if (!sp_it.empty()) {
-    nparts = int(std::max<int64_t>(1, std::min<int64_t>(16, (152 + int64_t(sp_it.size()) - 1) / int64_t(sp_it.size()))));
+    nparts = int(std::max<int64_t>(1, std::min<int64_t>(kGramMaxParts, (152 + int64_t(sp_it.size()) - 1) / int64_t(sp_it.size()))));
     for (auto& x : secs) {
       if (x.direct) continue;
       sp_g.push_back(SmallProb{x.b, 0, gtot, x.sm_off, x.val_off});
@@ -599,6 +601,9 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   double prev_worst = 0;
   const int max_total = std::max(iters, 480);
   std::vector<double> hl(valtot), hres(valtot);
+  // sweeps of the Rayleigh-Ritz eigensolver per iterated sector (tuning log)
+  std::vector<int> hsw(sp_it.size(), 0);
+  int* dsw = sp_it.empty() ? nullptr : (int*)ctx->buf("proj.sweeps", sizeof(int) * sp_it.size(), s);
   double* res = (double*)ctx->buf("proj.res", sizeof(double) * std::max<int64_t>(valtot, 1), s);
   // The direct sectors (N^T N decomposed whole) do not depend on the
   // iterations: their Gram products and eigensolver run once, on the
@@ -684,7 +689,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       gemm_any(ctx, "ss.zrr", rrp, g_z, Nm, Q, Z, s);
       gemm_any(ctx, "ss.h", rrp, g_h, Z, Z, Msm, s);
     }
-    small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s, "", ctx->rr_near_diag);
+    small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s, "", ctx->rr_near_diag, nullptr, dsw);
     // V = Q W (iterative) or W (direct, once the second stream is joined)
     if (!g_v.empty()) gemm_any(ctx, "ss.v", rrp, g_v, Q, Xv, dV, s);
     if (forked) {
@@ -696,6 +701,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                                    cudaMemcpyDeviceToDevice, s));
     }
     BST_CUDA(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * valtot, cudaMemcpyDeviceToHost, s));
+    if (dsw) BST_CUDA(cudaMemcpyAsync(hsw.data(), dsw, sizeof(int) * hsw.size(), cudaMemcpyDeviceToHost, s));
     if (round == 0 && dfro)
       BST_CUDA(cudaMemcpyAsync(hfro.data(), dfro, sizeof(double) * hfro.size(), cudaMemcpyDeviceToHost, s));
     BST_CUDA(cudaStreamSynchronize(s));
@@ -800,9 +806,14 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
     }
     if (ctx->tune_log.size() < (1u << 20)) {
       char line[160];
-      snprintf(line, sizeof(line), "projector subspace: %d iterations, max residual/lambda_max %.3e\n", total,
+      snprintf(line, sizeof(line), "projector subspace: %d iterations, max residual/lambda_max %.3e, blocks", total,
                worst);
       ctx->tune_log += line;
+      for (auto& x : secs)
+        if (!x.direct) ctx->tune_log += " " + std::to_string(x.b);
+      ctx->tune_log += ", Jacobi sweeps";
+      for (int v : hsw) ctx->tune_log += " " + std::to_string(v);
+      ctx->tune_log += "\n";
     }
     const bool ok = worst <= tol || (round > 0 && worst > 0.5 * prev_worst && worst <= 100 * tol);
     if (ok && !mixed_rr) break;
