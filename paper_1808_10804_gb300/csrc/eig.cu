@@ -231,11 +231,14 @@ __global__ void __launch_bounds__(1024) jacobi_eig_f32(const SmallProb* __restri
 // scalar kernel's rounds are bound by those passes), at the same
 // arithmetic.  bp = b rounded up to 32 (zero padding, decoupled).
 constexpr int kBjThreads = 512;
+// row stride of a pair's Q^T (16-byte rows for vector loads)
+constexpr int kQt = 36;
 
 __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* __restrict__ probs,
                                                                const double* __restrict__ in,
                                                                double* __restrict__ out, double* __restrict__ vals,
                                                                int max_sweeps, float tfloor, float junk,
+                                                               float tol, float skip_ang,
                                                                int* __restrict__ sweeps_used) {
   extern __shared__ float sh[];
   const SmallProb pr = probs[blockIdx.x];
@@ -246,13 +249,14 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
   const int npair = nb >> 1;    // <= 5
   float* A = sh;
   float* V = A + bp * ld;
-  float* Sub = V + bp * ld;     // npair x 32 x 33: subproblem, then Q^T
-  float* red = Sub + npair * 32 * 33;
+  float* Sub = V + bp * ld;     // npair x 32 x kQt: subproblem (row stride 33), then Q^T (row stride kQt)
+  float* red = Sub + npair * 32 * kQt;
   int* order = reinterpret_cast<int*>(red + kBjThreads);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31;
   const double* H = in + pr.in_off;
   __shared__ double dmax[32];
+  __shared__ int moved[8];  // per subproblem of a round: some rotation was applied
   {
     double m = 0;
     for (int i = tid; i < b; i += nt) m = fmax(m, fabs(H[(long long)i * b + i]));
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
     }
     const float wmax = red[0];
     __syncthreads();
-    if (wmax <= 1e-13f) break;
+    if (wmax <= tol) break;
     for (int r = 0; r < nb - 1; ++r) {
       // ---- the subproblems: warp p < npair takes block pair p ----
       if (warp < npair) {
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
           if (bj < 0) bj += nb - 1;
         }
         // index map of the pair: local 0..15 -> block bi, 16..31 -> block bj
-        float* S = Sub + warp * 32 * 33;
+        float* S = Sub + warp * 32 * kQt;
         const int gl = (lane < 16 ? bi * 16 + lane : bj * 16 + lane - 16);
         for (int k = 0; k < 32; ++k) {
           const int gk = (k < 16 ? bi * 16 + k : bj * 16 + k - 16);
@@ -330,6 +334,7 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
         for (int k = 0; k < 32; ++k) qt[k] = (k == lane) ? 1.f : 0.f;
         __syncwarp();
         // one cyclic sweep: 31 rounds of 16 disjoint rotations
+        bool any_rot = false;
         for (int rr = 0; rr < 31; ++rr) {
           // lane's partner in round rr (index 31 fixed, others rotate)
           int mate;
@@ -344,12 +349,20 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
           const float apq = S[p * 33 + q], app = S[p * 33 + p], aqq = S[q * 33 + q];
           float c = 1.f, sn = 0.f;
           const float dd = fmaxf(fabsf(app), kTau) * fmaxf(fabsf(aqq), kTau);
-          if (fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd) {
-            const float tau = (aqq - app) / (2.f * apq);
+          // (skip_ang > 0: rotations whose angle test 0.1 a^2 / gap^2 is
+          // below it are left out)
+          const float gq = aqq - app;
+          const bool rot = fabsf(apq) > 1e-30f && apq * apq > 1e-15f * dd &&
+                           !(skip_ang > 0.f && 0.1f * (apq * apq) <= skip_ang * fmaxf(gq * gq, 1e-37f));
+          if (rot) {
+            const float tau = gq / (2.f * apq);
             const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
             sn = t * c;
           }
+          // a step without any rotation leaves S and Q^T as they are
+          if (!__any_sync(0xffffffffu, rot)) continue;
+          any_rot = true;
           // row of this lane: S'[lane] = c S[lane] -/+ s S[mate], then the
           // columns likewise (S' is no longer symmetric); in halves of 16
           // (reads of a half before anyone writes it)
@@ -389,7 +402,8 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
         }
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) S[lane * 33 + k] = qt[k];
+        for (int k = 0; k < 32; ++k) S[lane * kQt + k] = qt[k];
+        if (lane == 0) moved[warp] = int(any_rot);
       }
       __syncthreads();
       // ---- A[P, :] <- Q^T A[P, :]: task (pair, column) ----
@@ -405,17 +419,22 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
           bj = r - pp;
           if (bj < 0) bj += nb - 1;
         }
-        const float* QT = Sub + pp * 32 * 33;
+        if (!moved[pp]) continue;  // Q = I: A[P, :] unchanged
+        const float* QT = Sub + pp * 32 * kQt;
         float a[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) a[k] = A[(k < 16 ? bi * 16 + k : bj * 16 + k - 16) * ld + col];
 #pragma unroll 4
         for (int i = 0; i < 32; ++i) {
           float acc0 = 0.f, acc1 = 0.f;
+          const float4* q4 = reinterpret_cast<const float4*>(QT + i * kQt);
 #pragma unroll
-          for (int k = 0; k < 32; k += 2) {
-            acc0 = fmaf(QT[i * 33 + k], a[k], acc0);
-            acc1 = fmaf(QT[i * 33 + k + 1], a[k + 1], acc1);
+          for (int k = 0; k < 32; k += 4) {
+            const float4 q = q4[k >> 2];
+            acc0 = fmaf(q.x, a[k], acc0);
+            acc1 = fmaf(q.y, a[k + 1], acc1);
+            acc0 = fmaf(q.z, a[k + 2], acc0);
+            acc1 = fmaf(q.w, a[k + 3], acc1);
           }
           A[(i < 16 ? bi * 16 + i : bj * 16 + i - 16) * ld + col] = acc0 + acc1;
         }
@@ -436,18 +455,23 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
           bj = r - pp;
           if (bj < 0) bj += nb - 1;
         }
+        if (!moved[pp]) continue;  // Q = I
         float* M = which ? V : A;
-        const float* QT = Sub + pp * 32 * 33;
+        const float* QT = Sub + pp * 32 * kQt;
         float a[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) a[k] = M[row * ld + (k < 16 ? bi * 16 + k : bj * 16 + k - 16)];
 #pragma unroll 4
         for (int j = 0; j < 32; ++j) {
           float acc0 = 0.f, acc1 = 0.f;
+          const float4* q4 = reinterpret_cast<const float4*>(QT + j * kQt);
 #pragma unroll
-          for (int k = 0; k < 32; k += 2) {
-            acc0 = fmaf(a[k], QT[j * 33 + k], acc0);
-            acc1 = fmaf(a[k + 1], QT[j * 33 + k + 1], acc1);
+          for (int k = 0; k < 32; k += 4) {
+            const float4 q = q4[k >> 2];
+            acc0 = fmaf(a[k], q.x, acc0);
+            acc1 = fmaf(a[k + 1], q.y, acc1);
+            acc0 = fmaf(a[k + 2], q.z, acc0);
+            acc1 = fmaf(a[k + 3], q.w, acc1);
           }
           M[row * ld + (j < 16 ? bi * 16 + j : bj * 16 + j - 16)] = acc0 + acc1;
         }
@@ -479,7 +503,7 @@ __global__ void __launch_bounds__(kBjThreads) jacobi_block_f32(const SmallProb* 
 size_t jacobi_block_smem(int b) {
   const int bp = (b + 31) & ~31;
   const int npair = bp / 32;
-  return sizeof(float) * (2 * bp * (bp + 1) + npair * 32 * 33 + kBjThreads) + sizeof(int) * bp;
+  return sizeof(float) * (2 * bp * (bp + 1) + npair * 32 * kQt + kBjThreads) + sizeof(int) * bp;
 }
 
 size_t jacobi_smem(int b) {

@@ -401,20 +401,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = mbar_wait(&sm.acc_full[buf], int(pc >> 1) & 1, abort_flag, err, spin);
         if (!ok) break;
         tc_fence_after();
-        uint32_t v[kHalf];
-        // exact FP32 integers below 2^24: one round-to-nearest conversion each
-        tmem_ld_cols(lane_base + buf * 3 * TN + 0 * TN + c0, v);
-        tmem_wait_ld();
+        // exact FP32 integers below 2^24: one round-to-nearest conversion
+        // each; 16 columns at a time (the 64-bit sums hold the registers)
 #pragma unroll
-        for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
-        tmem_ld_cols(lane_base + buf * 3 * TN + 1 * TN + c0, v);
-        tmem_wait_ld();
+        for (int h = 0; h < kHalf; h += 16) {
+          uint32_t v[16];
+          tmem_ld16(lane_base + buf * 3 * TN + 0 * TN + c0 + h, v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < kHalf; ++j) T[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
-        tmem_ld_cols(lane_base + buf * 3 * TN + 2 * TN + c0, v);
-        tmem_wait_ld();
+          for (int j = 0; j < 16; ++j) T[h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 18;
+          tmem_ld16(lane_base + buf * 3 * TN + 1 * TN + c0 + h, v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < kHalf; ++j) T[j] += __float2int_rn(__uint_as_float(v[j]));
+          for (int j = 0; j < 16; ++j) T[h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << 9;
+          tmem_ld16(lane_base + buf * 3 * TN + 2 * TN + c0 + h, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) T[h + j] += __float2int_rn(__uint_as_float(v[j]));
+        }
         tc_fence_before();
         mbar_arrive(&sm.acc_empty[buf]);
       }

@@ -116,7 +116,8 @@ struct ResProb {
   int64_t y_off, v_off, val_off, ld;
 };
 __global__ void jacobi_eig_f32(const SmallProb*, const double*, double*, double*, int, float, float);
-__global__ void jacobi_block_f32(const SmallProb*, const double*, double*, double*, int, float, float, int*);
+__global__ void jacobi_block_f32(const SmallProb*, const double*, double*, double*, int, float, float, float, float,
+                                 int*);
 size_t jacobi_block_smem(int b);
 __global__ void oa_update(const SmallProb*, const double*, const double*, double*, double*, double, double, double);
 __global__ void add_inplace(double*, const double*, long long);
@@ -311,8 +312,12 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   for (auto& p : sp) bmax = std::max(bmax, p.b);
   // FP32 Jacobi stage: the block kernel (32 x 32 subproblems per round)
   // (dsweeps: the sweeps each problem ran, of the last Jacobi stage)
-  auto jacobi = [&](const SmallProb* pp, const double* in, double* o, double* l, int sweeps, float tf, float jk) {
-    jacobi_block_f32<<<int(sp.size()), 512, jacobi_block_smem(bmax), s>>>(pp, in, o, l, sweeps, tf, jk, dsweeps);
+  // (tol: the stop test on min(relative, angle) of every pair; 1e-13 is
+  // the FP32 floor)
+  auto jacobi = [&](const SmallProb* pp, const double* in, double* o, double* l, int sweeps, float tf, float jk,
+                    float tol = 1e-13f, float skip_ang = 0.f) {
+    jacobi_block_f32<<<int(sp.size()), 512, jacobi_block_smem(bmax), s>>>(pp, in, o, l, sweeps, tf, jk, tol,
+                                                                          skip_ang, dsweeps);
   };
   double* X1 = (double*)ctx->buf(pre + "eig.x1", sizeof(double) * smtot, s);
   double* H1 = (double*)ctx->buf(pre + "eig.h1", sizeof(double) * smtot, s);
@@ -371,8 +376,14 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   } else if (near_diag) {
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
     // values below 1e-6 of the largest are not resolved by this FP32 pass
-    // (nor refined below): their pairs are left out of the convergence test
-    jacobi(dsp, H, X, lam, 10, 1e-5f, 1e-6f);
+    // (nor refined below): their pairs are left out of the convergence test.
+    // The pass stops once every pair's remaining rotation is below ~1e-4
+    // (or its off-diagonal below 3e-5 of the diagonals' geometric mean):
+    // the three refinement steps below square the angles three times, from
+    // there to far below FP64 rounding.  Rotations by less than ~3e-6 are
+    // left to the refinement as well (sweeps after the first find most
+    // pairs there, and skip their updates).
+    jacobi(dsp, H, X, lam, 10, 1e-5f, 1e-6f, 1e-9f, 1e-12f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   } else {
