@@ -667,6 +667,7 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const float* G = nparts > 0 ? gin + pr.in_off : nullptr;
+  __shared__ __align__(16) float colb[2][32];  // phase 1: a column of the diagonal block
   if (G) {
     // FP32 partial sums, added in slice order.  Every thread keeps the
     // loads of all slices of one 4-wide group in flight at once (the sums
@@ -724,7 +725,10 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
     // (the power of two exactly, the mantissas as two FP32 products)
     for (int q = tid; q < b * b; q += kCholThreads) {
       const int i = q / b, j = q - i * b;
-      L[i * ld + j] = ldexpf(L[i * ld + j], ksc[i] + ksc[j]) * (rsc[i] * rsc[j]);
+      // 2^e as two exact factors (|e| <= 256: each half a normal FP32 power)
+      const int e = ksc[i] + ksc[j], e1 = e >> 1, e2 = e - e1;
+      L[i * ld + j] = L[i * ld + j] * __int_as_float((e1 + 127) << 23) * __int_as_float((e2 + 127) << 23) *
+                      (rsc[i] * rsc[j]);
     }
   } else {
   // unit-diagonal scaling: row i times 1 / sqrt(M_ii) = rsc[i] 2^ksc[i]
@@ -778,26 +782,40 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
       for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        const float dkk = __shfl_sync(0xffffffffu, row[k], k);
+        // column k of the partly reduced block (D_rk of every lane r) goes
+        // through shared memory and comes back to every lane as 16-byte
+        // broadcast loads; double-buffered, so one warp barrier a pivot
+        float* cb = colb[k & 1];
+        cb[lane] = row[k];
+        __syncwarp();
+        float col[32];
+#pragma unroll
+        for (int g = k >> 2; g < 8; ++g) {
+          const float4 v = reinterpret_cast<const float4*>(cb)[g];
+          col[4 * g] = v.x;
+          col[4 * g + 1] = v.y;
+          col[4 * g + 2] = v.z;
+          col[4 * g + 3] = v.w;
+        }
+        const float dkk = col[k];
         const bool dk = !(dkk > 1e-6f);  // the same on every lane
         const float inv = dk ? 1.f : rsqrtf(dkk);  // 1 / D_kk
-        if (lane == k) {
-          row[k] = dk ? 1.f : dkk * inv;
-          mydrop = int(dk);
-          if (dk) {
+        // (selects, not branches: the lanes stay converged)
+        const float rk = row[k];
+        row[k] = lane == k ? (dk ? 1.f : dkk * inv) : (lane > k ? (dk ? 0.f : rk * inv) : rk);
+        if (dk) {  // uniform
+          mydrop = lane == k ? 1 : mydrop;
 #pragma unroll
-            for (int c = 0; c < k; ++c) row[c] = 0.f;
-          }
-        } else if (lane > k) {
-          row[k] = dk ? 0.f : row[k] * inv;
+          for (int c = 0; c < k; ++c) row[c] = lane == k ? 0.f : row[c];
         }
         x[k] *= inv;
         if (!dk) {
+          // D_rj -= L_rk L_jk and x_j -= L_jk x_k with L_jk = D_jk / D_kk
+          const float a = row[k] * inv, bx = x[k] * inv;
 #pragma unroll
           for (int j = k + 1; j < 32; ++j) {
-            const float ljk = __shfl_sync(0xffffffffu, row[k], j);  // D_jk
-            if (lane >= j) row[j] = fmaf(-row[k], ljk, row[j]);
-            x[j] = fmaf(-ljk, x[k], x[j]);
+            if (lane >= j) row[j] = fmaf(-a, col[j], row[j]);
+            x[j] = fmaf(-bx, col[j], x[j]);
           }
         }
       }
@@ -904,14 +922,26 @@ __global__ void __launch_bounds__(kCholThreads) cholinv_f32(const SmallProb* __r
   }
   // Rinv = S L^-T with S the unit-diagonal scaling: Rinv[i][j] = dsc[i] Li[j][i]
   double* R = out + pr.out_off;
-  for (int q0 = tid; q0 < bb; q0 += 4 * kCholThreads) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = q0 + u * kCholThreads;
-      if (q < bb) {
-        const int i = q / b, j = q - i * b;
-        R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : f32_to_f64_scaled(rsc[i] * Li[j * ld + i], ksc[i]);
+  if ((b & 1) || (pr.out_off & 1)) {
+    for (int q = tid; q < bb; q += kCholThreads) {
+      const int i = q / b, j = q - i * b;
+      R[q] = (drop[i] || drop[j] || j < i) ? 0.0 : f32_to_f64_scaled(rsc[i] * Li[j * ld + i], ksc[i]);
+    }
+  } else {
+    // two neighbouring entries of a row per thread, one 16-byte store;
+    // entries below the diagonal are zero without a look at Li
+    double2* R2 = reinterpret_cast<double2*>(R);
+    for (int q2 = tid; q2 < (bb >> 1); q2 += kCholThreads) {
+      const int q = q2 << 1;
+      const int i = q / b, j = q - i * b;
+      double2 v = make_double2(0.0, 0.0);
+      if (j + 1 >= i && !drop[i]) {
+        const float r = rsc[i];
+        const int e = ksc[i];
+        if (j >= i && !drop[j]) v.x = f32_to_f64_scaled(r * Li[j * ld + i], e);
+        if (!drop[j + 1]) v.y = f32_to_f64_scaled(r * Li[(j + 1) * ld + i], e);
       }
+      R2[q2] = v;
     }
   }
 }
