@@ -84,11 +84,14 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 
 // One 64x64 output tile of problem p over the K range [kb, ke), written to
 // out[m * om + n * on].  128 threads = 4 warps in a 2x2 arrangement, each warp
-// a 32x32 sub-tile made of 4x4 DMMA tiles of 8x8.
+// a 32x32 sub-tile made of 4x4 DMMA tiles of 8x8.  The operand tiles are
+// double-buffered in shared memory: the next K block's loads are in flight
+// (in registers) while the current block is multiplied.
+constexpr int kLd = (kF64TileM * kBK) / 128;  // elements of a 64 x 16 tile per thread
 __device__ __forceinline__ void f64_tile(const GemmProb& p, int m0, int n0, int kb, int ke,
                                          const double* __restrict__ A, const double* __restrict__ B,
                                          double* __restrict__ out, long long om, long long on,
-                                         double (*sA)[kF64TileM + kPad], double (*sB)[kF64TileN + kPad]) {
+                                         double (*sA)[kBK][kF64TileM + kPad], double (*sB)[kBK][kF64TileN + kPad]) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int g = lane >> 2, tg = lane & 3;
@@ -99,29 +102,40 @@ __device__ __forceinline__ void f64_tile(const GemmProb& p, int m0, int n0, int 
     for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
   const double* Ap = A + p.a_off;
   const double* Bp = B + p.b_off;
-  for (int k0 = kb; k0 < ke; k0 += kBK) {
+  double ra[kLd], rb[kLd];
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int e = tid; e < kF64TileM * kBK; e += 128) {
+    for (int u = 0; u < kLd; ++u) {
+      const int e = tid + u * 128;
       const int m = e / kBK, k = e % kBK;
-      const int gm = m0 + m, gk = k0 + k;
-      sA[k][m] = (gm < p.M && gk < ke) ? Ap[(long long)gm * p.a_m + (long long)gk * p.a_k] : 0.0;
-      const int gn = n0 + m;
-      sB[k][m] = (gn < p.N && gk < ke) ? Bp[(long long)gn * p.b_n + (long long)gk * p.b_k] : 0.0;
+      const int gm = m0 + m, gn = n0 + m, gk = k0 + k;
+      ra[u] = (gm < p.M && gk < ke) ? Ap[(long long)gm * p.a_m + (long long)gk * p.a_k] : 0.0;
+      rb[u] = (gn < p.N && gk < ke) ? Bp[(long long)gn * p.b_n + (long long)gk * p.b_k] : 0.0;
+    }
+  };
+  if (kb < ke) fetch(kb);
+  int buf = 0;
+  for (int k0 = kb; k0 < ke; k0 += kBK, buf ^= 1) {
+#pragma unroll
+    for (int u = 0; u < kLd; ++u) {
+      const int e = tid + u * 128;
+      sA[buf][e % kBK][e / kBK] = ra[u];
+      sB[buf][e % kBK][e / kBK] = rb[u];
     }
     __syncthreads();
+    if (k0 + kBK < ke) fetch(k0 + kBK);
 #pragma unroll
     for (int kk = 0; kk < kBK; kk += 4) {
       double af[4], bf[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) af[i] = sA[kk + tg][wm + i * 8 + g];
+      for (int i = 0; i < 4; ++i) af[i] = sA[buf][kk + tg][wm + i * 8 + g];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bf[j] = sB[kk + tg][wn + j * 8 + g];
+      for (int j = 0; j < 4; ++j) bf[j] = sB[buf][kk + tg][wn + j * 8 + g];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -135,13 +149,13 @@ __device__ __forceinline__ void f64_tile(const GemmProb& p, int m0, int n0, int 
       }
 }
 
-__global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restrict__ probs,
+__global__ void __launch_bounds__(128, 3) gemm_f64_kernel(const GemmProb* __restrict__ probs,
                                                        const int32_t* __restrict__ tile_prob,
                                                        const int32_t* __restrict__ tile_idx,
                                                        const double* __restrict__ A,
                                                        const double* __restrict__ B, double* __restrict__ C) {
-  __shared__ double sA[kBK][kF64TileM + kPad];
-  __shared__ double sB[kBK][kF64TileN + kPad];
+  __shared__ double sA[2][kBK][kF64TileM + kPad];
+  __shared__ double sB[2][kBK][kF64TileN + kPad];
   const GemmProb p = probs[tile_prob[blockIdx.x]];
   const int nt = (p.N + kF64TileN - 1) / kF64TileN;
   const int m0 = (tile_idx[blockIdx.x] / nt) * kF64TileM;
@@ -152,15 +166,15 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(const GemmProb* __restric
 // Split-K: CTA (tile, s) computes the partial product over the s-th K slice
 // (slices of a multiple of 16) into W[s][problem][m][n]; the reduction adds
 // the slices in a fixed order (deterministic result).
-__global__ void __launch_bounds__(128) gemm_f64_splitk_kernel(const GemmProb* __restrict__ probs,
+__global__ void __launch_bounds__(128, 3) gemm_f64_splitk_kernel(const GemmProb* __restrict__ probs,
                                                               const int32_t* __restrict__ tile_prob,
                                                               const int32_t* __restrict__ tile_idx,
                                                               const double* __restrict__ A,
                                                               const double* __restrict__ B, double* __restrict__ W,
                                                               const int64_t* __restrict__ w_off, long long wtot,
                                                               int ksplit) {
-  __shared__ double sA[kBK][kF64TileM + kPad];
-  __shared__ double sB[kBK][kF64TileN + kPad];
+  __shared__ double sA[2][kBK][kF64TileM + kPad];
+  __shared__ double sB[2][kBK][kF64TileN + kPad];
   const int pi = tile_prob[blockIdx.x];
   const GemmProb p = probs[pi];
   const int nt = (p.N + kF64TileN - 1) / kF64TileN;
