@@ -547,7 +547,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   double gram_flops = 0;
   for (auto& x : secs)
     if (!x.direct) gram_flops += 2.0 * double(std::max(x.M, x.N)) * x.b * x.b;
-  auto cholqr_factor = [&](const double* X, bool z_side) {
+  auto cholqr_factor = [&](const double* X, bool z_side, double* Rout) {
     {
       ProfScope ps(ctx, s, "gram_f32", gram_flops, 0.0);
       gram_f32_kernel<<<dim3(unsigned(sp_g.size()), unsigned(nparts)), 256, 0, s>>>(z_side ? dgz : dgq, nparts, X,
@@ -556,7 +556,7 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       count_launch(ctx);
     }
     ProfScope ps(ctx, s, "cholinv_f32", chol_flops, 0.0);
-    cholinv_f32<<<int(sp_g.size()), 512, cholinv_smem(bmax), s>>>(dsp_g, Msm, Rinv, ctx->d_err, Gp, nparts);
+    cholinv_f32<<<int(sp_g.size()), 512, cholinv_smem(bmax), s>>>(dsp_g, Msm, Rout, ctx->d_err, Gp, nparts);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   };
@@ -564,21 +564,32 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
   // N^T Z carry the condition number sigma_1/sigma_b once, not squared
   // N is split into tensor-core digits once per projector call: its two
   // plans ("ss.z": N, "ss.y": N^T) keep their A digits between steps
+  //
+  // The basis only has to stay well conditioned, not orthonormal: the
+  // iterates span the same subspace whatever basis they are written in.
+  // Once the block has settled (from the fourth step of a round on, mixed
+  // precision), N Q is mapped with the previous step's factor of the N Q
+  // side instead of a fresh one: both are close to the same diagonal of
+  // singular values, so Z Rinv_prev stays near orthonormal, and the fresh
+  // CholQR of the N^T side keeps Q orthonormal.  The Rayleigh-Ritz stage
+  // re-orthonormalises the block to FP64 (and the residual test decides).
+  double* Rz = (double*)ctx->buf("proj.Rinvz", sizeof(double) * std::max<int64_t>(smtot, 1), s);
+  const int fresh_z = prec == BST_FP64 ? 1 << 30 : 3;
   bool n_split = false;
   auto iterate = [&](int n) {
     for (int t = 0; t < n; ++t) {
       gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s, n_split);
-      cholqr_factor(Z, true);
-      gemm_any(ctx, "ss.qz", prec, g_qz, Z, Rinv, Z2, s);
+      if (t < fresh_z) cholqr_factor(Z, true, Rz);
+      gemm_any(ctx, "ss.qz", prec, g_qz, Z, Rz, Z2, s);
       gemm_any(ctx, "ss.y", prec, g_y, Nm, Z2, Y, s, n_split);
       n_split = true;
-      cholqr_factor(Y, false);
+      cholqr_factor(Y, false, Rinv);
       gemm_any(ctx, "ss.qy", prec, g_qy, Y, Rinv, Q, s);
     }
   };
   // second CholQR pass and two first-order polishes: orthonormal to FP64
   auto orthonormalise = [&]() {
-    cholqr_factor(Q, false);
+    cholqr_factor(Q, false, Rinv);
     gemm_any(ctx, "ss.qy", prec, g_qy, Q, Rinv, Y, s);
     for (int r = 0; r < 2; ++r) {
       double* src = (r == 0) ? Y : Q;
