@@ -377,13 +377,13 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
     ProfScope ps(ctx, s, "jacobi_f32", jac_flops, 0.0);
     // values below 1e-6 of the largest are not resolved by this FP32 pass
     // (nor refined below): their pairs are left out of the convergence test.
-    // The pass stops once every pair's remaining rotation is below ~1e-4
-    // (or its off-diagonal below 3e-5 of the diagonals' geometric mean):
+    // The pass stops once every pair's remaining rotation is below ~3e-4
+    // (or its off-diagonal below 1e-4 of the diagonals' geometric mean):
     // the three refinement steps below square the angles three times, from
-    // there to far below FP64 rounding.  Rotations by less than ~3e-6 are
+    // there to far below FP64 rounding.  Rotations by less than ~3e-5 are
     // left to the refinement as well (sweeps after the first find most
     // pairs there, and skip their updates).
-    jacobi(dsp, H, X, lam, 10, 1e-5f, 1e-6f, 1e-9f, 1e-12f);
+    jacobi(dsp, H, X, lam, 10, 1e-5f, 1e-6f, 1e-8f, 1e-10f);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx);
   } else {
