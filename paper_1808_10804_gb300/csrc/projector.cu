@@ -406,28 +406,54 @@ static void small_eig(Ctx* ctx, bst_prec prec, const std::vector<SmallProb>& sp,
   // three refinement steps: quadratic from the FP32 stage's angles, which
   // for a pair of values closer than ~1e-6 relative are limited by FP32
   // rounding to ~1e-2 (two steps reach 1e-8 there, three the FP64 floor)
+  // (not graded) X and T = H X side by side in one buffer XC, so that
+  // X^T X and X^T T are one launch: X^T [X | T]
+  std::vector<GemmProb> g_hx2, g_xs;
+  double *XC = nullptr, *XS = nullptr;
+  if (!gr) {
+    for (auto& p : sp) {
+      const int b = p.b;
+      const int64_t o = p.in_off;
+      g_hx2.push_back(gp(b, b, b, o, b, 1, o, 1, b, smtot + o, b, 1));         // T = H X
+      g_xs.push_back(gp(b, b, b, o, 1, b, o, 1, b, o, b, 1));                  // X^T X
+    }
+    for (auto& p : sp) {
+      const int b = p.b;
+      const int64_t o = p.in_off;
+      g_xs.push_back(gp(b, b, b, o, 1, b, smtot + o, 1, b, smtot + o, b, 1));  // X^T T
+    }
+    XC = (double*)ctx->buf(pre + "eig.xc", sizeof(double) * 2 * smtot, s);
+    XS = (double*)ctx->buf(pre + "eig.xs", sizeof(double) * 2 * smtot, s);
+    BST_CUDA(cudaMemcpyAsync(XC, X, sizeof(double) * smtot, cudaMemcpyDeviceToDevice, s));
+  }
   for (int it = 0; it < 3; ++it) {
-    gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
+    const double* xtx = XtX;
+    const double* sm = S;
     if (gr) {
+      gemm_any(ctx, pre + "oa.xtx", prec, g_xtx, X, X, XtX, s, false, ws);
       // S = (N X)^T (N X): accurate relative to the singular values, so
       // every pair above eps sigma_1 is refined
       gemm_any(ctx, pre + "oa.w", prec, g_w, gr->Nm, X, Wg, s, false, ws);
       gemm_any(ctx, pre + "oa.ww", prec, g_ww, Wg, Wg, S, s, false, ws);
     } else {
-      gemm_any(ctx, pre + "oa.hx", prec, g_hx, H, X, T, s, false, ws);
-      gemm_any(ctx, pre + "oa.s", prec, g_s, X, T, S, s, false, ws);
+      gemm_any(ctx, pre + "oa.hx2", prec, g_hx2, H, XC, XC, s, false, ws);
+      gemm_any(ctx, pre + "oa.xs", prec, g_xs, XC, XC, XS, s, false, ws);
+      xtx = XS;
+      sm = XS + smtot;
     }
     // about two CTAs per SM over all problems
     const int slices = std::max(1, std::min(64, 304 / int(sp.size())));
     // graded: the FP32 passes resolve eigenvalues down to ~1e-12 of the
     // largest; S is accurate to ~eps sigma_1 (sigma_i + sigma_j)
-    oa_update<<<dim3(unsigned(sp.size()), unsigned(slices)), 256, 0, s>>>(dsp, XtX, S, E, lam, 1e-9,
+    oa_update<<<dim3(unsigned(sp.size()), unsigned(slices)), 256, 0, s>>>(dsp, xtx, sm, E, lam, 1e-9,
                                                                           gr ? 1e-12 : 1e-6, gr ? 1e-13 : 0.0);
-    gemm_any(ctx, pre + "oa.xe", prec, g_xe, X, E, T, s, false, ws);
-    add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(X, T, smtot);
+    double* Xi = gr ? X : XC;
+    gemm_any(ctx, pre + "oa.xe", prec, g_xe, Xi, E, T, s, false, ws);
+    add_inplace<<<std::max<int64_t>(1, std::min<int64_t>((smtot + 255) / 256, 1216)), 256, 0, s>>>(Xi, T, smtot);
     BST_CUDA(cudaGetLastError());
     count_launch(ctx, 2);
   }
+  if (!gr) BST_CUDA(cudaMemcpyAsync(X, XC, sizeof(double) * smtot, cudaMemcpyDeviceToDevice, s));
 }
 
 // Sum of squares of each listed block of x (one CTA per block, fixed order).
