@@ -1010,14 +1010,16 @@ size_t cholinv_smem(int b) {
 }
 
 // out = alpha * I + beta * in (square blocks)
+// (grid: problems x row slices; CTA (p, y) takes rows y, y + gridDim.y, ...)
 __global__ void ident_combo(const SmallProb* __restrict__ probs, const double* __restrict__ in, double* __restrict__ out,
                             double alpha, double beta) {
   const SmallProb pr = probs[blockIdx.x];
   const int b = pr.b;
-  for (int q = threadIdx.x; q < b * b; q += blockDim.x) {
-    const int i = q / b, j = q % b;
-    out[pr.out_off + q] = (i == j ? alpha : 0.0) + beta * in[pr.in_off + q];
-  }
+  for (int i = blockIdx.y; i < b; i += gridDim.y)
+    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+      const long long q = (long long)i * b + j;
+      out[pr.out_off + q] = (i == j ? alpha : 0.0) + beta * in[pr.in_off + q];
+    }
 }
 
 // Deterministic pseudo-random normal entries (counter-based hash + Box-Muller).
@@ -1030,7 +1032,12 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x;
 }
 
-__global__ void randn_fill(double* x, long long n, uint64_t seed) {
+// One launch fills several ranges: range blockIdx.y is x[off, off + n) with
+// its own seed (table: off, n, seed as 64-bit words).
+__global__ void randn_fill(double* x, const long long* __restrict__ ranges) {
+  const long long off = ranges[3 * blockIdx.y], n = ranges[3 * blockIdx.y + 1];
+  const uint64_t seed = static_cast<uint64_t>(ranges[3 * blockIdx.y + 2]);
+  x += off;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint64_t a = mix64(seed * 0x9E3779B97F4A7C15ull + 2 * i + 1);
     const uint64_t c = mix64(a ^ 0xD1B54A32D192ED03ull);

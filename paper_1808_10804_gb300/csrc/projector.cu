@@ -128,7 +128,7 @@ struct GramProb {
 };
 __global__ void gram_f32_kernel(const GramProb*, int, const double*, float*);
 __global__ void ident_combo(const SmallProb*, const double*, double*, double, double);
-__global__ void randn_fill(double*, long long, uint64_t);
+__global__ void randn_fill(double*, const long long*);
 __global__ void ritz_residual(const ResProb*, const double*, const double*, const double*, double*);
 size_t jacobi_smem(int b);
 size_t cholinv_smem(int b);
@@ -621,21 +621,29 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       double* src = (r == 0) ? Y : Q;
       double* dst = (r == 0) ? Q : Y;
       gemm_any(ctx, "ss.gy", prec, g_gy, src, src, Msm, s);
-      ident_combo<<<int(sp_it.size()), 256, 0, s>>>(dsp_it, Msm, Rinv, 1.5, -0.5);
+      ident_combo<<<dim3(unsigned(sp_it.size()), 32), 128, 0, s>>>(dsp_it, Msm, Rinv, 1.5, -0.5);
       count_launch(ctx);
       gemm_any(ctx, "ss.qy", prec, g_qy, src, Rinv, dst, s);
     }
     std::swap(Q, Y);  // the polished block is in Y
   };
   if (!sp_it.empty()) {
-    // deterministic random start
+    // deterministic random start (a seed per sector, one launch)
+    std::vector<long long> rng;
+    int64_t nmax = 0;
     for (auto& x : secs)
       if (!x.direct) {
         const int64_t n = int64_t(x.N) * x.b;
-        randn_fill<<<int(std::min<int64_t>((n + 255) / 256, 1216)), 256, 0, s>>>(Q + x.q_off, n,
-                                                                              0x5eed0000ull + uint64_t(x.cs->key + 4096));
-        count_launch(ctx);
+        rng.push_back(x.q_off);
+        rng.push_back(n);
+        rng.push_back(static_cast<long long>(0x5eed0000ull + uint64_t(x.cs->key + 4096)));
+        nmax = std::max(nmax, n);
       }
+    const long long* drng = upload_cached(ctx, "proj.randn", rng, s);
+    randn_fill<<<dim3(unsigned(std::min<int64_t>((nmax + 255) / 256, 256)), unsigned(rng.size() / 3)), 256, 0, s>>>(
+        Q, drng);
+    BST_CUDA(cudaGetLastError());
+    count_launch(ctx);
   }
   // Rounds of `iters` iterations, each closed by a Rayleigh-Ritz step.  A
   // round is accepted when every Ritz pair that the truncation would keep
