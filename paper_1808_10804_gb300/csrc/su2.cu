@@ -309,6 +309,48 @@ struct Su2Plan {
   }
 };
 
+// One output element per thread: acc[t] = sum over the group's
+// contributions i of X[i][t] P_i[m][col], for the NT output trees of the
+// group.  NT is a compile-time bound (1, 2, 4 or 8 >= the group's tree
+// count): this part's FP64 pipe does about two FMAs per clock per SM, so the
+// kernel is bound by its multiply-adds and does only the ones it needs.
+template <int NT>
+__device__ __forceinline__ void recouple_body(const RcGroup& g, int ntau, int e, bool live, int m, int col,
+                                              const RcContrib* __restrict__ ct, const double* __restrict__ X,
+                                              const double* __restrict__ P, double* C, double alpha, double beta,
+                                              RcContrib* sct, double* sx) {
+  double acc[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) acc[t] = 0.0;
+  for (int c0 = 0; c0 < g.ncontrib; c0 += kRcStage) {
+    const int nc = min(kRcStage, g.ncontrib - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += kRcThreads) sct[i] = ct[g.contrib0 + c0 + i];
+    for (int i = threadIdx.x; i < nc * NT; i += kRcThreads) {
+      const int ci = i / NT, t = i - ci * NT;
+      sx[i] = X[(g.contrib0 + c0 + ci) * kMaxTau + t];
+    }
+    __syncthreads();
+    if (live) {
+      for (int i = 0; i < nc; ++i) {
+        const double p = P[sct[i].p_off + (long long)m * sct[i].ld + col];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc[t] = fma(sx[i * NT + t], p, acc[t]);
+      }
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if (t < ntau) {
+      double* out = C + g.c_off[t] + e;
+      double v = alpha * acc[t];
+      if (beta != 0.0) v += beta * *out;
+      *out = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kRcThreads) recouple_kernel(const RcGroup* __restrict__ groups,
                                                               const int2* __restrict__ chunks,
                                                               const RcContrib* __restrict__ ct,
@@ -323,33 +365,11 @@ __global__ void __launch_bounds__(kRcThreads) recouple_kernel(const RcGroup* __r
   const int e = ch.y + threadIdx.x;
   const bool live = e < n;
   const int m = live ? e / g.N : 0, col = live ? e - m * g.N : 0;
-  double acc[kMaxTau];
-#pragma unroll
-  for (int t = 0; t < kMaxTau; ++t) acc[t] = 0.0;
-  for (int c0 = 0; c0 < g.ncontrib; c0 += kRcStage) {
-    const int nc = min(kRcStage, g.ncontrib - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nc; i += kRcThreads) sct[i] = ct[g.contrib0 + c0 + i];
-    for (int i = threadIdx.x; i < nc * kMaxTau; i += kRcThreads) sx[i] = X[(g.contrib0 + c0) * kMaxTau + i];
-    __syncthreads();
-    if (live) {
-      for (int i = 0; i < nc; ++i) {
-        const double p = P[sct[i].p_off + (long long)m * sct[i].ld + col];
-#pragma unroll
-        for (int t = 0; t < kMaxTau; ++t) acc[t] += sx[i * kMaxTau + t] * p;
-      }
-    }
-  }
-  if (!live) return;
-#pragma unroll
-  for (int t = 0; t < kMaxTau; ++t) {
-    if (t < g.ntau) {
-      double* out = C + g.c_off[t] + e;
-      double v = alpha * acc[t];
-      if (beta != 0.0) v += beta * *out;
-      *out = v;
-    }
-  }
+  const int ntau = g.ntau;  // the same for the whole CTA
+  if (ntau <= 1) recouple_body<1>(g, ntau, e, live, m, col, ct, X, P, C, alpha, beta, sct, sx);
+  else if (ntau <= 2) recouple_body<2>(g, ntau, e, live, m, col, ct, X, P, C, alpha, beta, sct, sx);
+  else if (ntau <= 4) recouple_body<4>(g, ntau, e, live, m, col, ct, X, P, C, alpha, beta, sct, sx);
+  else recouple_body<kMaxTau>(g, ntau, e, live, m, col, ct, X, P, C, alpha, beta, sct, sx);
 }
 
 namespace {
