@@ -481,7 +481,8 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
                              double*& dV, std::vector<double>& hSig, cudaStream_t s, bool top_chi = true) {
   // The iterations only have to converge the subspace, so they run in the
   // call's arithmetic; the Rayleigh-Ritz stage fixes the individual vectors,
-  // whose error is amplified by 1/gap, and always runs in FP64.
+  // whose error is amplified by 1/gap: its Gram, eigensolver and V = Q W
+  // run in FP64 (N Q itself comes from the call's product, see below).
   const bst_prec rr = BST_FP64;
   int64_t vtot = 0, qtot = 0, ztot = 0, smtot = 0, valtot = 0;
   // Block of an iterated sector.  In mixed precision: the sector keeps at
@@ -741,8 +742,13 @@ static bool factors_subspace(Ctx* ctx, double* Nm, std::vector<PSec>& secs, int6
       iterate(steps);
       total += steps;
       orthonormalise();
-      // Rayleigh-Ritz: H = (N Q)^T (N Q)
-      gemm_any(ctx, "ss.zrr", rrp, g_z, Nm, Q, Z, s);
+      // Rayleigh-Ritz: H = (N Q)^T (N Q).  N Q comes from the iterations'
+      // product (the call's arithmetic, N's digits already split): the
+      // digit GEMM reproduces it to ~2^-40 of its row and column scales,
+      // which moves the Ritz pairs far less than the residual tolerance;
+      // Z^T Z, the eigensolver and V = Q W run in the Rayleigh-Ritz
+      // arithmetic (FP64 for the final round)
+      gemm_any(ctx, "ss.z", prec, g_z, Nm, Q, Z, s, n_split);
       gemm_any(ctx, "ss.h", rrp, g_h, Z, Z, Msm, s);
     }
     small_eig(ctx, rrp, sp_it, Msm, Xv, lam, smtot, valtot, s, "", ctx->rr_near_diag, nullptr, dsw);
