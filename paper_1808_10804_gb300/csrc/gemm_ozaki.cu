@@ -17,9 +17,12 @@
 // The epilogue forms the result with 64-bit integer arithmetic and one
 // conversion to FP64.  Relative error ~2^-40 against the row/column scales.
 //
-// Kernel: persistent, one CTA per SM walking the plan's 128 x 64 output
-// tiles; warp 0 drives TMA (64-byte swizzled K-major tiles, 3-stage ring),
-// warp 1 issues tcgen05.mma from one thread, warps 2..9 drain tensor memory.  Every wait of the pipeline
+// Kernel: persistent, one CTA per SM walking the plan's 128 x 64 (or
+// 128 x 32) output tiles; warp 0 drives TMA (64-byte swizzled K-major tiles,
+// a ring of 3 stages for five slices, up to 6 for three), warp 1 issues
+// tcgen05.mma from one thread (the 15 digit products of a 16-K step as 8
+// products, each an A slice times a run of stacked B slices), warps 2..9
+// drain tensor memory.  Every wait of the pipeline
 // is bounded by the launch's spin limit: on expiry the kernel records
 // BST_E_TIMEOUT in the context's error word and every role leaves its loop;
 // before tensor memory is freed and the CTA exits, the TMA copies it has
