@@ -396,7 +396,7 @@ BST_API bst_status bst_svd_projector(bst_ctx ctx, bst_layout Rtop, const double*
  * row-major n x n symmetric matrices H (device, back to back, n <= 160) ->
  * eigenvectors X (device, same layout, column j = eigenvector j) and
  * eigenvalues lam (device, n per matrix, descending).  Two FP32 Jacobi
- * passes followed by two Ogita-Aishima refinement steps whose matrix
+ * passes followed by three Ogita-Aishima refinement steps whose matrix
  * products run in `prec`.  Accuracy: eigenvalues above 1e-6 lambda_max (and
  * their eigenvectors, where separated) reach FP64 accuracy (BST_FP64) or
  * ~1e-12 lambda_max (BST_OZAKI); eigenvalues below 1e-6 lambda_max form one
