@@ -959,19 +959,20 @@ struct GramProb {
 
 constexpr int kGramRows = 32;
 
-__global__ void __launch_bounds__(256) gram_f32_kernel(const GramProb* __restrict__ probs, int nparts,
-                                                       const double* __restrict__ X, float* __restrict__ out) {
-  __shared__ float xs[kGramRows][kEigMax + 4];
-  const GramProb p = probs[blockIdx.x];
-  const int s = blockIdx.y;
+// U x U entries per thread (ti + 16 u, tj + 16 v, u, v < U): U = 8 covers
+// b <= 128, U = 10 covers b <= 160; the smaller instance does 64 instead of
+// 100 multiply-adds per row for the common b = 128.
+template <int U>
+__device__ __forceinline__ void gram_f32_body(const GramProb& p, int s, int nparts, const double* __restrict__ X,
+                                              float* __restrict__ out, float (*xs)[kEigMax + 4]) {
   const int r0 = int((long long)p.M * s / nparts), r1 = int((long long)p.M * (s + 1) / nparts);
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   for (int e = threadIdx.x; e < kGramRows * (kEigMax + 4); e += 256) (&xs[0][0])[e] = 0.f;
-  float acc[10][10];
+  float acc[U][U];
 #pragma unroll
-  for (int u = 0; u < 10; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 10; ++v) acc[u][v] = 0.f;
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.f;
   for (int rb = r0; rb < r1; rb += kGramRows) {
     const int nr = min(kGramRows, r1 - rb);
     __syncthreads();
@@ -981,26 +982,34 @@ __global__ void __launch_bounds__(256) gram_f32_kernel(const GramProb* __restric
     }
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
-      float a[10], c[10];
+      float a[U], c[U];
 #pragma unroll
-      for (int u = 0; u < 10; ++u) {
+      for (int u = 0; u < U; ++u) {
         a[u] = xs[r][ti + 16 * u];
         c[u] = xs[r][tj + 16 * u];
       }
 #pragma unroll
-      for (int u = 0; u < 10; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 10; ++v) acc[u][v] = fmaf(a[u], c[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fmaf(a[u], c[v], acc[u][v]);
     }
   }
   float* o = out + p.out_off + (long long)s * p.b * p.b;
 #pragma unroll
-  for (int u = 0; u < 10; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 10; ++v) {
+    for (int v = 0; v < U; ++v) {
       const int i = ti + 16 * u, j = tj + 16 * v;
       if (i < p.b && j < p.b) o[i * p.b + j] = acc[u][v];
     }
+}
+
+__global__ void __launch_bounds__(256) gram_f32_kernel(const GramProb* __restrict__ probs, int nparts,
+                                                       const double* __restrict__ X, float* __restrict__ out) {
+  __shared__ float xs[kGramRows][kEigMax + 4];
+  const GramProb p = probs[blockIdx.x];
+  if (p.b <= 128) gram_f32_body<8>(p, int(blockIdx.y), nparts, X, out, xs);
+  else gram_f32_body<10>(p, int(blockIdx.y), nparts, X, out, xs);
 }
 
 size_t cholinv_smem(int b) {
