@@ -124,8 +124,11 @@ __device__ __forceinline__ void f64_tile(const GemmProb& p, int m0, int n0, int 
     }
     __syncthreads();
     if (k0 + kBK < ke) fetch(k0 + kBK);
+    // (k steps past the end of the range hold only zero padding)
+    const int kn = min(kBK, ke - k0);
 #pragma unroll
     for (int kk = 0; kk < kBK; kk += 4) {
+      if (kk >= kn) break;
       double af[4], bf[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) af[i] = sA[buf][kk + tg][wm + i * 8 + g];
